@@ -1,0 +1,226 @@
+/*
+ * ed.h -- C ABI of the GB300 time-dependent Hubbard exact-diagonalisation
+ * library (libhubbard_ed.so).
+ *
+ * The library implements the hot path of Innerberger, Worm, Prauhart, Kauch,
+ * "Electron-light interaction in nonequilibrium: exact diagonalization for
+ * time dependent Hubbard Hamiltonians" (arXiv:2005.13498): the Hubbard
+ * Hamiltonian H(t) with Peierls phases (Sec. 2.1-2.2, Eqs. (1), (3)) in one
+ * (n_up, n_dn) sector (Sec. 2.3, 3.1), applied matrix-free on the GPU inside a
+ * fixed-dimension Lanczos approximation of exp(-i tau H(t_mid)) v (Sec. 3.4,
+ * Algorithm 6) for the exponential midpoint rule (Eq. (32)), with the
+ * observables of Sec. 3.5 and the nonequilibrium Green's functions of Eq. (15).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Sites are 0..Ns-1 (Ns <= 16).  A spin configuration is an Ns-bit word,
+ *   bit i = occupation of site i.  Each spin basis lists all words with n
+ *   set bits in ascending integer order; this is the order of the fermionic
+ *   hash of Eq. (36).  A sector vector is a dim_up x dim_dn matrix Psi stored
+ *   row-major: element (r_up, r_dn) at offset r_up * dim_dn + r_dn.
+ * - Complex vectors are interleaved (re, im): ED_C128 = two float64 per
+ *   element, ED_C64 = two float32 per element.  ED_C64 keeps every Lanczos
+ *   scalar (inner products, norms, the tridiagonal matrix and its
+ *   exponential) in float64; only vectors and the apply run in float32.
+ * - Fermion sign: modes are ordered all up sites, then all down sites; a hop
+ *   p -> q of one spin picks up (-1)^(occupied sites of that spin strictly
+ *   between p and q) (Eqs. (7)-(8), (26)).  The paper's site-interleaved mode
+ *   order differs by a diagonal +-1 gauge that leaves every observable here
+ *   unchanged.
+ * - Hopping p -> q on bond b has matrix element -t_b exp(-i A(t).d_b) times
+ *   the fermion sign, the reverse hop the complex conjugate (Eq. (3) with a
+ *   uniform vector potential, e = 1); d_b = r_q - r_p.
+ * - Pointers to vectors may be device pointers (CUDA memory allocated by the
+ *   caller) or, where a call says so, host pointers; the library detects which
+ *   and copies host data in and out itself.  All other arrays are host memory.
+ * - Streams: `stream` is a cudaStream_t passed as void*; NULL = the legacy
+ *   default stream.  Calls on one context must not run concurrently from
+ *   several host threads.
+ * - Errors: every call returns an ed_status; no C++ exception crosses the
+ *   ABI.  ed_last_error() returns a human-readable message for the last
+ *   failing call on that context (or on any context when ctx is NULL).
+ * - Ownership: the context owns its tables and workspace; caller-provided
+ *   vectors stay owned by the caller and are never freed by the library.
+ */
+#ifndef HUBBARD_ED_H
+#define HUBBARD_ED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ed_ctx ed_ctx;
+
+typedef enum {
+  ED_OK = 0,
+  ED_ERR_ARG = 1,          /* invalid argument (bad sector, null pointer, ...)   */
+  ED_ERR_CUDA = 2,         /* a CUDA runtime call failed                          */
+  ED_ERR_OOM = 3,          /* device allocation failed or exceeds the workspace cap */
+  ED_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                  */
+  ED_ERR_UNSUPPORTED = 5,  /* outside the supported range (Ns > 16, m > 64, ...)   */
+  ED_ERR_STATE = 6,        /* call order violated (e.g. apply before set_lattice)  */
+  ED_ERR_NUMERIC = 7       /* non-finite value detected in a norm or coefficient   */
+} ed_status;
+
+typedef enum { ED_C128 = 0, ED_C64 = 1 } ed_dtype;
+
+/* Vector potential of the pump pulse, A(t) = A0 exp(-(t-t0)^2/(2 sigma^2))
+ * sin(omega (t - t0)) * dir, entering every bond through A(t).d_b (Eq. (3)).
+ * dir is used as given (not normalised).                                     */
+typedef struct {
+  double A0, omega, sigma, t0;
+  double dir[3];
+} ed_pulse;
+
+/* Optional per-step outputs of ed_propagate (all host arrays, each nullable). */
+typedef struct {
+  double* docc;    /* [n_steps+1] <d>(t_n) = (1/Ns) sum_k w_d[k] |psi_k|^2,
+                      Eq. (13) through the weight vector of Sec. 3.5; not
+                      divided by |psi|^2                                       */
+  double* norm2;   /* [n_steps+1] |psi(t_n)|^2                                 */
+  double* energy;  /* [n_steps+1] E(t_n) = (1/Ns) <psi|H(t_n)|psi>, Eq. (14);
+                      costs one extra apply per step                          */
+  double* delta;   /* [n_steps] a-posteriori estimate delta of Algorithm 6
+                      (diagnostic only; the Krylov dimension stays fixed)      */
+  int32_t* m_eff;  /* [n_steps] Krylov dimension used (< m after breakdown)    */
+  int32_t profile; /* nonzero: launch kernels one by one (no CUDA graph) with
+                      a CUDA event pair around every launch on the launching
+                      stream, and report per-kind device time below           */
+  double* kernel_ms;        /* [ED_KERNEL_KINDS] summed event time per kind  */
+  int64_t* kernel_launches; /* [ED_KERNEL_KINDS] launches per kind           */
+} ed_observables;
+
+/* Kernel kinds reported by the profile mode, in this order.                  */
+#define ED_KERNEL_KINDS 6
+/* 0 apply (fused H x_j with the three-term recurrence and <v_j, w>),
+ * 1 update (x_{j+1} = w - alpha_j v_j and |x_{j+1}|), 2 small exponential,
+ * 3 combine (psi = beta V y with <d> and |psi|^2), 4 energy apply,
+ * 5 Green's-function overlaps.                                               */
+
+/* Create a context for the sector H^{n_up}_{n_dn}(Ns) (Sec. 3.1, Eq. (18)):
+ * enumerates both spin bases and their ranks on the host.
+ * Errors: ED_ERR_ARG if out == NULL or n_up/n_dn outside 0..Ns;
+ * ED_ERR_UNSUPPORTED if Ns < 1 or Ns > 16.  On error *out is set to NULL.   */
+ed_status ed_build_basis(ed_ctx** out, int Ns, int n_up, int n_dn);
+
+/* Sector shape: dim_up = C(Ns, n_up), dim_dn = C(Ns, n_dn) (Eq. (18)).       */
+ed_status ed_dims(const ed_ctx* ctx, int64_t* dim_up, int64_t* dim_dn);
+
+/* Copy the spin basis words (ascending) of spin 0 (up) or 1 (down) into
+ * words[dim_spin] (host).  Used to check the basis against other codes.       */
+ed_status ed_get_basis(const ed_ctx* ctx, int spin, uint32_t* words);
+
+/* Define the lattice and interaction (Sec. 2.1, Eq. (1); Sec. 3.2-3.3).
+ * Bond b joins sites p[b] != q[b] with hopping magnitude t_hop[b] and
+ * displacement d[3b..3b+2] = r_q - r_p (minimum image across a periodic wrap).
+ * U is the on-site repulsion; eps (nullable, Ns entries) adds
+ * eps_i (n_i,up + n_i,dn) (eps_i = -v_ii of the paper).  Builds the per-spin
+ * connection tables (target rank, bond class and orientation, fermion sign;
+ * the O(N_nz) hop-emulation construction suggested in Sec. 3.3) and uploads
+ * them to the current CUDA device.  May be called again to change the lattice.
+ * Bonds listed twice add up.  Errors: ED_ERR_ARG for a bad site index,
+ * p == q, a non-finite value or more than 128 distinct (t, d) bond classes;
+ * ED_ERR_CUDA / ED_ERR_OOM for device failures.                             */
+ed_status ed_set_lattice(ed_ctx* ctx, int n_bonds, const int32_t* p,
+                         const int32_t* q, const double* t_hop,
+                         const double* d, double U, const double* eps);
+
+/* Set the static vector potential A (3 doubles) used by ed_apply_H and
+ * ed_double_occupation-side energy queries.  Default A = 0.                  */
+ed_status ed_set_field(ed_ctx* ctx, const double A[3]);
+
+/* Copy the connection table of spin 0/1 to host arrays for inspection:
+ * off[dim+1] (row offsets) and ent[off[dim]] packed entries
+ * (bits 0-15 target rank, bits 16-23 group = 2*class + orientation,
+ * bit 31 fermion sign (1 = negative)); n_classes receives the number of bond
+ * classes.  Either array may be NULL to query sizes only (*nnz_out).          */
+ed_status ed_get_table(const ed_ctx* ctx, int spin, int32_t* off,
+                       uint32_t* ent, int64_t* nnz_out, int32_t* n_classes);
+
+/* w = H(A) v for nvec vectors stored back to back (each dim_up*dim_dn
+ * elements), A from ed_set_field.  v and w are DEVICE pointers of the given
+ * dtype and must not overlap.  Asynchronous on `stream`.
+ * Errors: ED_ERR_STATE before ed_set_lattice, ED_ERR_ARG for NULL / host
+ * pointers or nvec < 1.                                                      */
+ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype,
+                     int nvec, void* stream);
+
+/* Ground state of H(A = 0) (Sec. 3.4, "Ground state"): float64 Lanczos with
+ * full reorthogonalisation and explicit restarts (replacing the paper's
+ * shifted power iteration, Algorithms 4-5), started from a seeded
+ * pseudo-random vector.  psi (DEVICE or host, complex128, unit norm on
+ * return, phase-fixed so that its largest-magnitude element is real and
+ * positive) receives the eigenvector, *E0 the eigenvalue; resid_out
+ * (nullable) receives |H psi - E0 psi|.  Stops when the residual is below
+ * tol * max(1, |E0|) or after max_iter applies (then returns ED_OK with the
+ * best estimate; check resid_out).                                           */
+ed_status ed_ground_state(ed_ctx* ctx, void* psi, double* E0, double tol,
+                          int max_iter, uint64_t seed, double* resid_out);
+
+/* Propagate psi from t_start over n_steps steps of the exponential midpoint
+ * rule (Eq. (32)): psi <- exp(-i dt H(t_n + dt/2)) psi, t_n = t_start + n dt,
+ * each exponential by m Lanczos steps (Algorithm 6 with fixed m, breakdown
+ * exit when beta_j <= tol * max(1, max|alpha|, max beta), tol = 1e-13 for
+ * ED_C128 and 1e-6 for ED_C64).  psi (DEVICE or host pointer of `dtype`) is
+ * updated in place.  obs (nullable) receives observables at t_0..t_{n_steps}.
+ * One step is captured as a CUDA graph and replayed.  Requires 1 <= m <= 64.
+ * Errors: ED_ERR_ARG, ED_ERR_STATE, ED_ERR_UNSUPPORTED (m > 64),
+ * ED_ERR_NUMERIC (non-finite norm), ED_ERR_CUDA / ED_ERR_OOM.                */
+ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype,
+                       const ed_pulse* pulse, double t_start, double dt,
+                       int n_steps, int m, const ed_observables* obs,
+                       void* stream);
+
+/* <d> = (1/Ns) sum_k w_d[k] |psi_k|^2 (Sec. 3.5, Eq. (13)) and, if d_site is
+ * not NULL, the per-site values <n_i,up n_i,dn> (Ns entries).  psi is a DEVICE
+ * or host pointer.  Synchronous.                                             */
+ed_status ed_double_occupation(ed_ctx* ctx, const void* psi, ed_dtype dtype,
+                               double* d_avg, double* d_site);
+
+/* Nonequilibrium Green's functions of Eq. (15) with reference time 0
+ * (Sec. 2.5, 3.7): for every site i and spin s, phi = c_is psi0 and
+ * phi' = c^+_is psi0 are built in the sectors with one electron fewer / more
+ * (the hash lookup of Sec. 3.7), then phi, phi' and psi0 itself are propagated
+ * together by the midpoint rule (pulse, dt, m as in ed_propagate) in one
+ * batched launch per kernel, and after every step
+ *   G_less[n][i][s]  = i <c_is psi(t_n)| phi_is(t_n)>,
+ *   G_great[n][i][s] = -i <c^+_is psi(t_n)| phi'_is(t_n)>,
+ * n = 0..n_steps.  psi0 (DEVICE or host, complex128, in ctxN's sector) is not
+ * modified.  G_less / G_great are host arrays of (n_steps+1)*Ns*2 complex128
+ * (interleaved re, im); an entry whose target sector does not exist is 0.
+ * dtype selects the vector precision of the propagation (ED_C64: float32
+ * vectors with float64 Lanczos scalars and float64 overlaps).                */
+ed_status ed_spectral_propagate(ed_ctx* ctxN, const void* psi0,
+                                ed_dtype dtype, const ed_pulse* pulse,
+                                double dt, int n_steps, int m,
+                                double* G_less, double* G_great, void* stream);
+
+/* Apply c_is (create = 0) or c^+_is (create = 1) to psi of ctx's sector and
+ * write the result into out (a vector of ctx_dst's sector, which must be
+ * (n_up-+1, n_dn) for s = 0 or (n_up, n_dn-+1) for s = 1 on the same Ns).
+ * Sign (-1)^(occupied modes before (i, s)), Eqs. (7)-(8).  DEVICE pointers,
+ * asynchronous on stream.                                                    */
+ed_status ed_apply_fermion_op(ed_ctx* ctx, ed_ctx* ctx_dst, int site, int spin,
+                              int create, const void* psi, void* out,
+                              ed_dtype dtype, void* stream);
+
+/* Bytes of device memory the context currently holds (tables + workspace).  */
+ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes);
+
+/* Release the context and all device memory it owns.  NULL is accepted.      */
+ed_status ed_destroy(ed_ctx* ctx);
+
+/* Message of the last failing call on ctx (ctx may be NULL).  Never NULL.    */
+const char* ed_last_error(const ed_ctx* ctx);
+
+/* Library version string.                                                    */
+const char* ed_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUBBARD_ED_H */

@@ -1,0 +1,408 @@
+// C ABI (include/ed.h): contexts, tables on the device, and the drivers of
+// ed_apply_H, ed_propagate and the sector maps.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "ctx.h"
+
+using namespace ed;
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace ed {
+
+ed_status fail(ed_ctx* ctx, ed_status st, const std::string& msg) {
+  g_last_error = msg;
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+ed_status cuda_fail(ed_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void build_sector_host(SectorGPU& S, const LatticeHost& L, int n_up, int n_dn) {
+  S.Ns = L.Ns;
+  S.n_up = n_up;
+  S.n_dn = n_dn;
+  S.up = build_spin_table(L, n_up);
+  S.dn = build_spin_table(L, n_dn);
+  S.has_eps = L.has_eps;
+  S.uploaded = false;
+}
+
+cudaError_t upload_sector(SectorGPU& S) {
+  cudaError_t e;
+  if ((e = upload(S.up_off, S.up.off)) != cudaSuccess) return e;
+  if ((e = upload(S.up_ent, S.up.ent)) != cudaSuccess) return e;
+  if ((e = upload(S.dn_off, S.dn.off)) != cudaSuccess) return e;
+  if ((e = upload(S.dn_ent, S.dn.ent)) != cudaSuccess) return e;
+  if ((e = upload(S.up_word, S.up.words)) != cudaSuccess) return e;
+  if ((e = upload(S.dn_word, S.dn.words)) != cudaSuccess) return e;
+  if (S.has_eps) {
+    if ((e = upload(S.up_eps, S.up.eps_sum)) != cudaSuccess) return e;
+    if ((e = upload(S.dn_eps, S.dn.eps_sum)) != cudaSuccess) return e;
+  } else {
+    S.up_eps.release();
+    S.dn_eps.release();
+  }
+  SectorDev& d = S.dev;
+  d.dim_up = S.up.dim;
+  d.dim_dn = S.dn.dim;
+  d.n_up = S.n_up;
+  d.n_dn = S.n_dn;
+  d.up_off = static_cast<const int32_t*>(S.up_off.p);
+  d.up_ent = static_cast<const uint32_t*>(S.up_ent.p);
+  d.dn_off = static_cast<const int32_t*>(S.dn_off.p);
+  d.dn_ent = static_cast<const uint32_t*>(S.dn_ent.p);
+  d.up_word = static_cast<const uint32_t*>(S.up_word.p);
+  d.dn_word = static_cast<const uint32_t*>(S.dn_word.p);
+  d.up_eps = S.has_eps ? static_cast<const double*>(S.up_eps.p) : nullptr;
+  d.dn_eps = S.has_eps ? static_cast<const double*>(S.dn_eps.p) : nullptr;
+  S.uploaded = true;
+  return cudaSuccess;
+}
+
+cudaError_t build_sector_gpu(SectorGPU& S, const LatticeHost& L, int n_up, int n_dn) {
+  build_sector_host(S, L, n_up, n_dn);
+  return upload_sector(S);
+}
+
+ed_status ensure_device(ed_ctx* ctx) {
+  if (!ctx->lattice_set) return fail(ctx, ED_ERR_STATE, "ed_set_lattice has not been called");
+  if (ctx->sec.uploaded) return ED_OK;
+  CK(ctx, cudaGetDevice(&ctx->device));
+  if (!ctx->stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+  CK(ctx, upload_sector(ctx->sec));
+  return ED_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Event-based ordering between the caller's stream and the context stream.
+cudaError_t join_streams(cudaStream_t from, cudaStream_t to) {
+  if (from == to) return cudaSuccess;
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(ev, from);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+  cudaEventDestroy(ev);
+  return e;
+}
+
+std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* pulse,
+                                      double t_start, double dt, int n_steps, bool mid) {
+  const int ng = 2 * L.n_classes;
+  std::vector<double> out((size_t)n_steps * ng * 2);
+  for (int n = 0; n < n_steps; ++n) {
+    const double t = t_start + (n + (mid ? 0.5 : 0.0)) * dt;
+    double A[3] = {0, 0, 0};
+    if (pulse) pulse_A(pulse->A0, pulse->omega, pulse->sigma, pulse->t0, pulse->dir, t, A);
+    group_coefficients(L, A, out.data() + (size_t)n * ng * 2);
+  }
+  return out;
+}
+
+}  // namespace ed
+
+extern "C" {
+
+const char* ed_version(void) { return "hubbard_ed 0.1 (sm_103a)"; }
+
+const char* ed_last_error(const ed_ctx* ctx) {
+  if (ctx && !ctx->err.empty()) return ctx->err.c_str();
+  return g_last_error.c_str();
+}
+
+ed_status ed_build_basis(ed_ctx** out, int Ns, int n_up, int n_dn) {
+  if (!out) return fail(nullptr, ED_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (Ns < 1 || Ns > kMaxSites) return fail(nullptr, ED_ERR_UNSUPPORTED, "Ns must be in 1..16");
+  if (n_up < 0 || n_up > Ns || n_dn < 0 || n_dn > Ns)
+    return fail(nullptr, ED_ERR_ARG, "n_up and n_dn must be in 0..Ns");
+  ed_ctx* c = new (std::nothrow) ed_ctx();
+  if (!c) return fail(nullptr, ED_ERR_OOM, "host allocation failed");
+  c->Ns = Ns;
+  c->n_up = n_up;
+  c->n_dn = n_dn;
+  c->up_words = spin_basis(Ns, n_up);
+  c->dn_words = spin_basis(Ns, n_dn);
+  c->dim_up = (int64_t)c->up_words.size();
+  c->dim_dn = (int64_t)c->dn_words.size();
+  *out = c;
+  return ED_OK;
+}
+
+ed_status ed_dims(const ed_ctx* ctx, int64_t* dim_up, int64_t* dim_dn) {
+  if (!ctx || !dim_up || !dim_dn) return fail(nullptr, ED_ERR_ARG, "NULL argument");
+  *dim_up = ctx->dim_up;
+  *dim_dn = ctx->dim_dn;
+  return ED_OK;
+}
+
+ed_status ed_get_basis(const ed_ctx* ctx, int spin, uint32_t* words) {
+  if (!ctx || !words || (spin != 0 && spin != 1)) return fail(nullptr, ED_ERR_ARG, "bad argument");
+  const auto& w = spin == 0 ? ctx->up_words : ctx->dn_words;
+  std::memcpy(words, w.data(), w.size() * sizeof(uint32_t));
+  return ED_OK;
+}
+
+ed_status ed_set_lattice(ed_ctx* ctx, int n_bonds, const int32_t* p, const int32_t* q,
+                         const double* t_hop, const double* d, double U, const double* eps) {
+  if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
+  LatticeHost L;
+  std::string err = make_lattice(L, ctx->Ns, n_bonds, p, q, t_hop, d, U, eps);
+  if (!err.empty()) return fail(ctx, ED_ERR_ARG, err);
+  ctx->lat = L;
+  ctx->lattice_set = false;
+  ctx->engine.reset();
+  ctx->spec_engine.reset();
+  ctx->spec_sectors.clear();
+  ctx->plan.valid = false;
+  build_sector_host(ctx->sec, ctx->lat, ctx->n_up, ctx->n_dn);
+  ctx->lattice_set = true;
+  return ED_OK;
+}
+
+ed_status ed_set_field(ed_ctx* ctx, const double A[3]) {
+  if (!ctx || !A) return fail(nullptr, ED_ERR_ARG, "NULL argument");
+  for (int k = 0; k < 3; ++k) {
+    if (!std::isfinite(A[k])) return fail(ctx, ED_ERR_ARG, "A is not finite");
+    ctx->A[k] = A[k];
+  }
+  return ED_OK;
+}
+
+ed_status ed_get_table(const ed_ctx* ctx, int spin, int32_t* off, uint32_t* ent,
+                       int64_t* nnz_out, int32_t* n_classes) {
+  if (!ctx || (spin != 0 && spin != 1)) return fail(nullptr, ED_ERR_ARG, "bad argument");
+  if (!ctx->lattice_set) return fail(nullptr, ED_ERR_STATE, "lattice not set");
+  const SpinTable& T = spin == 0 ? ctx->sec.up : ctx->sec.dn;
+  if (nnz_out) *nnz_out = (int64_t)T.ent.size();
+  if (n_classes) *n_classes = ctx->lat.n_classes;
+  if (off) std::memcpy(off, T.off.data(), T.off.size() * sizeof(int32_t));
+  if (ent) std::memcpy(ent, T.ent.data(), T.ent.size() * sizeof(uint32_t));
+  return ED_OK;
+}
+
+ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return fail(nullptr, ED_ERR_ARG, "NULL argument");
+  const SectorGPU& S = ctx->sec;
+  int64_t b = S.up_off.bytes + S.up_ent.bytes + S.dn_off.bytes + S.dn_ent.bytes +
+              S.up_word.bytes + S.dn_word.bytes + S.up_eps.bytes + S.dn_eps.bytes;
+  if (ctx->engine) b += ctx->engine->device_bytes();
+  if (ctx->spec_engine) b += ctx->spec_engine->device_bytes();
+  *bytes = b;
+  return ED_OK;
+}
+
+ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nvec,
+                     void* stream) {
+  if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
+  if (ed_status e = ensure_device(ctx)) return e;
+  if (!v || !w || nvec < 1) return fail(ctx, ED_ERR_ARG, "v, w must be non-NULL and nvec >= 1");
+  if (dtype != ED_C128 && dtype != ED_C64) return fail(ctx, ED_ERR_ARG, "bad dtype");
+  if (v == w) return fail(ctx, ED_ERR_ARG, "v and w must not alias");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fp64 = dtype == ED_C128;
+  ApplyPlan& P = ctx->plan;
+  const bool same_field = P.A[0] == ctx->A[0] && P.A[1] == ctx->A[1] && P.A[2] == ctx->A[2];
+  if (!(P.valid && P.nvec == nvec && P.v == v && P.w == w && P.fp64 == fp64 && same_field)) {
+    if (!is_device_ptr(v) || !is_device_ptr(w))
+      return fail(ctx, ED_ERR_ARG, "ed_apply_H needs device pointers");
+    P.valid = false;
+    const int64_t D = ctx->dim_up * ctx->dim_dn;
+    const size_t esz = fp64 ? 16 : 8;
+    std::vector<VecDev> vd(nvec);
+    std::vector<ApplyBlock> amap;
+    for (int b = 0; b < nvec; ++b) {
+      std::memset(&vd[b], 0, sizeof(VecDev));
+      vd[b].sector = 0;
+      vd[b].D = D;
+      vd[b].x1 = const_cast<char*>(static_cast<const char*>(v)) + (size_t)b * D * esz;
+      vd[b].w = static_cast<char*>(w) + (size_t)b * D * esz;
+      vd[b].apply_begin = (int)amap.size();
+      for (int r = 0; r < ctx->dim_up; ++r) amap.push_back({b, r, 1, 0});
+      vd[b].apply_end = (int)amap.size();
+    }
+    const int ng = 2 * ctx->lat.n_classes;
+    std::vector<double> cf(std::max(1, ng) * 2, 0.0);
+    group_coefficients(ctx->lat, ctx->A, cf.data());
+    std::vector<float> cff(cf.begin(), cf.end());
+    std::vector<SectorDev> secs = {ctx->sec.dev};
+    std::vector<LanczosState> st(nvec);
+    std::memset(st.data(), 0, st.size() * sizeof(LanczosState));
+    CK(ctx, upload(P.sec, secs));
+    CK(ctx, upload(P.vec, vd));
+    CK(ctx, upload(P.st, st));
+    CK(ctx, upload(P.amap, amap));
+    CK(ctx, P.partials.alloc(sizeof(double) * 4 * amap.size()));
+    CK(ctx, P.counters.alloc(sizeof(unsigned) * nvec));
+    CK(ctx, cudaMemset(P.counters.p, 0, sizeof(unsigned) * nvec));
+    if (fp64) CK(ctx, upload(P.coefs, cf));
+    else CK(ctx, upload(P.coefs, cff));
+    std::memset(&P.args, 0, sizeof(P.args));
+    P.args.sec = static_cast<const SectorDev*>(P.sec.p);
+    P.args.vec = static_cast<VecDev*>(P.vec.p);
+    P.args.st = static_cast<LanczosState*>(P.st.p);
+    P.args.apply_map = static_cast<const ApplyBlock*>(P.amap.p);
+    P.args.partials = static_cast<double*>(P.partials.p);
+    P.args.counters = static_cast<unsigned*>(P.counters.p);
+    P.args.coefs = P.coefs.p;
+    P.args.n_groups = ng;
+    P.args.nvec = nvec;
+    P.args.Ns = ctx->Ns;
+    P.args.max_dim_dn = (int)ctx->dim_dn;
+    P.args.U = ctx->lat.U;
+    P.shape = apply_shape((int)ctx->dim_dn, fp64, ng);
+    CK(ctx, prepare_apply(fp64, P.shape));
+    P.nblk = (int)amap.size();
+    P.nvec = nvec;
+    P.v = v;
+    P.w = w;
+    P.fp64 = fp64;
+    for (int k = 0; k < 3; ++k) P.A[k] = ctx->A[k];
+    P.valid = true;
+  }
+  CK(ctx, launch_apply(fp64, P.args, P.nblk, P.shape, 0, s));
+  return ED_OK;
+}
+
+ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* pulse,
+                       double t_start, double dt, int n_steps, int m,
+                       const ed_observables* obs, void* stream) {
+  if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
+  if (!ctx->lattice_set) return fail(ctx, ED_ERR_STATE, "ed_set_lattice has not been called");
+  if (!psi) return fail(ctx, ED_ERR_ARG, "psi is NULL");
+  if (dtype != ED_C128 && dtype != ED_C64) return fail(ctx, ED_ERR_ARG, "bad dtype");
+  if (n_steps < 0) return fail(ctx, ED_ERR_ARG, "n_steps < 0");
+  if (m < 1) return fail(ctx, ED_ERR_ARG, "m < 1");
+  if (m > kMaxKrylov) return fail(ctx, ED_ERR_UNSUPPORTED, "m > 64");
+  if (!std::isfinite(dt) || !std::isfinite(t_start)) return fail(ctx, ED_ERR_ARG, "dt/t_start not finite");
+  if (pulse && !(std::isfinite(pulse->A0) && std::isfinite(pulse->omega) &&
+                 std::isfinite(pulse->sigma) && pulse->sigma != 0.0 && std::isfinite(pulse->t0)))
+    return fail(ctx, ED_ERR_ARG, "pulse parameters not finite or sigma == 0");
+  if (ed_status e = ensure_device(ctx)) return e;
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = ctx->stream;
+  const bool fp64 = dtype == ED_C128;
+  const int64_t D = ctx->dim_up * ctx->dim_dn;
+  const size_t esz = fp64 ? 16 : 8;
+  const bool on_device = is_device_ptr(psi);
+  const bool energy = obs && obs->energy;
+  const bool profile = obs && obs->profile;
+
+  EngineConfig cfg;
+  cfg.fp64 = fp64;
+  cfg.m = m;
+  cfg.energy = energy;
+  cfg.n_steps_cap = std::max(1, n_steps);
+  std::vector<EngineVector> vecs = {{0, D, on_device ? psi : nullptr, !on_device}};
+  CK(ctx, join_streams(us, s));
+  if (!ctx->engine || !ctx->engine->compatible(cfg, vecs)) {
+    ctx->engine.reset(new Engine());
+    cfg.n_steps_cap = std::max(cfg.n_steps_cap, 64);
+    std::string err = ctx->engine->setup(cfg, {ctx->sec.dev}, vecs, 2 * ctx->lat.n_classes,
+                                         ctx->Ns, ctx->lat.U, fp64 ? 1e-13 : 1e-6, s);
+    if (!err.empty()) {
+      ctx->engine.reset();
+      return fail(ctx, err.find("memory") != std::string::npos ? ED_ERR_OOM : ED_ERR_CUDA, err);
+    }
+  }
+  Engine& E = *ctx->engine;
+  if (!on_device) CK(ctx, cudaMemcpyAsync(E.vec_x1(0), psi, D * esz, cudaMemcpyHostToDevice, s));
+  std::vector<double> coefs = step_coefficients(ctx->lat, pulse, t_start, dt, n_steps, true);
+  std::vector<double> coefs_obs;
+  if (energy) coefs_obs = step_coefficients(ctx->lat, pulse, t_start, dt, n_steps + 1, false);
+  CKS(ctx, E.begin(coefs, coefs_obs, n_steps, dt, s));
+  CKS(ctx, E.run(n_steps, profile, obs ? obs->kernel_ms : nullptr,
+                 obs ? obs->kernel_launches : nullptr, s));
+  int status = 0;
+  CKS(ctx, E.fetch(0, n_steps, obs ? obs->docc : nullptr, obs ? obs->norm2 : nullptr,
+                   energy ? obs->energy : nullptr, obs ? obs->delta : nullptr,
+                   obs ? obs->m_eff : nullptr, &status, s));
+  if (!on_device) {
+    CK(ctx, cudaMemcpyAsync(psi, E.vec_x1(0), D * esz, cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+  }
+  CK(ctx, join_streams(s, us));
+  if (status != 0) return fail(ctx, ED_ERR_NUMERIC, "non-finite norm or inner product during propagation");
+  return ED_OK;
+}
+
+ed_status ed_double_occupation(ed_ctx* ctx, const void* psi, ed_dtype dtype, double* d_avg,
+                               double* d_site) {
+  if (!ctx || !psi || !d_avg) return fail(ctx, ED_ERR_ARG, "NULL argument");
+  if (ed_status e = ensure_device(ctx)) return e;
+  const bool fp64 = dtype == ED_C128;
+  const int64_t D = ctx->dim_up * ctx->dim_dn;
+  const size_t esz = fp64 ? 16 : 8;
+  cudaStream_t s = ctx->stream;
+  DevMem tmp, part, out;
+  const void* p = psi;
+  if (!is_device_ptr(psi)) {
+    CK(ctx, tmp.alloc(D * esz));
+    CK(ctx, cudaMemcpyAsync(tmp.p, psi, D * esz, cudaMemcpyHostToDevice, s));
+    p = tmp.p;
+  }
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(1216, (D + 1023) / 1024));
+  CK(ctx, part.alloc(sizeof(double) * (kMaxSites + 1) * nblk));
+  CK(ctx, out.alloc(sizeof(double) * (kMaxSites + 1)));
+  CK(ctx, launch_docc_sites(fp64, p, &ctx->sec.dev, (int)ctx->dim_up, (int)ctx->dim_dn, ctx->Ns,
+                            static_cast<double*>(part.p), nblk, static_cast<double*>(out.p), s));
+  double h[kMaxSites + 1];
+  CK(ctx, cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  *d_avg = h[0] / ctx->Ns;
+  if (d_site)
+    for (int i = 0; i < ctx->Ns; ++i) d_site[i] = h[1 + i];
+  return ED_OK;
+}
+
+ed_status ed_apply_fermion_op(ed_ctx* ctx, ed_ctx* dst, int site, int spin, int create,
+                              const void* psi, void* out, ed_dtype dtype, void* stream) {
+  if (!ctx || !dst || !psi || !out) return fail(ctx, ED_ERR_ARG, "NULL argument");
+  if (site < 0 || site >= ctx->Ns || (spin != 0 && spin != 1))
+    return fail(ctx, ED_ERR_ARG, "bad site or spin");
+  const int dn = create ? 1 : -1;
+  const int tu = ctx->n_up + (spin == 0 ? dn : 0), td = ctx->n_dn + (spin == 1 ? dn : 0);
+  if (dst->Ns != ctx->Ns || dst->n_up != tu || dst->n_dn != td)
+    return fail(ctx, ED_ERR_ARG, "destination context has the wrong sector");
+  if (ed_status e = ensure_device(ctx)) return e;
+  if (!is_device_ptr(psi) || !is_device_ptr(out))
+    return fail(ctx, ED_ERR_ARG, "device pointers required");
+  std::vector<int32_t> map = fermion_map(ctx->Ns, ctx->n_up, ctx->n_dn, site, spin, create != 0);
+  DevMem dmap;
+  CK(ctx, upload(dmap, map));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(ctx, launch_fermion_op(dtype == ED_C128, psi, out, (int)ctx->dim_up, (int)ctx->dim_dn,
+                            (int)dst->dim_up, (int)dst->dim_dn, spin,
+                            static_cast<const int32_t*>(dmap.p), s));
+  CK(ctx, cudaStreamSynchronize(s));  // map buffer is freed on return
+  return ED_OK;
+}
+
+ed_status ed_destroy(ed_ctx* ctx) {
+  if (!ctx) return ED_OK;
+  ctx->engine.reset();
+  ctx->spec_engine.reset();
+  ctx->spec_sectors.clear();
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return ED_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal definitions shared by the host driver and the CUDA kernels.
+// Not part of the public ABI (include/ed.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ed {
+
+constexpr int kMaxKrylov = 64;      // largest supported Krylov dimension m
+constexpr int kMaxSites = 16;       // Ns <= 16: spin ranks fit in 16 bits
+constexpr int kMaxGroups = 256;     // 2 * bond classes (group id is 8 bits)
+
+// Packed connection-table entry (one per allowed hop into a target state):
+//   bits  0-15  rank of the source configuration (same spin basis)
+//   bits 16-23  group = 2 * bond class + orientation (0: p->q, 1: q->p)
+//   bit  31     fermion sign of the hop (1 = negative)
+constexpr uint32_t kEntRankMask = 0xFFFFu;
+constexpr int kEntGroupShift = 16;
+constexpr uint32_t kEntSignBit = 0x80000000u;
+
+// Device view of one sector's tables (pointers into device memory).
+struct SectorDev {
+  int dim_up, dim_dn;
+  int n_up, n_dn;
+  const int32_t* up_off;    // [dim_up + 1]
+  const uint32_t* up_ent;   // packed entries, target-row major
+  const int32_t* dn_off;    // [dim_dn + 1]
+  const uint32_t* dn_ent;
+  const uint32_t* up_word;  // [dim_up] spin configuration words
+  const uint32_t* dn_word;  // [dim_dn]
+  const double* up_eps;     // [dim_up] sum of eps over occupied sites, or null
+  const double* dn_eps;     // [dim_dn]
+};
+
+// Per-vector Lanczos scalars, all float64, 1-based Krylov index j.
+// x_j denotes the stored (unnormalised) vector, v_j = inv_scale[j] * x_j the
+// Lanczos vector of Algorithm 6.  x_1 is the propagated state itself.
+struct LanczosState {
+  double alpha[kMaxKrylov + 2];
+  double beta[kMaxKrylov + 2];
+  double inv_scale[kMaxKrylov + 2];
+  double comb_re[kMaxKrylov + 2];   // combine coefficients: psi = sum comb_j x_j
+  double comb_im[kMaxKrylov + 2];
+  double scale;      // running max(1, |alpha|, beta) for the breakdown test
+  double beta0;      // |psi| at the start of the step
+  double delta;      // a-posteriori estimate of the last step
+  double dot_out;    // scratch result of a plain dot product
+  double red[4];     // scratch results of generic reductions
+  int m;             // requested Krylov dimension
+  int m_eff;         // dimension in use (set < m on breakdown)
+  int stopped;       // 1 once breakdown was detected in this step
+  int step;          // time-step counter (indexes coefficient arrays)
+  int status;        // 0 ok, ED_ERR_NUMERIC on a non-finite norm
+  int pad[3];
+};
+
+// One propagated vector of a batch.
+struct VecDev {
+  int sector;          // index into the SectorDev array
+  int pad0;
+  int64_t D;           // dim_up * dim_dn
+  void* x1;            // the state psi (x_1)
+  void* V;             // (m-1) * D slots for x_2 .. x_m
+  void* w;             // scratch vector of D elements
+  int apply_begin, apply_end;   // range of apply blocks of this vector
+  int ew_begin, ew_end;         // range of elementwise blocks
+  double* out_docc;    // device [n_steps+1] or null
+  double* out_norm2;   // device [n_steps+1] or null
+  double* out_energy;  // device [n_steps+1] or null
+  double* out_delta;   // device [n_steps] or null
+  int* out_meff;       // device [n_steps] or null
+};
+
+// Elementwise block: elements [begin, end) of vector vec.
+struct EwBlock {
+  int vec;
+  int pad;
+  int64_t begin, end;
+};
+
+// Apply block: rows [row0, row0 + nrows) of vector vec.
+struct ApplyBlock {
+  int vec;
+  int row0;
+  int nrows;
+  int pad;
+};
+
+// Everything the batched kernels need, passed by value.
+struct BatchArgs {
+  const SectorDev* sec;
+  VecDev* vec;
+  LanczosState* st;
+  const ApplyBlock* apply_map;
+  const EwBlock* ew_map;
+  double* partials;       // >= 4 * max(#apply blocks, #ew blocks)
+  unsigned* counters;     // [nvec], zero between kernels
+  const void* coefs;      // [n_steps][n_groups] complex of the vector dtype
+  const void* coefs_obs;  // [n_steps+1][n_groups] (energy at t_n) or null
+  int n_groups;
+  int nvec;
+  int Ns;
+  int max_dim_dn;
+  double U;
+  double tau;
+  double break_tol;
+};
+
+}  // namespace ed

@@ -1,0 +1,92 @@
+// Internal context type and helpers shared by the C-ABI translation units.
+#pragma once
+
+#include "../../include/ed.h"
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "engine.h"
+#include "kernels.cuh"
+#include "tables.h"
+
+namespace ed {
+
+struct SectorGPU {
+  int Ns = 0, n_up = 0, n_dn = 0;
+  SpinTable up, dn;
+  DevMem up_off, up_ent, dn_off, dn_ent, up_word, dn_word, up_eps, dn_eps;
+  SectorDev dev{};
+  bool has_eps = false;
+  bool uploaded = false;
+};
+
+struct ApplyPlan {
+  int nvec = 0;
+  const void* v = nullptr;
+  void* w = nullptr;
+  bool fp64 = false;
+  DevMem sec, vec, st, amap, partials, counters, coefs;
+  BatchArgs args{};
+  LaunchShape shape{};
+  int nblk = 0;
+  double A[3] = {0, 0, 0};
+  bool valid = false;
+};
+
+}  // namespace ed
+
+struct ed_ctx {
+  int Ns = 0, n_up = 0, n_dn = 0;
+  int64_t dim_up = 0, dim_dn = 0;
+  std::vector<uint32_t> up_words, dn_words;
+  bool lattice_set = false;
+  ed::LatticeHost lat;
+  ed::SectorGPU sec;
+  double A[3] = {0, 0, 0};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  ed::ApplyPlan plan;
+  std::unique_ptr<ed::Engine> engine;
+  std::unique_ptr<ed::Engine> spec_engine;
+  std::vector<std::unique_ptr<ed::SectorGPU>> spec_sectors;
+};
+
+namespace ed {
+
+ed_status fail(ed_ctx* ctx, ed_status st, const std::string& msg);
+ed_status cuda_fail(ed_ctx* ctx, cudaError_t e, const char* what);
+cudaError_t build_sector_gpu(SectorGPU& S, const LatticeHost& L, int n_up, int n_dn);
+void build_sector_host(SectorGPU& S, const LatticeHost& L, int n_up, int n_dn);
+cudaError_t upload_sector(SectorGPU& S);
+// Upload the context's tables and create its stream on first GPU use.
+ed_status ensure_device(ed_ctx* ctx);
+bool is_device_ptr(const void* p);
+cudaError_t join_streams(cudaStream_t from, cudaStream_t to);
+std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* pulse,
+                                      double t_start, double dt, int n_steps, bool mid);
+
+template <typename T>
+cudaError_t upload(DevMem& m, const std::vector<T>& v) {
+  cudaError_t e = m.alloc(std::max<size_t>(1, v.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpy(m.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+}  // namespace ed
+
+#define CK(ctx, call)                                               \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ed::cuda_fail((ctx), e_, #call);  \
+  } while (0)
+
+#define CKS(ctx, strexpr)                                           \
+  do {                                                              \
+    std::string s_ = (strexpr);                                     \
+    if (!s_.empty()) return ed::fail((ctx), ED_ERR_CUDA, s_);       \
+  } while (0)

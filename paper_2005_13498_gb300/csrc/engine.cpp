@@ -1,0 +1,370 @@
+// Batched midpoint-rule propagation engine (see engine.h).
+#include "engine.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace ed {
+
+#define ED_TRY(call)                                                    \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess)                                              \
+      return std::string(#call) + ": " + cudaGetErrorString(e_);        \
+  } while (0)
+
+cudaError_t DevMem::alloc(size_t n) {
+  release();
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return e;
+  }
+  bytes = n;
+  return cudaSuccess;
+}
+
+void DevMem::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+Engine::~Engine() {
+  if (exec_) cudaGraphExecDestroy(exec_);
+  if (graph_) cudaGraphDestroy(graph_);
+}
+
+size_t Engine::device_bytes() const {
+  return d_sec_.bytes + d_vec_.bytes + d_st_.bytes + d_amap_.bytes + d_emap_.bytes +
+         d_partials_.bytes + d_counters_.bytes + d_coefs_.bytes + d_coefs_obs_.bytes +
+         d_V_.bytes + d_w_.bytes + d_out_.bytes + d_owned_x1_.bytes + d_maps_.bytes +
+         d_map_off_.bytes + d_map_spin_.bytes + d_ovl_.bytes;
+}
+
+bool Engine::compatible(const EngineConfig& cfg, const std::vector<EngineVector>& vecs) const {
+  if (cfg.fp64 != cfg_.fp64 || cfg.m != cfg_.m || cfg.energy != cfg_.energy ||
+      cfg.overlaps != cfg_.overlaps || cfg.n_steps_cap > cfg_.n_steps_cap)
+    return false;
+  if (vecs.size() != vecs_.size()) return false;
+  for (size_t i = 0; i < vecs.size(); ++i) {
+    if (vecs[i].sector != vecs_[i].sector || vecs[i].D != vecs_[i].D) return false;
+    if (!vecs[i].owned_x1 && (vecs_[i].owned_x1 || vecs[i].x1 != vecs_[i].x1)) return false;
+    if (vecs[i].owned_x1 != vecs_[i].owned_x1) return false;
+  }
+  return true;
+}
+
+static int64_t ew_chunk(int64_t D) {
+  int64_t c = (D + 1215) / 1216;
+  c = ((c + 255) / 256) * 256;
+  return std::max<int64_t>(1024, std::min<int64_t>(16384, c));
+}
+
+std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>& sectors,
+                          const std::vector<EngineVector>& vecs, int n_groups, int Ns,
+                          double U, double break_tol, cudaStream_t stream) {
+  if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
+  if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
+  cfg_ = cfg;
+  sectors_ = sectors;
+  vecs_ = vecs;
+  n_groups_ = n_groups;
+  Ns_ = Ns;
+  U_ = U;
+  break_tol_ = break_tol;
+  have_overlaps_ = false;
+  const size_t esz = cfg.fp64 ? 16 : 8;
+  const int nv = (int)vecs.size();
+  const int m = cfg.m;
+
+  // owned state buffers
+  int64_t owned = 0;
+  for (auto& v : vecs_) if (v.owned_x1) owned += v.D;
+  ED_TRY(d_owned_x1_.alloc((size_t)owned * esz));
+  {
+    int64_t o = 0;
+    for (auto& v : vecs_)
+      if (v.owned_x1) {
+        v.x1 = static_cast<char*>(d_owned_x1_.p) + (size_t)o * esz;
+        o += v.D;
+      }
+  }
+  // Krylov storage and scratch
+  int64_t totD = 0;
+  for (auto& v : vecs_) totD += v.D;
+  ED_TRY(d_V_.alloc((size_t)std::max(0, m - 1) * totD * esz));
+  ED_TRY(d_w_.alloc((size_t)totD * esz));
+
+  // block maps
+  std::vector<ApplyBlock> amap;
+  std::vector<EwBlock> emap;
+  std::vector<VecDev> vd(nv);
+  int max_dim_dn = 1;
+  int64_t voff = 0;
+  const int ncap = cfg.n_steps_cap;
+  // outputs per vector: docc, norm2, energy [ncap+1], delta [ncap], meff [ncap]
+  const size_t per_vec_out = (size_t)4 * (ncap + 1) + (ncap + 1);
+  ED_TRY(d_out_.alloc(per_vec_out * nv * sizeof(double)));
+  for (int i = 0; i < nv; ++i) {
+    const SectorDev& sd = sectors_[vecs_[i].sector];
+    max_dim_dn = std::max(max_dim_dn, sd.dim_dn);
+    VecDev& v = vd[i];
+    std::memset(&v, 0, sizeof(v));
+    v.sector = vecs_[i].sector;
+    v.D = vecs_[i].D;
+    v.x1 = vecs_[i].x1;
+    v.V = static_cast<char*>(d_V_.p) + (size_t)std::max(0, m - 1) * voff * esz;
+    v.w = static_cast<char*>(d_w_.p) + (size_t)voff * esz;
+    voff += v.D;
+    v.apply_begin = (int)amap.size();
+    for (int r = 0; r < sd.dim_up; ++r) amap.push_back({i, r, 1, 0});
+    v.apply_end = (int)amap.size();
+    v.ew_begin = (int)emap.size();
+    const int64_t ch = ew_chunk(v.D);
+    for (int64_t b = 0; b < v.D; b += ch) emap.push_back({i, 0, b, std::min(v.D, b + ch)});
+    v.ew_end = (int)emap.size();
+    double* base = static_cast<double*>(d_out_.p) + per_vec_out * i;
+    v.out_docc = base;
+    v.out_norm2 = base + (ncap + 1);
+    v.out_energy = base + 2 * (ncap + 1);
+    v.out_delta = base + 3 * (ncap + 1);
+    v.out_meff = reinterpret_cast<int*>(base + 4 * (ncap + 1));
+  }
+  n_apply_ = (int)amap.size();
+  n_ew_ = (int)emap.size();
+  shape_ = apply_shape(max_dim_dn, cfg.fp64, n_groups);
+  ED_TRY(prepare_apply(cfg.fp64, shape_));
+
+  ED_TRY(d_sec_.alloc(sizeof(SectorDev) * sectors_.size()));
+  ED_TRY(d_vec_.alloc(sizeof(VecDev) * nv));
+  ED_TRY(d_st_.alloc(sizeof(LanczosState) * nv));
+  ED_TRY(d_amap_.alloc(sizeof(ApplyBlock) * amap.size()));
+  ED_TRY(d_emap_.alloc(sizeof(EwBlock) * emap.size()));
+  ED_TRY(d_partials_.alloc(sizeof(double) * 4 * std::max(n_apply_, n_ew_)));
+  ED_TRY(d_counters_.alloc(sizeof(unsigned) * nv));
+  ED_TRY(d_coefs_.alloc(esz * (size_t)n_groups * std::max(1, ncap)));
+  if (cfg.energy) ED_TRY(d_coefs_obs_.alloc(esz * (size_t)n_groups * (ncap + 1)));
+  else d_coefs_obs_.release();
+  ED_TRY(cudaMemcpyAsync(d_sec_.p, sectors_.data(), sizeof(SectorDev) * sectors_.size(),
+                         cudaMemcpyHostToDevice, stream));
+  ED_TRY(cudaMemcpyAsync(d_vec_.p, vd.data(), sizeof(VecDev) * nv, cudaMemcpyHostToDevice,
+                         stream));
+  ED_TRY(cudaMemcpyAsync(d_amap_.p, amap.data(), sizeof(ApplyBlock) * amap.size(),
+                         cudaMemcpyHostToDevice, stream));
+  ED_TRY(cudaMemcpyAsync(d_emap_.p, emap.data(), sizeof(EwBlock) * emap.size(),
+                         cudaMemcpyHostToDevice, stream));
+  ED_TRY(cudaMemsetAsync(d_counters_.p, 0, sizeof(unsigned) * nv, stream));
+  ED_TRY(cudaStreamSynchronize(stream));
+
+  std::memset(&args_, 0, sizeof(args_));
+  args_.sec = static_cast<const SectorDev*>(d_sec_.p);
+  args_.vec = static_cast<VecDev*>(d_vec_.p);
+  args_.st = static_cast<LanczosState*>(d_st_.p);
+  args_.apply_map = static_cast<const ApplyBlock*>(d_amap_.p);
+  args_.ew_map = static_cast<const EwBlock*>(d_emap_.p);
+  args_.partials = static_cast<double*>(d_partials_.p);
+  args_.counters = static_cast<unsigned*>(d_counters_.p);
+  args_.coefs = d_coefs_.p;
+  args_.coefs_obs = d_coefs_obs_.p;
+  args_.n_groups = n_groups;
+  args_.nvec = nv;
+  args_.Ns = Ns;
+  args_.max_dim_dn = max_dim_dn;
+  args_.U = U;
+  args_.tau = 0.0;
+  args_.break_tol = break_tol;
+  return "";
+}
+
+std::string Engine::set_overlap_maps(const std::vector<int32_t>& maps,
+                                     const std::vector<int64_t>& off,
+                                     const std::vector<int32_t>& spin, int psi_index,
+                                     cudaStream_t s) {
+  const int nv = (int)vecs_.size();
+  if ((int)off.size() != nv || (int)spin.size() != nv) return "overlap map arrays: bad size";
+  ED_TRY(d_maps_.alloc(std::max<size_t>(1, maps.size()) * sizeof(int32_t)));
+  ED_TRY(d_map_off_.alloc(nv * sizeof(int64_t)));
+  ED_TRY(d_map_spin_.alloc(nv * sizeof(int32_t)));
+  ED_TRY(d_ovl_.alloc((size_t)(cfg_.n_steps_cap + 1) * nv * 2 * sizeof(double)));
+  if (!maps.empty())
+    ED_TRY(cudaMemcpyAsync(d_maps_.p, maps.data(), maps.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+  ED_TRY(cudaMemcpyAsync(d_map_off_.p, off.data(), nv * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  ED_TRY(cudaMemcpyAsync(d_map_spin_.p, spin.data(), nv * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  ED_TRY(cudaMemsetAsync(d_ovl_.p, 0, d_ovl_.bytes, s));
+  ED_TRY(cudaStreamSynchronize(s));
+  oargs_.maps = static_cast<const int32_t*>(d_maps_.p);
+  oargs_.map_off = static_cast<const int64_t*>(d_map_off_.p);
+  oargs_.map_spin = static_cast<const int32_t*>(d_map_spin_.p);
+  oargs_.psi_index = psi_index;
+  oargs_.out = static_cast<double*>(d_ovl_.p);
+  have_overlaps_ = true;
+  if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
+  if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
+  return "";
+}
+
+static std::string upload_coefs(DevMem& dst, const std::vector<double>& c, bool fp64,
+                                cudaStream_t s) {
+  if (c.empty()) return "";
+  if (fp64) {
+    if (c.size() * sizeof(double) > dst.bytes) return "coefficient buffer too small";
+    ED_TRY(cudaMemcpyAsync(dst.p, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  } else {
+    std::vector<float> f(c.size());
+    for (size_t i = 0; i < c.size(); ++i) f[i] = (float)c[i];
+    if (f.size() * sizeof(float) > dst.bytes) return "coefficient buffer too small";
+    ED_TRY(cudaMemcpyAsync(dst.p, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    ED_TRY(cudaStreamSynchronize(s));  // f goes out of scope
+  }
+  return "";
+}
+
+std::string Engine::begin(const std::vector<double>& coefs, const std::vector<double>& coefs_obs,
+                          int n_steps, double tau, cudaStream_t stream) {
+  if (n_steps > cfg_.n_steps_cap) return "n_steps exceeds engine capacity";
+  std::string err = upload_coefs(d_coefs_, coefs, cfg_.fp64, stream);
+  if (!err.empty()) return err;
+  err = upload_coefs(d_coefs_obs_, coefs_obs, cfg_.fp64, stream);
+  if (!err.empty()) return err;
+  std::vector<LanczosState> st(vecs_.size());
+  for (auto& s : st) {
+    std::memset(&s, 0, sizeof(s));
+    s.m = cfg_.m;
+    s.m_eff = cfg_.m;
+    s.scale = 1.0;
+  }
+  ED_TRY(cudaMemcpyAsync(d_st_.p, st.data(), sizeof(LanczosState) * st.size(),
+                         cudaMemcpyHostToDevice, stream));
+  ED_TRY(cudaStreamSynchronize(stream));
+  if (tau != tau_ || args_.tau != tau) {
+    tau_ = tau;
+    args_.tau = tau;
+    if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
+    if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
+  }
+  return "";
+}
+
+std::string Engine::launch_step(cudaStream_t s, bool profile, cudaEvent_t* ev, int* kind_of,
+                                int* nev) {
+  const bool f = cfg_.fp64;
+  auto mark = [&](int kind) -> std::string {
+    if (!profile) return "";
+    ED_TRY(cudaEventRecord(ev[*nev], s));
+    kind_of[*nev] = kind;
+    ++*nev;
+    return "";
+  };
+  std::string err;
+#define STEP_LAUNCH(kind, call)                         \
+  do {                                                  \
+    if (!(err = mark(-1)).empty()) return err;          \
+    ED_TRY(call);                                       \
+    if (!(err = mark(kind)).empty()) return err;        \
+  } while (0)
+  for (int j = 1; j <= cfg_.m; ++j) {
+    STEP_LAUNCH(KK_APPLY, launch_apply(f, args_, n_apply_, shape_, j, s));
+    if (j < cfg_.m) STEP_LAUNCH(KK_UPDATE, launch_update(f, args_, n_ew_, j, s));
+  }
+  STEP_LAUNCH(KK_EXPM, launch_expm(args_, s));
+  STEP_LAUNCH(KK_COMBINE, launch_combine(f, args_, n_ew_, s));
+  if (cfg_.energy) STEP_LAUNCH(KK_ENERGY, launch_apply(f, args_, n_apply_, shape_, -1, s));
+  if (have_overlaps_) STEP_LAUNCH(KK_OVERLAP, launch_overlap(f, args_, oargs_, n_ew_, s));
+#undef STEP_LAUNCH
+  return "";
+}
+
+std::string Engine::capture(cudaStream_t s) {
+  if (exec_) return "";
+  ED_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  std::string err = launch_step(s, false, nullptr, nullptr, nullptr);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (!err.empty()) {
+    if (g) cudaGraphDestroy(g);
+    return err;
+  }
+  if (e != cudaSuccess) return std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+  graph_ = g;
+  ED_TRY(cudaGraphInstantiate(&exec_, graph_, 0));
+  return "";
+}
+
+std::string Engine::run(int n_steps, bool profile, double* kernel_ms, int64_t* launches,
+                        cudaStream_t s) {
+  const bool f = cfg_.fp64;
+  // observables at t_0 (also sets beta0 and the first scale)
+  ED_TRY(launch_observe(f, args_, n_ew_, s));
+  if (have_overlaps_) ED_TRY(launch_overlap(f, args_, oargs_, n_ew_, s));
+  if (cfg_.energy) ED_TRY(launch_apply(f, args_, n_apply_, shape_, -1, s));
+  if (!profile) {
+    std::string err = capture(s);
+    if (!err.empty()) return err;
+    for (int n = 0; n < n_steps; ++n) ED_TRY(cudaGraphLaunch(exec_, s));
+    return "";
+  }
+  const int per_step = 2 * (2 * cfg_.m + 3);
+  std::vector<cudaEvent_t> ev((size_t)per_step * std::max(1, n_steps));
+  std::vector<int> kind(ev.size(), -1);
+  for (auto& e : ev) ED_TRY(cudaEventCreate(&e));
+  int nev = 0;
+  std::string err;
+  for (int n = 0; n < n_steps && err.empty(); ++n)
+    err = launch_step(s, true, ev.data(), kind.data(), &nev);
+  if (err.empty()) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) err = std::string("sync: ") + cudaGetErrorString(e);
+  }
+  if (err.empty()) {
+    for (int k = 0; k < KK_COUNT; ++k) {
+      if (kernel_ms) kernel_ms[k] = 0.0;
+      if (launches) launches[k] = 0;
+    }
+    for (int i = 1; i < nev; i += 2) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      if (kind[i] >= 0) {
+        if (kernel_ms) kernel_ms[kind[i]] += ms;
+        if (launches) launches[kind[i]] += 1;
+      }
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return err;
+}
+
+std::string Engine::fetch(int vec, int n_steps, double* docc, double* norm2, double* energy,
+                          double* delta, int32_t* meff, int* status, cudaStream_t s) {
+  VecDev v;
+  ED_TRY(cudaMemcpyAsync(&v, static_cast<VecDev*>(d_vec_.p) + vec, sizeof(VecDev),
+                         cudaMemcpyDeviceToHost, s));
+  LanczosState st;
+  ED_TRY(cudaMemcpyAsync(&st, static_cast<LanczosState*>(d_st_.p) + vec, sizeof(st),
+                         cudaMemcpyDeviceToHost, s));
+  ED_TRY(cudaStreamSynchronize(s));
+  const size_t nb = (size_t)(n_steps + 1) * sizeof(double);
+  if (docc) ED_TRY(cudaMemcpyAsync(docc, v.out_docc, nb, cudaMemcpyDeviceToHost, s));
+  if (norm2) ED_TRY(cudaMemcpyAsync(norm2, v.out_norm2, nb, cudaMemcpyDeviceToHost, s));
+  if (energy) ED_TRY(cudaMemcpyAsync(energy, v.out_energy, nb, cudaMemcpyDeviceToHost, s));
+  if (delta && n_steps > 0)
+    ED_TRY(cudaMemcpyAsync(delta, v.out_delta, n_steps * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (meff && n_steps > 0)
+    ED_TRY(cudaMemcpyAsync(meff, v.out_meff, n_steps * sizeof(int), cudaMemcpyDeviceToHost, s));
+  ED_TRY(cudaStreamSynchronize(s));
+  if (status) *status = st.status;
+  return "";
+}
+
+std::string Engine::fetch_overlaps(int n_steps, std::vector<double>& out, cudaStream_t s) {
+  out.assign((size_t)(n_steps + 1) * vecs_.size() * 2, 0.0);
+  if (!have_overlaps_) return "no overlaps configured";
+  ED_TRY(cudaMemcpyAsync(out.data(), d_ovl_.p, out.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost, s));
+  ED_TRY(cudaStreamSynchronize(s));
+  return "";
+}
+
+}  // namespace ed

@@ -1,0 +1,86 @@
+// Batched propagation engine: owns the device workspace of one or more
+// vectors propagated together by the exponential midpoint rule, and the CUDA
+// graph of one time step.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "kernels.cuh"
+
+namespace ed {
+
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t alloc(size_t n);
+  void release();
+  ~DevMem() { release(); }
+};
+
+struct EngineVector {
+  int sector;      // index into the engine's sector list
+  int64_t D;
+  void* x1;        // device pointer of the state (external or owned)
+  bool owned_x1;
+};
+
+struct EngineConfig {
+  bool fp64 = false;
+  int m = 1;
+  bool energy = false;
+  bool overlaps = false;
+  int n_steps_cap = 0;
+};
+
+class Engine {
+ public:
+  ~Engine();
+  // Allocate everything; sectors must stay alive while the engine exists.
+  std::string setup(const EngineConfig& cfg, const std::vector<SectorDev>& sectors,
+                    const std::vector<EngineVector>& vecs, int n_groups, int Ns,
+                    double U, double break_tol, cudaStream_t stream);
+  bool compatible(const EngineConfig& cfg, const std::vector<EngineVector>& vecs) const;
+  // Upload per-step coefficients ([n_steps][n_groups] complex double; energy
+  // coefficients [n_steps+1][n_groups] or empty) and reset the Lanczos state.
+  std::string begin(const std::vector<double>& coefs, const std::vector<double>& coefs_obs,
+                    int n_steps, double tau, cudaStream_t stream);
+  // Observables at t_0, then n_steps steps (graph replays or profiled launches).
+  std::string run(int n_steps, bool profile, double* kernel_ms, int64_t* launches,
+                  cudaStream_t stream);
+  // Copy per-vector outputs of the last run to host (synchronises stream).
+  std::string fetch(int vec, int n_steps, double* docc, double* norm2, double* energy,
+                    double* delta, int32_t* meff, int* status, cudaStream_t stream);
+  std::string fetch_overlaps(int n_steps, std::vector<double>& out, cudaStream_t stream);
+  // Green's-function overlaps after every step (and at t_0): vector b with
+  // off[b] >= 0 is overlapped with the image of vector psi_index under its map.
+  std::string set_overlap_maps(const std::vector<int32_t>& maps, const std::vector<int64_t>& off,
+                               const std::vector<int32_t>& spin, int psi_index, cudaStream_t s);
+  size_t device_bytes() const;
+  void* vec_x1(int v) const { return vecs_[v].x1; }
+  int nvec() const { return (int)vecs_.size(); }
+
+ private:
+  std::string launch_step(cudaStream_t s, bool profile, cudaEvent_t* ev, int* kind_of,
+                          int* nev);
+  std::string capture(cudaStream_t s);
+
+  EngineConfig cfg_;
+  std::vector<EngineVector> vecs_;
+  std::vector<SectorDev> sectors_;
+  int n_groups_ = 0, Ns_ = 0;
+  double U_ = 0.0, break_tol_ = 0.0, tau_ = 0.0;
+  int n_apply_ = 0, n_ew_ = 0;
+  LaunchShape shape_{};
+  BatchArgs args_{};
+  OverlapArgs oargs_{};
+  bool have_overlaps_ = false;
+  DevMem d_sec_, d_vec_, d_st_, d_amap_, d_emap_, d_partials_, d_counters_;
+  DevMem d_coefs_, d_coefs_obs_, d_V_, d_w_, d_out_, d_owned_x1_;
+  DevMem d_maps_, d_map_off_, d_map_spin_, d_ovl_;
+  cudaGraph_t graph_ = nullptr;
+  cudaGraphExec_t exec_ = nullptr;
+};
+
+}  // namespace ed

@@ -1,0 +1,949 @@
+// Batched Hubbard-apply and Lanczos kernels for sm_103a.
+//
+// Psi of a sector is a dim_up x dim_dn row-major matrix.  H acts as
+//   W[u,d] = sum_{(u',g,s) in C_up(u)} s c_g Psi[u',d]      (T_up: across rows)
+//          + sum_{(d',g,s) in C_dn(d)} s c_g Psi[u,d']      (T_dn: within a row)
+//          + (U popcount(up[u] & dn[d]) + eps_up[u] + eps_dn[d]) Psi[u,d]
+// (Eq. (1) with the Peierls phases of Eq. (3); c_g the per-step coefficient of
+// bond class g/2 in orientation g%2).  One CTA processes one row u: the row
+// Psi[u,:] is staged in shared memory for T_dn, the T_up gathers read whole
+// rows Psi[u',:] with coalesced loads along d, and the signed values of one
+// bond group are summed before a single complex multiply by c_g.
+//
+// The Lanczos recursion (Algorithm 6) is split into two passes per step j:
+//   apply :  w = s_j H x_j - beta_{j-1} s_{j-1} x_{j-1},  alpha_j = Re<v_j, w>
+//   update:  x_{j+1} = w - alpha_j s_j x_j,  beta_j = |x_{j+1}|,
+//            s_{j+1} = 1 / beta_j   (normalisation is applied lazily)
+// Reductions are deterministic: per-block partial sums in float64, then the
+// last block of each vector sums the partials in block order.
+#include "kernels.cuh"
+
+#include <cstdio>
+
+namespace ed {
+
+// ---------------------------------------------------------------- utilities
+template <typename R> struct C2T;
+template <> struct C2T<float> { using T = float2; };
+template <> struct C2T<double> { using T = double2; };
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+template <typename R> __device__ __forceinline__ typename C2T<R>::T
+load_coef(const void* p, int idx) {
+  return reinterpret_cast<const typename C2T<R>::T*>(p)[idx];
+}
+
+// Block reduction of K doubles; the result is valid in thread 0.
+template <int K>
+__device__ __forceinline__ void block_reduce(double (&v)[K], double* red) {
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(full, v[k], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[wid * K + k] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      v[k] = lane < nw ? red[lane * K + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(full, v[k], o);
+    }
+  }
+}
+
+// Write this block's partials; the last block of [b0, b1) sums all partials
+// in block order.  Returns true in every thread of the last block; the totals
+// are valid in thread 0.
+template <int K>
+__device__ __forceinline__ bool reduce_last_block(double (&v)[K], int blk, int b0,
+                                                  int b1, double* partials,
+                                                  unsigned* counter,
+                                                  double* red, int* flag) {
+  block_reduce<K>(v, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)blk * K + k] = v[k];
+    __threadfence();
+    unsigned ticket = atomicAdd(counter, 1u);
+    *flag = (ticket == (unsigned)(b1 - b0 - 1));
+  }
+  __syncthreads();
+  if (!*flag) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += __ldcg(&partials[(size_t)b * K + k]);
+  block_reduce<K>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = acc[k];
+    *counter = 0u;
+  }
+  return true;
+}
+
+__device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz) {
+  // x_1 is the state, x_j (j >= 2) is V slot j-2
+  return j == 1 ? vd.x1
+                : static_cast<const char*>(vd.V) + (size_t)(j - 2) * vd.D * esz;
+}
+
+// ------------------------------------------------------------------- apply
+// j >= 1: Lanczos pass j; j == 0: plain apply (coefs row 0, x1 -> w);
+// j == -1: energy of x1 with coefs_obs[step].
+template <int EPT> struct ApplyBound { static constexpr int v = EPT >= 16 ? 256 : (EPT >= 8 ? 512 : 1024); };
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(ApplyBound<EPT>::v)
+k_apply(BatchArgs a, int j) {
+  using C = typename C2T<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32 * 2];
+  __shared__ int flag;
+
+  const ApplyBlock ab = a.apply_map[blockIdx.x];
+  const VecDev vd = a.vec[ab.vec];
+  LanczosState* st = a.st + ab.vec;
+  if (j >= 1 && st->stopped) return;   // uniform over the vector's blocks
+  const SectorDev sd = a.sec[vd.sector];
+  const int dim_dn = sd.dim_dn;
+
+  C* row = reinterpret_cast<C*>(smem_raw);
+  C* coef = row + a.max_dim_dn;
+
+  // coefficients of this step (or of the observation time / static field)
+  const void* cbase;
+  if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
+  else if (j == 0) cbase = a.coefs;
+  else cbase = static_cast<const char*>(a.coefs_obs) + (size_t)st->step * a.n_groups * sizeof(C);
+  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
+    coef[g] = reinterpret_cast<const C*>(cbase)[g];
+
+  const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
+  const C* xp = (j >= 2) ? static_cast<const C*>(xptr(vd, j - 1, sizeof(C))) : nullptr;
+  C* w = static_cast<C*>(vd.w);
+  const R s_in = (j >= 1) ? (R)st->inv_scale[j] : (R)1;
+  const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
+  const R U = (R)a.U;
+  const int chunk = blockDim.x * EPT;
+
+  double dot_d = 0.0;   // Re<x, w>: per-row partials in R, accumulated in double
+
+  for (int r = 0; r < ab.nrows; ++r) {
+    const int u = ab.row0 + r;
+    const C* xrow = x + (size_t)u * dim_dn;
+    __syncthreads();
+    for (int d = threadIdx.x; d < dim_dn; d += blockDim.x) row[d] = xrow[d];
+    __syncthreads();
+    const uint32_t uw = __ldg(sd.up_word + u);
+    const R eu = sd.up_eps ? (R)__ldg(sd.up_eps + u) : (R)0;
+    const int e0 = __ldg(sd.up_off + u), e1 = __ldg(sd.up_off + u + 1);
+    C* wrow = w + (size_t)u * dim_dn;
+    const C* xprow = xp ? xp + (size_t)u * dim_dn : nullptr;
+
+    for (int c0 = 0; c0 < dim_dn; c0 += chunk) {
+      C acc[EPT];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int d = c0 + threadIdx.x + k * blockDim.x;
+        acc[k] = czero<C>();
+        if (d < dim_dn) {
+          // diagonal: U * #doubles (+ on-site energies)
+          R dg = U * (R)__popc(uw & __ldg(sd.dn_word + d)) + eu;
+          if (sd.dn_eps) dg += (R)__ldg(sd.dn_eps + d);
+          const C xv = row[d];
+          C a2;
+          a2.x = dg * xv.x;
+          a2.y = dg * xv.y;
+          // T_dn: gathers within the staged row
+          const int f0 = __ldg(sd.dn_off + d), f1 = __ldg(sd.dn_off + d + 1);
+          for (int f = f0; f < f1; ++f) {
+            const uint32_t ent = __ldg(sd.dn_ent + f);
+            const C v = row[ent & kEntRankMask];
+            C c = coef[(ent >> kEntGroupShift) & 0xFFu];
+            if (ent & kEntSignBit) { c.x = -c.x; c.y = -c.y; }
+            a2.x += c.x * v.x - c.y * v.y;
+            a2.y += c.x * v.y + c.y * v.x;
+          }
+          acc[k] = a2;
+        }
+      }
+      // T_up: the entry list of row u is uniform across the block; entries
+      // are sorted by group, signed values of one group are summed first.
+      int e = e0;
+      while (e < e1) {
+        uint32_t ent = __ldg(sd.up_ent + e);
+        const uint32_t g = (ent >> kEntGroupShift) & 0xFFu;
+        C sum[EPT];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) sum[k] = czero<C>();
+        while (true) {
+          const C* src = x + (size_t)(ent & kEntRankMask) * dim_dn;
+          if (ent & kEntSignBit) {
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+              const int d = c0 + threadIdx.x + k * blockDim.x;
+              if (d < dim_dn) { const C v = src[d]; sum[k].x -= v.x; sum[k].y -= v.y; }
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+              const int d = c0 + threadIdx.x + k * blockDim.x;
+              if (d < dim_dn) { const C v = src[d]; sum[k].x += v.x; sum[k].y += v.y; }
+            }
+          }
+          ++e;
+          if (e >= e1) break;
+          ent = __ldg(sd.up_ent + e);
+          if (((ent >> kEntGroupShift) & 0xFFu) != g) break;
+        }
+        const C c = coef[g];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          acc[k].x += c.x * sum[k].x - c.y * sum[k].y;
+          acc[k].y += c.x * sum[k].y + c.y * sum[k].x;
+        }
+      }
+      // epilogue: scale, three-term subtraction, store, inner product
+      R dot_acc = (R)0;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int d = c0 + threadIdx.x + k * blockDim.x;
+        if (d < dim_dn) {
+          C o;
+          o.x = s_in * acc[k].x;
+          o.y = s_in * acc[k].y;
+          if (xprow) {
+            const C pv = xprow[d];
+            o.x -= s_prev * pv.x;
+            o.y -= s_prev * pv.y;
+          }
+          wrow[d] = o;
+          const C xv = row[d];
+          dot_acc += xv.x * o.x + xv.y * o.y;
+        }
+      }
+      dot_d += (double)dot_acc;
+    }
+  }
+  if (j == 0) return;
+  double v[1] = {dot_d};
+  if (reduce_last_block<1>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
+                           a.partials, a.counters + ab.vec, red, &flag)) {
+    if (threadIdx.x == 0) {
+      if (j >= 1) {
+        st->alpha[j] = v[0] * st->inv_scale[j];
+        if (!isfinite(v[0])) { st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1; }
+      } else {
+        if (vd.out_energy) vd.out_energy[st->step] = v[0] / a.Ns;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ update
+// x_{j+1} = w - alpha_j s_j x_j ;  beta_j = |x_{j+1}| ;  breakdown test.
+template <typename R>
+__global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
+  using C = typename C2T<R>::T;
+  __shared__ double red[32];
+  __shared__ int flag;
+  const EwBlock eb = a.ew_map[blockIdx.x];
+  const VecDev vd = a.vec[eb.vec];
+  LanczosState* st = a.st + eb.vec;
+  if (st->stopped) return;
+  const C* w = static_cast<const C*>(vd.w);
+  const C* x = static_cast<const C*>(xptr(vd, j, sizeof(C)));
+  C* xn = static_cast<C*>(const_cast<void*>(xptr(vd, j + 1, sizeof(C))));
+  const R as = (R)(st->alpha[j] * st->inv_scale[j]);
+  double nrm_d = 0.0;
+  R nrm = (R)0;
+  int cnt = 0;
+  for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
+    const C wv = w[i], xv = x[i];
+    C o;
+    o.x = wv.x - as * xv.x;
+    o.y = wv.y - as * xv.y;
+    xn[i] = o;
+    nrm += o.x * o.x + o.y * o.y;
+    if (++cnt == 8) { nrm_d += (double)nrm; nrm = (R)0; cnt = 0; }
+  }
+  double v[1] = {nrm_d + (double)nrm};
+  if (reduce_last_block<1>(v, blockIdx.x, vd.ew_begin, vd.ew_end, a.partials,
+                           a.counters + eb.vec, red, &flag)) {
+    if (threadIdx.x == 0) {
+      const double beta = sqrt(v[0]);
+      const double sc = fmax(st->scale, fabs(st->alpha[j]));
+      st->beta[j] = beta;
+      if (!isfinite(beta)) {
+        st->status = 7; st->stopped = 1; st->m_eff = j;
+      } else if (beta <= a.break_tol * sc) {
+        st->stopped = 1; st->m_eff = j;
+      } else {
+        st->inv_scale[j + 1] = 1.0 / beta;
+        st->scale = fmax(sc, beta);
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------------------- expm
+// exp(-i tau T) e_1 for the real symmetric tridiagonal T of size n <= 64,
+// one warp.  T is shifted by the centre sigma of its Gershgorin interval,
+// the time step is split into nsub pieces with tau*halfwidth/nsub <= 1/2, and
+// each piece is a Taylor series summed until the next term is below 1e-17 of
+// the sum (the truncation error is then below rounding).  Lane l owns rows l
+// and l + 32.
+__device__ void tridiag_expm_e1(const double* al, const double* be, int n,
+                                double tau, double* yre, double* yim,
+                                double* tre, double* tim) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  double lo = 1e300, hi = -1e300;
+  for (int i = lane; i < n; i += 32) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < n - 1 ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, al[i] - r);
+    hi = fmax(hi, al[i] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(full, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(full, hi, o));
+  }
+  const double sigma = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+  int nsub = (int)ceil(fabs(tau) * half / 0.5);
+  if (nsub < 1) nsub = 1;
+  if (nsub > 4096) nsub = 4096;
+  const double ts = tau / nsub;
+  for (int i = lane; i < 64; i += 32) {
+    yre[i] = (i == 0) ? 1.0 : 0.0;
+    yim[i] = 0.0;
+  }
+  __syncwarp();
+  for (int sub = 0; sub < nsub; ++sub) {
+    for (int i = lane; i < 64; i += 32) { tre[i] = yre[i]; tim[i] = yim[i]; }
+    __syncwarp();
+    for (int k = 1; k <= 80; ++k) {
+      double nre[2] = {0.0, 0.0}, nim[2] = {0.0, 0.0};
+      double tn = 0.0, an = 0.0;
+      const double f = ts / k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i < n) {
+          double qr = (al[i] - sigma) * tre[i];
+          double qi = (al[i] - sigma) * tim[i];
+          if (i > 0) { qr += be[i - 1] * tre[i - 1]; qi += be[i - 1] * tim[i - 1]; }
+          if (i < n - 1) { qr += be[i] * tre[i + 1]; qi += be[i] * tim[i + 1]; }
+          // (-i f) (qr + i qi) = f qi - i f qr
+          nre[h] = f * qi;
+          nim[h] = -f * qr;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i < n) {
+          tre[i] = nre[h]; tim[i] = nim[h];
+          yre[i] += nre[h]; yim[i] += nim[h];
+          tn += nre[h] * nre[h] + nim[h] * nim[h];
+          an += yre[i] * yre[i] + yim[i] * yim[i];
+        }
+      }
+      __syncwarp();
+      for (int o = 16; o > 0; o >>= 1) {
+        tn += __shfl_xor_sync(full, tn, o);
+        an += __shfl_xor_sync(full, an, o);
+      }
+      if (tn <= 1e-34 * an) break;
+    }
+    __syncwarp();
+  }
+  // undo the shift: multiply by exp(-i tau sigma)
+  double sn, cs;
+  sincos(-tau * sigma, &sn, &cs);
+  for (int i = lane; i < n; i += 32) {
+    const double r = yre[i], im = yim[i];
+    yre[i] = r * cs - im * sn;
+    yim[i] = r * sn + im * cs;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) k_expm(BatchArgs a) {
+  __shared__ double al[64], be[64], yre[64], yim[64], pre[64], pim[64];
+  __shared__ double tre[64], tim[64];
+  const int b = blockIdx.x;
+  LanczosState* st = a.st + b;
+  const VecDev vd = a.vec[b];
+  const int lane = threadIdx.x;
+  const int n = st->m_eff;
+  for (int i = lane; i < 64; i += 32) {
+    al[i] = i < n ? st->alpha[i + 1] : 0.0;
+    be[i] = i < n - 1 ? st->beta[i + 1] : 0.0;
+  }
+  __syncwarp();
+  tridiag_expm_e1(al, be, n, a.tau, yre, yim, tre, tim);
+  double delta = 0.0;
+  if (n > 1) {
+    tridiag_expm_e1(al, be, n - 1, a.tau, pre, pim, tre, tim);
+    double dn = 0.0, yn = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double pr = i < n - 1 ? pre[i] : 0.0, pi = i < n - 1 ? pim[i] : 0.0;
+      dn += (yre[i] - pr) * (yre[i] - pr) + (yim[i] - pi) * (yim[i] - pi);
+      yn += yre[i] * yre[i] + yim[i] * yim[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dn += __shfl_xor_sync(0xffffffffu, dn, o);
+      yn += __shfl_xor_sync(0xffffffffu, yn, o);
+    }
+    delta = sqrt(dn / yn);
+  }
+  for (int i = lane; i < n; i += 32) {
+    const double f = st->beta0 * st->inv_scale[i + 1];
+    st->comb_re[i + 1] = f * yre[i];
+    st->comb_im[i + 1] = f * yim[i];
+  }
+  if (lane == 0) {
+    st->delta = delta;
+    if (vd.out_delta) vd.out_delta[st->step] = delta;
+    if (vd.out_meff) vd.out_meff[st->step] = n;
+  }
+}
+
+// ------------------------------------------------------ combine / observe
+// psi <- sum_j comb_j x_j (in place over x_1), fused with |psi|^2 and
+// sum_k w_d[k] |psi_k|^2 (Sec. 3.5), then the per-step bookkeeping.
+template <typename R, bool COMBINE>
+__global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
+  using C = typename C2T<R>::T;
+  __shared__ double red[64];
+  __shared__ int flag;
+  __shared__ C cf[kMaxKrylov + 1];
+  const EwBlock eb = a.ew_map[blockIdx.x];
+  const VecDev vd = a.vec[eb.vec];
+  LanczosState* st = a.st + eb.vec;
+  const SectorDev sd = a.sec[vd.sector];
+  const int n = COMBINE ? st->m_eff : 1;
+  if (COMBINE) {
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
+      cf[jj].x = (R)st->comb_re[jj + 1];
+      cf[jj].y = (R)st->comb_im[jj + 1];
+    }
+    __syncthreads();
+  }
+  C* x1 = static_cast<C*>(vd.x1);
+  const C* V = static_cast<const C*>(vd.V);
+  const int dim_dn = sd.dim_dn;
+  double nd = 0.0, wd = 0.0;
+  R nl = (R)0, wl = (R)0;
+  int cnt = 0;
+  for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
+    C p;
+    if (COMBINE) {
+      const C x = x1[i];
+      p.x = cf[0].x * x.x - cf[0].y * x.y;
+      p.y = cf[0].x * x.y + cf[0].y * x.x;
+      for (int jj = 1; jj < n; ++jj) {
+        const C v = V[(size_t)(jj - 1) * vd.D + i];
+        const C c = cf[jj];
+        p.x += c.x * v.x - c.y * v.y;
+        p.y += c.x * v.y + c.y * v.x;
+      }
+      x1[i] = p;
+    } else {
+      p = x1[i];
+    }
+    const int u = (int)(i / dim_dn);
+    const int d = (int)(i - (int64_t)u * dim_dn);
+    const R q = p.x * p.x + p.y * p.y;
+    nl += q;
+    wl += (R)__popc(__ldg(sd.up_word + u) & __ldg(sd.dn_word + d)) * q;
+    if (++cnt == 8) { nd += (double)nl; wd += (double)wl; nl = wl = (R)0; cnt = 0; }
+  }
+  double v[2] = {nd + (double)nl, wd + (double)wl};
+  if (reduce_last_block<2>(v, blockIdx.x, vd.ew_begin, vd.ew_end, a.partials,
+                           a.counters + eb.vec, red, &flag)) {
+    if (threadIdx.x == 0) {
+      const double norm2 = v[0];
+      const int slot = COMBINE ? st->step + 1 : st->step;
+      if (vd.out_docc) vd.out_docc[slot] = v[1] / a.Ns;
+      if (vd.out_norm2) vd.out_norm2[slot] = norm2;
+      const double b0 = sqrt(norm2);
+      if (!isfinite(b0)) st->status = 7;
+      st->beta0 = b0;
+      st->inv_scale[1] = b0 > 0.0 ? 1.0 / b0 : 0.0;
+      st->scale = 1.0;
+      st->m_eff = st->m;
+      st->stopped = b0 > 0.0 && isfinite(b0) ? 0 : 1;
+      if (COMBINE) st->step = st->step + 1;
+    }
+  }
+}
+
+// -------------------------------------------------------- fermion operator
+template <typename R>
+__global__ void k_fermion_op(const typename C2T<R>::T* in,
+                             typename C2T<R>::T* out, int dim_dn_src,
+                             int dim_up_dst, int dim_dn_dst, int spin,
+                             const int32_t* map) {
+  using C = typename C2T<R>::T;
+  const int64_t n = (int64_t)dim_up_dst * dim_dn_dst;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int u = (int)(t / dim_dn_dst);
+    const int d = (int)(t - (int64_t)u * dim_dn_dst);
+    const int32_t m = __ldg(map + (spin == 0 ? u : d));
+    C o = czero<C>();
+    if (m != 0x7FFFFFFF) {
+      const int src = m & 0x7FFFFFFF;
+      const C v = spin == 0 ? in[(int64_t)src * dim_dn_src + d]
+                            : in[(int64_t)u * dim_dn_src + src];
+      o = (m < 0) ? C{-v.x, -v.y} : v;
+    }
+    out[t] = o;
+  }
+}
+
+// ---------------------------------------------------------------- overlaps
+// <op psi | phi_b> = sum_t conj(sign(t) psi[src(t)]) phi_b[t]
+template <typename R>
+__global__ void __launch_bounds__(256) k_overlap(BatchArgs a, OverlapArgs o) {
+  using C = typename C2T<R>::T;
+  __shared__ double red[64];
+  __shared__ int flag;
+  const EwBlock eb = a.ew_map[blockIdx.x];
+  const int64_t moff = o.map_off[eb.vec];
+  if (moff < 0) return;
+  const VecDev vd = a.vec[eb.vec];
+  const VecDev vp = a.vec[o.psi_index];
+  const SectorDev sd = a.sec[vd.sector];
+  const SectorDev sp = a.sec[vp.sector];
+  const int spin = o.map_spin[eb.vec];
+  const int32_t* map = o.maps + moff;
+  const C* phi = static_cast<const C*>(vd.x1);
+  const C* psi = static_cast<const C*>(vp.x1);
+  const int dim_dn = sd.dim_dn, dim_dn_src = sp.dim_dn;
+  double ar = 0.0, ai = 0.0;
+  for (int64_t t = eb.begin + threadIdx.x; t < eb.end; t += blockDim.x) {
+    const int u = (int)(t / dim_dn);
+    const int d = (int)(t - (int64_t)u * dim_dn);
+    const int32_t m = __ldg(map + (spin == 0 ? u : d));
+    if (m == 0x7FFFFFFF) continue;
+    const int src = m & 0x7FFFFFFF;
+    const C p = spin == 0 ? psi[(int64_t)src * dim_dn_src + d]
+                          : psi[(int64_t)u * dim_dn_src + src];
+    const C f = phi[t];
+    // conj(s p) f, s = +-1
+    double re = (double)p.x * f.x + (double)p.y * f.y;
+    double im = (double)p.x * f.y - (double)p.y * f.x;
+    if (m < 0) { re = -re; im = -im; }
+    ar += re;
+    ai += im;
+  }
+  double v[2] = {ar, ai};
+  if (reduce_last_block<2>(v, blockIdx.x, vd.ew_begin, vd.ew_end, a.partials,
+                           a.counters + eb.vec, red, &flag)) {
+    if (threadIdx.x == 0) {
+      const int step = a.st[o.psi_index].step;
+      double* out = o.out + ((size_t)step * a.nvec + eb.vec) * 2;
+      out[0] = v[0];
+      out[1] = v[1];
+    }
+  }
+}
+
+// ------------------------------------------------------ ground-state helpers
+__global__ void __launch_bounds__(256)
+k_multidot(const double2* V, int64_t ldV, int k, const double2* w, int64_t D,
+           double2* partial) {
+  // block b handles chunk [b*chunk, (b+1)*chunk); partial[b*k + i]
+  extern __shared__ double2 sacc[];  // [blockDim/32][k]
+  const int64_t chunk = (D + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(D, i0 + chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = 0; i < k; ++i) {
+    double re = 0.0, im = 0.0;
+    const double2* Vi = V + (size_t)i * ldV;
+    for (int64_t t = i0 + threadIdx.x; t < i1; t += blockDim.x) {
+      const double2 a = Vi[t], b = w[t];
+      re += a.x * b.x + a.y * b.y;
+      im += a.x * b.y - a.y * b.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) sacc[wid * k + i] = make_double2(re, im);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < nw; ++q) { re += sacc[q * k + i].x; im += sacc[q * k + i].y; }
+    partial[(size_t)blockIdx.x * k + i] = make_double2(re, im);
+  }
+}
+
+__global__ void k_reduce_cols(const double2* partial, int nblk, int k, double2* out) {
+  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < k; i += blockDim.x * gridDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < nblk; ++b) { re += partial[(size_t)b * k + i].x; im += partial[(size_t)b * k + i].y; }
+    out[i] = make_double2(re, im);
+  }
+}
+
+__global__ void k_multiaxpy(const double2* V, int64_t ldV, int k, const double2* c,
+                            double2* w, int64_t D) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < D;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double2 acc = w[t];
+    for (int i = 0; i < k; ++i) {
+      const double2 v = V[(size_t)i * ldV + t], ci = c[i];
+      acc.x -= ci.x * v.x - ci.y * v.y;
+      acc.y -= ci.x * v.y + ci.y * v.x;
+    }
+    w[t] = acc;
+  }
+}
+
+__global__ void k_combine_real(const double2* V, int64_t ldV, int k, const double* c,
+                               double2* y, int64_t D) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < D;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < k; ++i) {
+      const double2 v = V[(size_t)i * ldV + t];
+      acc.x += c[i] * v.x;
+      acc.y += c[i] * v.y;
+    }
+    y[t] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_norm_dot_partial(const double2* x, const double2* y, int64_t D, double* partial) {
+  __shared__ double red[64];
+  const int64_t chunk = (D + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(D, i0 + chunk);
+  double v[2] = {0.0, 0.0};
+  for (int64_t t = i0 + threadIdx.x; t < i1; t += blockDim.x) {
+    const double2 a = x[t];
+    v[0] += a.x * a.x + a.y * a.y;
+    if (y) { const double2 b = y[t]; v[1] += a.x * b.x + a.y * b.y; }
+  }
+  block_reduce<2>(v, red);
+  if (threadIdx.x == 0) { partial[2 * blockIdx.x] = v[0]; partial[2 * blockIdx.x + 1] = v[1]; }
+}
+
+__global__ void __launch_bounds__(256) k_sum_pairs(const double* partial, int nblk, double* out) {
+  __shared__ double red[64];
+  double v[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { v[0] += partial[2 * b]; v[1] += partial[2 * b + 1]; }
+  block_reduce<2>(v, red);
+  if (threadIdx.x == 0) { out[0] = v[0]; out[1] = v[1]; }
+}
+
+__global__ void k_scale(double2* x, int64_t D, const double* s_dev, int inv_sqrt) {
+  const double s = inv_sqrt ? 1.0 / sqrt(*s_dev) : *s_dev;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < D;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    x[t].x *= s;
+    x[t].y *= s;
+  }
+}
+
+__global__ void k_axpy_real(double2* y, const double2* x, int64_t D, const double* a_dev,
+                            double a_sign) {
+  const double a = a_sign * (*a_dev);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < D;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    y[t].x += a * x[t].x;
+    y[t].y += a * x[t].y;
+  }
+}
+
+// splitmix64 (Steele, Lea, Flood 2014) of (seed, index) -> two uniforms in
+// (-1, 1) per element; the start vector only needs to overlap the ground state.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void k_random_fill(double2* x, int64_t D, uint64_t seed) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < D;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t r1 = splitmix64(seed ^ splitmix64(2 * (uint64_t)t));
+    const uint64_t r2 = splitmix64(seed ^ splitmix64(2 * (uint64_t)t + 1));
+    x[t].x = ((double)(r1 >> 11) * 0x1.0p-53) * 2.0 - 1.0;
+    x[t].y = ((double)(r2 >> 11) * 0x1.0p-53) * 2.0 - 1.0;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_docc_sites(const typename C2T<R>::T* psi, SectorDev sd, int Ns, double* partial) {
+  __shared__ double red[32 * (kMaxSites + 1)];
+  const int64_t D = (int64_t)sd.dim_up * sd.dim_dn;
+  const int64_t chunk = (D + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(D, i0 + chunk);
+  double v[kMaxSites + 1];
+#pragma unroll
+  for (int i = 0; i <= kMaxSites; ++i) v[i] = 0.0;
+  for (int64_t t = i0 + threadIdx.x; t < i1; t += blockDim.x) {
+    const int u = (int)(t / sd.dim_dn);
+    const int d = (int)(t - (int64_t)u * sd.dim_dn);
+    const auto p = psi[t];
+    const double q = (double)p.x * p.x + (double)p.y * p.y;
+    const uint32_t both = sd.up_word[u] & sd.dn_word[d];
+    v[0] += __popc(both) * q;
+#pragma unroll
+    for (int i = 0; i < kMaxSites; ++i)
+      if ((both >> i) & 1u) v[1 + i] += q;
+  }
+  block_reduce<kMaxSites + 1>(v, red);
+  if (threadIdx.x == 0)
+    for (int i = 0; i <= kMaxSites; ++i) partial[(size_t)blockIdx.x * (kMaxSites + 1) + i] = v[i];
+}
+
+__global__ void k_sum_sites(const double* partial, int nblk, int K, double* out) {
+  const int i = threadIdx.x;
+  if (i >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * K + i];
+  out[i] = s;
+}
+
+__global__ void k_convert_c128_c64(const double2* in, float2* out, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = make_float2((float)in[t].x, (float)in[t].y);
+}
+__global__ void k_convert_c64_c128(const float2* in, double2* out, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = make_double2((double)in[t].x, (double)in[t].y);
+}
+
+// ---------------------------------------------------------------- launchers
+static int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  const int64_t cap = 152 * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
+  // elements per thread: 16 (float) / 8 (double) for long rows, fewer for
+  // short rows; the block covers the row in chunks of threads * ept columns.
+  int ept = fp64 ? 8 : 16;
+  while (ept > 1 && (max_dim_dn + ept - 1) / ept < 32) ept /= 2;
+  const int bound = ept >= 16 ? 256 : (ept >= 8 ? 512 : 1024);
+  int threads = (max_dim_dn + ept - 1) / ept;
+  threads = ((threads + 31) / 32) * 32;
+  if (threads < 32) threads = 32;
+  if (threads > bound) threads = bound;
+  LaunchShape sh;
+  sh.threads = threads;
+  sh.ept = ept;
+  const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
+  sh.smem = (size_t)(max_dim_dn + n_groups) * csz;
+  return sh;
+}
+
+template <typename R, int EPT>
+static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
+                                  int j, cudaStream_t s) {
+  k_apply<R, EPT><<<nblk, sh.threads, sh.smem, s>>>(a, j);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t prepare_apply_r(const LaunchShape& sh) {
+  cudaError_t e = cudaSuccess;
+  const int sm = (int)sh.smem;
+  switch (sh.ept) {
+    case 1: e = cudaFuncSetAttribute(k_apply<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+    case 2: e = cudaFuncSetAttribute(k_apply<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+    case 4: e = cudaFuncSetAttribute(k_apply<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+    case 8: e = cudaFuncSetAttribute(k_apply<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+    case 16: e = cudaFuncSetAttribute(k_apply<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  return e;
+}
+
+cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
+  if (sh.smem > 227 * 1024) return cudaErrorInvalidValue;
+  return fp64 ? prepare_apply_r<double>(sh) : prepare_apply_r<float>(sh);
+}
+
+template <typename R>
+static cudaError_t launch_apply_r(const BatchArgs& a, int nblk, const LaunchShape& sh,
+                                  int j, cudaStream_t s) {
+  switch (sh.ept) {
+    case 1: return launch_apply_t<R, 1>(a, nblk, sh, j, s);
+    case 2: return launch_apply_t<R, 2>(a, nblk, sh, j, s);
+    case 4: return launch_apply_t<R, 4>(a, nblk, sh, j, s);
+    case 8: return launch_apply_t<R, 8>(a, nblk, sh, j, s);
+    case 16: return launch_apply_t<R, 16>(a, nblk, sh, j, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
+                         int j, cudaStream_t s) {
+  return fp64 ? launch_apply_r<double>(a, nblk, sh, j, s)
+              : launch_apply_r<float>(a, nblk, sh, j, s);
+}
+
+cudaError_t launch_update(bool fp64, const BatchArgs& a, int nblk, int j, cudaStream_t s) {
+  if (fp64) k_update<double><<<nblk, 256, 0, s>>>(a, j);
+  else k_update<float><<<nblk, 256, 0, s>>>(a, j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s) {
+  k_expm<<<a.nvec, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(bool fp64, const BatchArgs& a, int nblk, cudaStream_t s) {
+  if (fp64) k_combine<double, true><<<nblk, 256, 0, s>>>(a);
+  else k_combine<float, true><<<nblk, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observe(bool fp64, const BatchArgs& a, int nblk, cudaStream_t s) {
+  if (fp64) k_combine<double, false><<<nblk, 256, 0, s>>>(a);
+  else k_combine<float, false><<<nblk, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fermion_op(bool fp64, const void* in, void* out, int dim_up_src,
+                              int dim_dn_src, int dim_up_dst, int dim_dn_dst, int spin,
+                              const int32_t* map, cudaStream_t s) {
+  (void)dim_up_src;
+  const int64_t n = (int64_t)dim_up_dst * dim_dn_dst;
+  const int g = grid_for(n, 256);
+  if (fp64)
+    k_fermion_op<double><<<g, 256, 0, s>>>(static_cast<const double2*>(in),
+                                           static_cast<double2*>(out), dim_dn_src,
+                                           dim_up_dst, dim_dn_dst, spin, map);
+  else
+    k_fermion_op<float><<<g, 256, 0, s>>>(static_cast<const float2*>(in),
+                                          static_cast<float2*>(out), dim_dn_src,
+                                          dim_up_dst, dim_dn_dst, spin, map);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_overlap(bool fp64, const BatchArgs& a, const OverlapArgs& o, int nblk,
+                           cudaStream_t s) {
+  if (fp64) k_overlap<double><<<nblk, 256, 0, s>>>(a, o);
+  else k_overlap<float><<<nblk, 256, 0, s>>>(a, o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multidot(const double2* V, int64_t ldV, int k, const double2* w,
+                            int64_t D, double2* partial, int nblk, cudaStream_t s) {
+  const size_t sm = (size_t)(256 / 32) * k * sizeof(double2);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_multidot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_multidot<<<nblk, 256, sm, s>>>(V, ldV, k, w, D, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_cols(const double2* partial, int nblk, int k, double2* out,
+                               cudaStream_t s) {
+  k_reduce_cols<<<(k + 127) / 128, 128, 0, s>>>(partial, nblk, k, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multiaxpy(const double2* V, int64_t ldV, int k, const double2* c,
+                             double2* w, int64_t D, cudaStream_t s) {
+  k_multiaxpy<<<grid_for(D, 256), 256, 0, s>>>(V, ldV, k, c, w, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_real(const double2* V, int64_t ldV, int k, const double* c,
+                                double2* y, int64_t D, cudaStream_t s) {
+  k_combine_real<<<grid_for(D, 256), 256, 0, s>>>(V, ldV, k, c, y, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_dot(const double2* x, const double2* y, int64_t D, double* partial,
+                            int nblk, double* out, cudaStream_t s) {
+  k_norm_dot_partial<<<nblk, 256, 0, s>>>(x, y, D, partial);
+  k_sum_pairs<<<1, 256, 0, s>>>(partial, nblk, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double2* x, int64_t D, const double* s_dev, bool inverse_sqrt,
+                         cudaStream_t s) {
+  k_scale<<<grid_for(D, 256), 256, 0, s>>>(x, D, s_dev, inverse_sqrt ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_real(double2* y, const double2* x, int64_t D, const double* a_dev,
+                             double a_sign, cudaStream_t s) {
+  k_axpy_real<<<grid_for(D, 256), 256, 0, s>>>(y, x, D, a_dev, a_sign);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_random_fill(double2* x, int64_t D, uint64_t seed, cudaStream_t s) {
+  k_random_fill<<<grid_for(D, 256), 256, 0, s>>>(x, D, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_docc_sites(bool fp64, const void* psi, const SectorDev* sec, int dim_up,
+                              int dim_dn, int Ns, double* partial, int nblk, double* out,
+                              cudaStream_t s) {
+  (void)dim_up;
+  (void)dim_dn;
+  if (fp64)
+    k_docc_sites<double><<<nblk, 256, 0, s>>>(static_cast<const double2*>(psi), *sec, Ns,
+                                              partial);
+  else
+    k_docc_sites<float><<<nblk, 256, 0, s>>>(static_cast<const float2*>(psi), *sec, Ns,
+                                             partial);
+  k_sum_sites<<<1, 32, 0, s>>>(partial, nblk, kMaxSites + 1, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* in, bool in_fp64, void* out, bool out_fp64,
+                           int64_t n, cudaStream_t s) {
+  if (in_fp64 == out_fp64)
+    return cudaMemcpyAsync(out, in, n * (in_fp64 ? 16 : 8), cudaMemcpyDeviceToDevice, s);
+  if (in_fp64)
+    k_convert_c128_c64<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const double2*>(in),
+                                                         static_cast<float2*>(out), n);
+  else
+    k_convert_c64_c128<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const float2*>(in),
+                                                         static_cast<double2*>(out), n);
+  return cudaGetLastError();
+}
+
+}  // namespace ed

@@ -1,0 +1,90 @@
+// Kernel launchers (host-callable), implemented in kernels.cu.
+#pragma once
+
+#include "common.h"
+
+namespace ed {
+
+enum KernelKind { KK_APPLY = 0, KK_UPDATE = 1, KK_EXPM = 2, KK_COMBINE = 3,
+                  KK_ENERGY = 4, KK_OVERLAP = 5, KK_COUNT = 6 };
+
+struct LaunchShape {
+  int threads;   // block size of the apply kernel
+  int ept;       // elements per thread in the apply kernel
+  size_t smem;   // dynamic shared memory of the apply kernel
+};
+
+// Pick block size / elements-per-thread for rows of length max_dim_dn.
+LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups);
+// Raise the dynamic shared-memory limit of the apply kernel for this shape
+// (once, before launches or graph capture).
+cudaError_t prepare_apply(bool fp64, const LaunchShape& sh);
+
+// j >= 1: Lanczos step j; j == 0: plain apply x1 -> w with coefs row 0;
+// j == -1: energy (w = H x1 with coefs_obs[step], out_energy[step] = <x1,w>/Ns).
+cudaError_t launch_apply(bool fp64, const BatchArgs& a, int n_apply_blocks,
+                         const LaunchShape& sh, int j, cudaStream_t s);
+cudaError_t launch_update(bool fp64, const BatchArgs& a, int n_ew_blocks, int j,
+                          cudaStream_t s);
+cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s);
+cudaError_t launch_combine(bool fp64, const BatchArgs& a, int n_ew_blocks,
+                           cudaStream_t s);
+// Observables of x1 without combining (t_0): sets beta0, inv_scale[1], outputs.
+cudaError_t launch_observe(bool fp64, const BatchArgs& a, int n_ew_blocks,
+                           cudaStream_t s);
+
+// Fermion operator: out[t] = sign * in[src(t)] through a row map (spin 0) or a
+// column map (spin 1).  map entries: src | (neg << 31); 0x7FFFFFFF = no source.
+cudaError_t launch_fermion_op(bool fp64, const void* in, void* out,
+                              int dim_up_src, int dim_dn_src,
+                              int dim_up_dst, int dim_dn_dst, int spin,
+                              const int32_t* map, cudaStream_t s);
+
+// Overlaps <op psi | phi_b> for the phi vectors of a batch: per vector b with
+// map_off[b] >= 0, psi = vec[psi_index].x1; result added to out[(step)*nb*2..]
+struct OverlapArgs {
+  const int32_t* maps;      // concatenated maps
+  const int64_t* map_off;   // [nvec] offset into maps, -1 = no overlap
+  const int32_t* map_spin;  // [nvec] 0 row map, 1 column map
+  int psi_index;            // vector holding psi(t_n)
+  double* out;              // [n_steps+1][nvec][2] (re, im)
+};
+cudaError_t launch_overlap(bool fp64, const BatchArgs& a, const OverlapArgs& o,
+                           int n_ew_blocks, cudaStream_t s);
+
+// ---- ground-state helpers (float64 only) ---------------------------------
+// partial[blk][i] = sum over block chunk of conj(V_i) w, i < k  (k <= 256)
+cudaError_t launch_multidot(const double2* V, int64_t ldV, int k,
+                            const double2* w, int64_t D, double2* partial,
+                            int nblk, cudaStream_t s);
+cudaError_t launch_reduce_cols(const double2* partial, int nblk, int k,
+                               double2* out, cudaStream_t s);
+// w -= sum_i c_i V_i  (c on device)
+cudaError_t launch_multiaxpy(const double2* V, int64_t ldV, int k,
+                             const double2* c, double2* w, int64_t D,
+                             cudaStream_t s);
+// y = sum_i c_i V_i (c real, on device)
+cudaError_t launch_combine_real(const double2* V, int64_t ldV, int k,
+                                const double* c, double2* y, int64_t D,
+                                cudaStream_t s);
+// partial sums of |x|^2 and optionally Re<x, y>; out[2] via deterministic
+// two-pass reduction (partial has nblk*2 doubles).
+cudaError_t launch_norm_dot(const double2* x, const double2* y, int64_t D,
+                            double* partial, int nblk, double* out,
+                            cudaStream_t s);
+cudaError_t launch_scale(double2* x, int64_t D, const double* s_dev,
+                         bool inverse_sqrt, cudaStream_t s);
+cudaError_t launch_axpy_real(double2* y, const double2* x, int64_t D,
+                             const double* a_dev, double a_sign,
+                             cudaStream_t s);
+cudaError_t launch_random_fill(double2* x, int64_t D, uint64_t seed,
+                               cudaStream_t s);
+// double occupancy: out[0] = sum_k w_d |psi|^2, out[1+i] = site i values
+cudaError_t launch_docc_sites(bool fp64, const void* psi, const SectorDev* sec,
+                              int dim_up, int dim_dn, int Ns, double* partial,
+                              int nblk, double* out, cudaStream_t s);
+// dtype conversion
+cudaError_t launch_convert(const void* in, bool in_fp64, void* out,
+                           bool out_fp64, int64_t n_complex, cudaStream_t s);
+
+}  // namespace ed

@@ -1,0 +1,187 @@
+// Basis enumeration, combinadic ranks, connection tables, sector maps.
+#include "tables.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+namespace ed {
+
+uint64_t binomial(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  uint64_t r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+  return r;
+}
+
+static int popc(uint32_t x) { return __builtin_popcount(x); }
+
+std::vector<uint32_t> spin_basis(int Ns, int n) {
+  std::vector<uint32_t> out;
+  out.reserve((size_t)binomial(Ns, n));
+  if (n == 0) {
+    out.push_back(0u);
+    return out;
+  }
+  // next word with the same popcount (lowest-set-bit carry), ascending
+  uint32_t w = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  const uint64_t limit = 1ull << Ns;
+  while ((uint64_t)w < limit) {
+    out.push_back(w);
+    const uint32_t low = w & (0u - w);
+    const uint32_t ripple = w + low;
+    if (ripple == 0u) break;
+    const uint32_t ones = ((ripple ^ w) >> 2) / low;
+    w = ripple | ones;
+  }
+  return out;
+}
+
+uint32_t combinadic_rank(uint32_t word) {
+  uint32_t r = 0;
+  int k = 1;
+  while (word) {
+    const int pos = __builtin_ctz(word);
+    r += (uint32_t)binomial(pos, k);
+    ++k;
+    word &= word - 1;
+  }
+  return r;
+}
+
+std::string make_lattice(LatticeHost& L, int Ns, int n_bonds, const int32_t* p,
+                         const int32_t* q, const double* t, const double* d,
+                         double U, const double* eps) {
+  if (n_bonds < 0) return "n_bonds < 0";
+  if (n_bonds > 0 && (!p || !q || !t || !d)) return "bond arrays must not be NULL";
+  if (!std::isfinite(U)) return "U is not finite";
+  L = LatticeHost();
+  L.Ns = Ns;
+  L.n_bonds = n_bonds;
+  L.U = U;
+  for (int b = 0; b < n_bonds; ++b) {
+    if (p[b] < 0 || p[b] >= Ns || q[b] < 0 || q[b] >= Ns)
+      return "bond " + std::to_string(b) + ": site index out of range";
+    if (p[b] == q[b]) return "bond " + std::to_string(b) + ": p == q";
+    if (!std::isfinite(t[b]) || !std::isfinite(d[3 * b]) ||
+        !std::isfinite(d[3 * b + 1]) || !std::isfinite(d[3 * b + 2]))
+      return "bond " + std::to_string(b) + ": non-finite value";
+    L.p.push_back(p[b]);
+    L.q.push_back(q[b]);
+    L.t.push_back(t[b]);
+    for (int k = 0; k < 3; ++k) L.d.push_back(d[3 * b + k]);
+  }
+  if (eps) {
+    L.has_eps = true;
+    for (int i = 0; i < Ns; ++i) {
+      if (!std::isfinite(eps[i])) return "eps is not finite";
+      L.eps.push_back(eps[i]);
+    }
+  }
+  // bond classes: identical (t, d) <=> identical coefficient at every A
+  for (int b = 0; b < n_bonds; ++b) {
+    int c = -1;
+    for (int k = 0; k < L.n_classes; ++k) {
+      if (L.class_t[k] == L.t[b] && L.class_d[3 * k] == L.d[3 * b] &&
+          L.class_d[3 * k + 1] == L.d[3 * b + 1] && L.class_d[3 * k + 2] == L.d[3 * b + 2]) {
+        c = k;
+        break;
+      }
+    }
+    if (c < 0) {
+      c = L.n_classes++;
+      L.class_t.push_back(L.t[b]);
+      for (int k = 0; k < 3; ++k) L.class_d.push_back(L.d[3 * b + k]);
+    }
+    L.bond_class.push_back(c);
+  }
+  if (2 * L.n_classes > 256) return "more than 128 distinct bond classes";
+  return "";
+}
+
+SpinTable build_spin_table(const LatticeHost& L, int n) {
+  SpinTable T;
+  T.n = n;
+  T.words = spin_basis(L.Ns, n);
+  T.dim = (int)T.words.size();
+  T.off.assign(T.dim + 1, 0);
+  struct E { uint32_t group, src, neg; };
+  std::vector<E> row;
+  for (int r = 0; r < T.dim; ++r) {
+    const uint32_t y = T.words[r];
+    row.clear();
+    for (int b = 0; b < L.n_bonds; ++b) {
+      const int p = L.p[b], q = L.q[b];
+      const uint32_t bp = 1u << p, bq = 1u << q;
+      const int lo = std::min(p, q), hi = std::max(p, q);
+      const uint32_t between = ((1u << hi) - 1u) & ~((1u << (lo + 1)) - 1u);
+      const uint32_t neg = (uint32_t)(popc(y & between) & 1);
+      // orientation 0: hop p -> q produced y (q set, p clear in y)
+      if ((y & bq) && !(y & bp))
+        row.push_back({(uint32_t)(2 * L.bond_class[b]), combinadic_rank(y ^ bp ^ bq), neg});
+      // orientation 1: hop q -> p produced y (p set, q clear in y)
+      if ((y & bp) && !(y & bq))
+        row.push_back({(uint32_t)(2 * L.bond_class[b] + 1), combinadic_rank(y ^ bp ^ bq), neg});
+    }
+    std::sort(row.begin(), row.end(), [](const E& a, const E& b) {
+      return a.group != b.group ? a.group < b.group : a.src < b.src;
+    });
+    for (const E& e : row)
+      T.ent.push_back((e.src & 0xFFFFu) | (e.group << 16) | (e.neg << 31));
+    T.off[r + 1] = (int32_t)T.ent.size();
+  }
+  if (L.has_eps) {
+    T.eps_sum.resize(T.dim);
+    for (int r = 0; r < T.dim; ++r) {
+      double s = 0.0;
+      for (int i = 0; i < L.Ns; ++i)
+        if ((T.words[r] >> i) & 1u) s += L.eps[i];
+      T.eps_sum[r] = s;
+    }
+  }
+  return T;
+}
+
+void group_coefficients(const LatticeHost& L, const double A[3], double* out) {
+  for (int c = 0; c < L.n_classes; ++c) {
+    const double phi = A[0] * L.class_d[3 * c] + A[1] * L.class_d[3 * c + 1] +
+                       A[2] * L.class_d[3 * c + 2];
+    const double tc = L.class_t[c];
+    const double cs = std::cos(phi), sn = std::sin(phi);
+    // -t exp(-i phi) and -t exp(+i phi)
+    out[4 * c + 0] = -tc * cs;
+    out[4 * c + 1] = tc * sn;
+    out[4 * c + 2] = -tc * cs;
+    out[4 * c + 3] = -tc * sn;
+  }
+}
+
+void pulse_A(const double A0, double omega, double sigma, double t0, const double dir[3],
+             double t, double out[3]) {
+  const double s = t - t0;
+  const double amp = A0 * std::exp(-s * s / (2.0 * sigma * sigma)) * std::sin(omega * s);
+  for (int k = 0; k < 3; ++k) out[k] = amp * dir[k];
+}
+
+std::vector<int32_t> fermion_map(int Ns, int n_up, int n_dn, int site, int spin,
+                                 bool create) {
+  const int n_src = spin == 0 ? n_up : n_dn;
+  const int n_dst = n_src + (create ? 1 : -1);
+  const std::vector<uint32_t> dst_words = spin_basis(Ns, n_dst);
+  std::vector<int32_t> map(dst_words.size(), 0x7FFFFFFF);
+  const uint32_t bit = 1u << site;
+  const uint32_t below = bit - 1u;
+  for (size_t t = 0; t < dst_words.size(); ++t) {
+    const uint32_t y = dst_words[t];
+    // c removes the electron: y lacks the bit; c^+ adds it: y has the bit
+    if (create ? !(y & bit) : (y & bit)) continue;
+    const uint32_t x = y ^ bit;  // source configuration
+    int parity = popc(x & below);
+    if (spin == 1) parity += n_up;
+    const uint32_t src = combinadic_rank(x);
+    map[t] = (int32_t)(src | ((uint32_t)(parity & 1) << 31));
+  }
+  return map;
+}
+
+}  // namespace ed

@@ -1,0 +1,69 @@
+// Host-side basis enumeration, ranks, connection tables and sector maps.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace ed {
+
+// Spin basis of n electrons on Ns sites: all Ns-bit words with n ones in
+// ascending order (Sec. 3.1; the order of the hash of Eq. (36)).
+std::vector<uint32_t> spin_basis(int Ns, int n);
+
+// Rank of a popcount-n word in that basis by the combinatorial number system,
+// sum_k C(p_k, k+1) over the 0-based sorted occupied positions p_0 < p_1 < ...
+// (Eq. (36) with 0-based positions).
+uint32_t combinadic_rank(uint32_t word);
+uint64_t binomial(int n, int k);
+
+struct LatticeHost {
+  int Ns = 0;
+  int n_bonds = 0;
+  std::vector<int> p, q;
+  std::vector<double> t, d;      // d: 3 per bond
+  double U = 0.0;
+  bool has_eps = false;
+  std::vector<double> eps;       // Ns
+  int n_classes = 0;             // bonds with equal (t, d) share a class
+  std::vector<int> bond_class;   // per bond
+  std::vector<double> class_t, class_d;
+};
+
+// Validates and fills the bond classes; returns "" or an error message.
+std::string make_lattice(LatticeHost& L, int Ns, int n_bonds, const int32_t* p,
+                         const int32_t* q, const double* t, const double* d,
+                         double U, const double* eps);
+
+// Connection table of one spin species (target-row major, CSR):
+// for target configuration y (rank r) every source x = y ^ 2^p ^ 2^q that a
+// hop along a bond turns into y, packed as (rank(x), group, sign).  Entries
+// of a row are sorted by (group, source rank).
+struct SpinTable {
+  int n = 0, dim = 0;
+  std::vector<uint32_t> words;
+  std::vector<int32_t> off;
+  std::vector<uint32_t> ent;
+  std::vector<double> eps_sum;   // per state: sum of eps over occupied sites
+};
+SpinTable build_spin_table(const LatticeHost& L, int n);
+
+// Per-group hopping coefficients for a vector potential A:
+//   group 2c   (hop p -> q of class c): -t_c exp(-i A.d_c)
+//   group 2c+1 (hop q -> p):            -t_c exp(+i A.d_c)
+// written as interleaved (re, im) doubles, 2 * n_classes complex numbers.
+void group_coefficients(const LatticeHost& L, const double A[3], double* out);
+
+// Vector potential of the pump pulse at time t.
+void pulse_A(const double A0, double omega, double sigma, double t0,
+             const double dir[3], double t, double out[3]);
+
+// Map for c_{i,s} (create = false) or c^+_{i,s} (create = true) from the
+// sector (n_up, n_dn) to the target sector, over the target ranks of spin s:
+// entry = source rank | (sign < 0) << 31, or 0x7FFFFFFF when the target
+// configuration has no source.  Sign (-1)^(occupied modes before (i, s)),
+// modes ordered all up then all down (so spin 1 includes (-1)^n_up).
+std::vector<int32_t> fermion_map(int Ns, int n_up, int n_dn, int site, int spin,
+                                 bool create);
+
+}  // namespace ed

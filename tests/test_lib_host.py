@@ -1,0 +1,173 @@
+"""The C-ABI library on the host (no GPU): symbols, basis, tables, errors.
+
+Basis words and connection tables are compared bit-exactly with the oracle:
+the sparsity pattern of the tables equals that of the oracle's per-spin
+hopping matrices, and at a generic vector potential every entry's group and
+sign reproduce the oracle's value.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ed():
+    from paper_2005_13498_gb300 import build
+    build.build()
+    from paper_2005_13498_gb300 import ed as mod
+    return mod
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ed.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:ed_status|const char\*)\s+(ed_\w+)\s*\(",
+                                 src, re.M)))
+
+
+def test_library_exports_every_declared_symbol(ed):
+    names = header_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(ed.lib, n), n
+    assert "sm_103a" in ed.ed_version()
+
+
+def test_errors_without_gpu_work(ed):
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_build_basis(17, 3, 3)
+    assert e.value.status == 5
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_build_basis(6, 7, 3)
+    assert e.value.status == 1
+    ctx = ed.ed_build_basis(4, 2, 2)
+    bad = {"Ns": 4, "p": [0], "q": [0], "t": [1.0], "d": [[1, 0, 0]], "eps": None}
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_set_lattice(ctx, bad, 1.0)
+    assert e.value.status == 1 and "p == q" in str(e.value)
+    bad = {"Ns": 4, "p": [0], "q": [9], "t": [1.0], "d": [[1, 0, 0]], "eps": None}
+    with pytest.raises(ed.EDError):
+        ed.ed_set_lattice(ctx, bad, 1.0)
+    # calls before the lattice is set
+    psi = np.zeros(36, dtype=np.complex128)
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_propagate(ctx, psi, ed.ED_C128, None, 0.0, 0.01, 1, 4)
+    assert e.value.status == 6
+    ed.ed_set_lattice(ctx, synth.ring(4), 2.0)
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_propagate(ctx, psi, ed.ED_C128, None, 0.0, 0.01, 1, 65)
+    assert e.value.status == 5
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_propagate(ctx, psi, ed.ED_C128, None, 0.0, 0.01, 1, 0)
+    assert e.value.status == 1
+    ed.ed_destroy(ctx)
+
+
+@pytest.mark.parametrize("Ns", [1, 2, 5, 8, 12, 14, 16])
+def test_basis_words_match_oracle(ed, Ns):
+    for n in sorted({0, 1, Ns // 2, Ns - 1, Ns}):
+        if not 0 <= n <= Ns:
+            continue
+        ctx = ed.ed_build_basis(Ns, n, max(0, Ns - n))
+        du, dd = ed.ed_dims(ctx)
+        assert du == len(oracle.spin_basis(Ns, n))
+        assert np.array_equal(ed.ed_get_basis(ctx, 0).astype(np.uint64),
+                              oracle.spin_basis(Ns, n))
+        assert np.array_equal(ed.ed_get_basis(ctx, 1).astype(np.uint64),
+                              oracle.spin_basis(Ns, max(0, Ns - n)))
+        ed.ed_destroy(ctx)
+
+
+def table_matrix(off, ent, coefs):
+    """Dense matrix of a connection table: M[r, src] += sign * coef[group]."""
+    dim = len(off) - 1
+    M = np.zeros((dim, dim), dtype=complex)
+    for r in range(dim):
+        for e in ent[off[r]:off[r + 1]]:
+            src = int(e) & 0xFFFF
+            g = (int(e) >> 16) & 0xFF
+            sgn = -1.0 if (int(e) >> 31) & 1 else 1.0
+            M[r, src] += sgn * coefs[g]
+    return M
+
+
+def class_coefficients(lat, A):
+    """Coefficients per group in the table's class order (first-seen order of
+    distinct (t, d) bonds)."""
+    classes = []
+    for b in range(len(lat["p"])):
+        key = (lat["t"][b], *lat["d"][b])
+        if key not in classes:
+            classes.append(key)
+    c = []
+    for key in classes:
+        phi = np.dot(key[1:], A)
+        c += [-key[0] * np.exp(-1j * phi), -key[0] * np.exp(1j * phi)]
+    return np.array(c)
+
+
+LATTICES = [
+    ("ring8", synth.ring(8), [(4, 4), (3, 5)]),
+    ("torus3x4", synth.torus(4, 3), [(6, 6), (5, 7)]),
+    ("ladder2x7", synth.ladder(7), [(7, 7), (6, 8)]),
+    ("complete6", synth.complete_graph(6, seed=4), [(3, 2)]),
+    ("triangle", synth.triangle(), [(2, 1)]),
+    ("chain5_eps", synth.chain(5, eps=[0.1, 0.2, -0.3, 0.0, 0.5]), [(2, 3)]),
+]
+
+
+@pytest.mark.parametrize("name,lat,sectors", LATTICES, ids=[x[0] for x in LATTICES])
+def test_tables_match_oracle_bit_exact(ed, name, lat, sectors):
+    A = np.array([0.31, -0.17, 0.23])
+    for (nu, nd) in sectors:
+        ctx = ed.ed_build_basis(lat["Ns"], nu, nd)
+        ed.ed_set_lattice(ctx, lat, 3.0)
+        for spin, n in ((0, nu), (1, nd)):
+            off, ent, ncl = ed.ed_get_table(ctx, spin)
+            T = oracle.spin_hopping_matrix(lat, n, A)
+            dim = T.shape[0]
+            if dim > 1000:
+                # pattern and values row by row without a dense matrix
+                coefs = class_coefficients(lat, A)
+                Tc = T.tocsr()
+                for r in range(0, dim, 7):
+                    row = {}
+                    for e in ent[off[r]:off[r + 1]]:
+                        src = int(e) & 0xFFFF
+                        g = (int(e) >> 16) & 0xFF
+                        sgn = -1.0 if (int(e) >> 31) & 1 else 1.0
+                        row[src] = row.get(src, 0) + sgn * coefs[g]
+                    ref = dict(zip(Tc.indices[Tc.indptr[r]:Tc.indptr[r + 1]],
+                                   Tc.data[Tc.indptr[r]:Tc.indptr[r + 1]]))
+                    assert set(row) == set(ref)
+                    for k in row:
+                        assert abs(row[k] - ref[k]) < 1e-14
+                continue
+            M = table_matrix(off, ent, class_coefficients(lat, A))
+            Td = T.toarray()
+            assert np.array_equal(M != 0, Td != 0)
+            assert np.abs(M - Td).max() < 1e-14
+            # rows sorted by (group, source)
+            for r in range(dim):
+                es = [(int(e) >> 16 & 0xFF, int(e) & 0xFFFF) for e in ent[off[r]:off[r + 1]]]
+                assert es == sorted(es)
+        ed.ed_destroy(ctx)
+
+
+def test_connection_counts_complete_graph(ed):
+    # every single-electron hop allowed: n (Ns - n) entries per state (Eq. (22))
+    Ns = 8
+    lat = synth.complete_graph(Ns, seed=2)
+    for n in range(Ns + 1):
+        ctx = ed.ed_build_basis(Ns, n, 0)
+        ed.ed_set_lattice(ctx, lat, 1.0)
+        off, ent, ncl = ed.ed_get_table(ctx, 0)
+        assert np.all(np.diff(off) == n * (Ns - n))
+        ed.ed_destroy(ctx)
