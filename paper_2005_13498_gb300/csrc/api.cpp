@@ -226,6 +226,8 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     P.valid = false;
     const int64_t D = ctx->dim_up * ctx->dim_dn;
     const size_t esz = fp64 ? 16 : 8;
+    const int ng = 2 * ctx->lat.n_classes;
+    P.shape = apply_shape((int)ctx->dim_dn, fp64, ng);
     std::vector<VecDev> vd(nvec);
     std::vector<ApplyBlock> amap;
     for (int b = 0; b < nvec; ++b) {
@@ -235,10 +237,9 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
       vd[b].x1 = const_cast<char*>(static_cast<const char*>(v)) + (size_t)b * D * esz;
       vd[b].w = static_cast<char*>(w) + (size_t)b * D * esz;
       vd[b].apply_begin = (int)amap.size();
-      for (int r = 0; r < ctx->dim_up; ++r) amap.push_back({b, r, 1, 0});
+      append_apply_blocks(amap, b, (int)ctx->dim_up, P.shape.nr);
       vd[b].apply_end = (int)amap.size();
     }
-    const int ng = 2 * ctx->lat.n_classes;
     std::vector<double> cf(std::max(1, ng) * 2, 0.0);
     group_coefficients(ctx->lat, ctx->A, cf.data());
     std::vector<float> cff(cf.begin(), cf.end());
@@ -267,7 +268,6 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     P.args.Ns = ctx->Ns;
     P.args.max_dim_dn = (int)ctx->dim_dn;
     P.args.U = ctx->lat.U;
-    P.shape = apply_shape((int)ctx->dim_dn, fp64, ng);
     CK(ctx, prepare_apply(fp64, P.shape));
     P.nblk = (int)amap.size();
     P.nvec = nvec;

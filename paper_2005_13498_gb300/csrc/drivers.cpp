@@ -101,11 +101,12 @@ cudaError_t gs_apply_setup(GsApply& G, ed_ctx* ctx) {
   std::vector<VecDev> vd(1);
   std::memset(vd.data(), 0, sizeof(VecDev));
   vd[0].D = ctx->dim_up * ctx->dim_dn;
+  const int ng = 2 * ctx->lat.n_classes;
+  G.shape = apply_shape((int)ctx->dim_dn, true, ng);
   std::vector<ApplyBlock> amap;
-  for (int r = 0; r < ctx->dim_up; ++r) amap.push_back({0, r, 1, 0});
+  append_apply_blocks(amap, 0, (int)ctx->dim_up, G.shape.nr);
   vd[0].apply_begin = 0;
   vd[0].apply_end = (int)amap.size();
-  const int ng = 2 * ctx->lat.n_classes;
   std::vector<double> cf(std::max(1, ng) * 2, 0.0);
   const double A0[3] = {0, 0, 0};
   group_coefficients(ctx->lat, A0, cf.data());
@@ -133,7 +134,6 @@ cudaError_t gs_apply_setup(GsApply& G, ed_ctx* ctx) {
   G.args.Ns = ctx->Ns;
   G.args.max_dim_dn = (int)ctx->dim_dn;
   G.args.U = ctx->lat.U;
-  G.shape = apply_shape((int)ctx->dim_dn, true, ng);
   G.nblk = (int)amap.size();
   return prepare_apply(true, G.shape);
 }

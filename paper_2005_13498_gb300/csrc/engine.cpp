@@ -102,6 +102,9 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   std::vector<EwBlock> emap;
   std::vector<VecDev> vd(nv);
   int max_dim_dn = 1;
+  for (int i = 0; i < nv; ++i) max_dim_dn = std::max(max_dim_dn, sectors_[vecs_[i].sector].dim_dn);
+  shape_ = apply_shape(max_dim_dn, cfg.fp64, n_groups);
+  const int shape_nr = shape_.nr;
   int64_t voff = 0;
   const int ncap = cfg.n_steps_cap;
   // outputs per vector: docc, norm2, energy [ncap+1], delta [ncap], meff [ncap]
@@ -119,7 +122,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     v.w = static_cast<char*>(d_w_.p) + (size_t)voff * esz;
     voff += v.D;
     v.apply_begin = (int)amap.size();
-    for (int r = 0; r < sd.dim_up; ++r) amap.push_back({i, r, 1, 0});
+    append_apply_blocks(amap, i, sd.dim_up, shape_nr);
     v.apply_end = (int)amap.size();
     v.ew_begin = (int)emap.size();
     const int64_t ch = ew_chunk(v.D);
@@ -134,7 +137,6 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   }
   n_apply_ = (int)amap.size();
   n_ew_ = (int)emap.size();
-  shape_ = apply_shape(max_dim_dn, cfg.fp64, n_groups);
   ED_TRY(prepare_apply(cfg.fp64, shape_));
 
   ED_TRY(d_sec_.alloc(sizeof(SectorDev) * sectors_.size()));

@@ -110,10 +110,18 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 // ------------------------------------------------------------------- apply
 // j >= 1: Lanczos pass j; j == 0: plain apply (coefs row 0, x1 -> w);
 // j == -1: energy of x1 with coefs_obs[step].
-template <int EPT> struct ApplyBound { static constexpr int v = EPT >= 16 ? 256 : (EPT >= 8 ? 512 : 1024); };
-
-template <typename R, int EPT>
-__global__ void __launch_bounds__(ApplyBound<EPT>::v)
+// One CTA processes NR consecutive rows u0..u0+NR-1 of one vector.  The rows
+// are staged in shared memory transposed, tile[d*NR + r], so that the T_dn
+// gathers of one column d' fetch the NR values of all rows with one vector
+// load and each connection-table entry is decoded once for NR rows.  Threads
+// own columns d = c0 + tid + k*blockDim (k < CPT) of every chunk c0; T_up
+// reads whole rows Psi[u', d] of the gather source with coalesced loads along
+// d (the entry list of row u is uniform across the block, sorted by group, and
+// signed values of one group are summed before the complex multiply).  The
+// coefficient table in shared memory holds +c_g and -c_g so that an entry's
+// sign selects its coefficient directly.
+template <typename R, int NR, int CPT>
+__global__ void __launch_bounds__(512)
 k_apply(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -126,17 +134,24 @@ k_apply(BatchArgs a, int j) {
   if (j >= 1 && st->stopped) return;   // uniform over the vector's blocks
   const SectorDev sd = a.sec[vd.sector];
   const int dim_dn = sd.dim_dn;
+  const int u0 = ab.row0;
+  const int nrows = ab.nrows;
 
-  C* row = reinterpret_cast<C*>(smem_raw);
-  C* coef = row + a.max_dim_dn;
+  C* tile = reinterpret_cast<C*>(smem_raw);            // [max_dim_dn][NR]
+  C* coefS = tile + (size_t)a.max_dim_dn * NR;        // [2 * n_groups]
 
-  // coefficients of this step (or of the observation time / static field)
   const void* cbase;
   if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
   else if (j == 0) cbase = a.coefs;
   else cbase = static_cast<const char*>(a.coefs_obs) + (size_t)st->step * a.n_groups * sizeof(C);
-  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
-    coef[g] = reinterpret_cast<const C*>(cbase)[g];
+  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) {
+    const C c = reinterpret_cast<const C*>(cbase)[g];
+    C m;
+    m.x = -c.x;
+    m.y = -c.y;
+    coefS[2 * g] = c;
+    coefS[2 * g + 1] = m;
+  }
 
   const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
   const C* xp = (j >= 2) ? static_cast<const C*>(xptr(vd, j - 1, sizeof(C))) : nullptr;
@@ -144,106 +159,125 @@ k_apply(BatchArgs a, int j) {
   const R s_in = (j >= 1) ? (R)st->inv_scale[j] : (R)1;
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
-  const int chunk = blockDim.x * EPT;
 
-  double dot_d = 0.0;   // Re<x, w>: per-row partials in R, accumulated in double
-
-  for (int r = 0; r < ab.nrows; ++r) {
-    const int u = ab.row0 + r;
-    const C* xrow = x + (size_t)u * dim_dn;
-    __syncthreads();
-    for (int d = threadIdx.x; d < dim_dn; d += blockDim.x) row[d] = xrow[d];
-    __syncthreads();
-    const uint32_t uw = __ldg(sd.up_word + u);
-    const R eu = sd.up_eps ? (R)__ldg(sd.up_eps + u) : (R)0;
-    const int e0 = __ldg(sd.up_off + u), e1 = __ldg(sd.up_off + u + 1);
-    C* wrow = w + (size_t)u * dim_dn;
-    const C* xprow = xp ? xp + (size_t)u * dim_dn : nullptr;
-
-    for (int c0 = 0; c0 < dim_dn; c0 += chunk) {
-      C acc[EPT];
+  // stage the NR rows, transposed
+  for (int d = threadIdx.x; d < dim_dn; d += blockDim.x) {
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int d = c0 + threadIdx.x + k * blockDim.x;
-        acc[k] = czero<C>();
-        if (d < dim_dn) {
-          // diagonal: U * #doubles (+ on-site energies)
-          R dg = U * (R)__popc(uw & __ldg(sd.dn_word + d)) + eu;
-          if (sd.dn_eps) dg += (R)__ldg(sd.dn_eps + d);
-          const C xv = row[d];
-          C a2;
-          a2.x = dg * xv.x;
-          a2.y = dg * xv.y;
-          // T_dn: gathers within the staged row
-          const int f0 = __ldg(sd.dn_off + d), f1 = __ldg(sd.dn_off + d + 1);
-          for (int f = f0; f < f1; ++f) {
-            const uint32_t ent = __ldg(sd.dn_ent + f);
-            const C v = row[ent & kEntRankMask];
-            C c = coef[(ent >> kEntGroupShift) & 0xFFu];
-            if (ent & kEntSignBit) { c.x = -c.x; c.y = -c.y; }
-            a2.x += c.x * v.x - c.y * v.y;
-            a2.y += c.x * v.y + c.y * v.x;
-          }
-          acc[k] = a2;
-        }
-      }
-      // T_up: the entry list of row u is uniform across the block; entries
-      // are sorted by group, signed values of one group are summed first.
-      int e = e0;
-      while (e < e1) {
-        uint32_t ent = __ldg(sd.up_ent + e);
-        const uint32_t g = (ent >> kEntGroupShift) & 0xFFu;
-        C sum[EPT];
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) sum[k] = czero<C>();
-        while (true) {
-          const C* src = x + (size_t)(ent & kEntRankMask) * dim_dn;
-          if (ent & kEntSignBit) {
-#pragma unroll
-            for (int k = 0; k < EPT; ++k) {
-              const int d = c0 + threadIdx.x + k * blockDim.x;
-              if (d < dim_dn) { const C v = src[d]; sum[k].x -= v.x; sum[k].y -= v.y; }
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < EPT; ++k) {
-              const int d = c0 + threadIdx.x + k * blockDim.x;
-              if (d < dim_dn) { const C v = src[d]; sum[k].x += v.x; sum[k].y += v.y; }
-            }
-          }
-          ++e;
-          if (e >= e1) break;
-          ent = __ldg(sd.up_ent + e);
-          if (((ent >> kEntGroupShift) & 0xFFu) != g) break;
-        }
-        const C c = coef[g];
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-          acc[k].x += c.x * sum[k].x - c.y * sum[k].y;
-          acc[k].y += c.x * sum[k].y + c.y * sum[k].x;
-        }
-      }
-      // epilogue: scale, three-term subtraction, store, inner product
-      R dot_acc = (R)0;
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int d = c0 + threadIdx.x + k * blockDim.x;
-        if (d < dim_dn) {
-          C o;
-          o.x = s_in * acc[k].x;
-          o.y = s_in * acc[k].y;
-          if (xprow) {
-            const C pv = xprow[d];
-            o.x -= s_prev * pv.x;
-            o.y -= s_prev * pv.y;
-          }
-          wrow[d] = o;
-          const C xv = row[d];
-          dot_acc += xv.x * o.x + xv.y * o.y;
-        }
-      }
-      dot_d += (double)dot_acc;
+    for (int r = 0; r < NR; ++r) {
+      C v = czero<C>();
+      if (r < nrows) v = x[(size_t)(u0 + r) * dim_dn + d];
+      tile[(size_t)d * NR + r] = v;
     }
+  }
+  uint32_t uw[NR];
+  R eu[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int u = r < nrows ? u0 + r : u0;
+    uw[r] = __ldg(sd.up_word + u);
+    eu[r] = sd.up_eps ? (R)__ldg(sd.up_eps + u) : (R)0;
+  }
+  __syncthreads();
+
+  double dot_d = 0.0;
+  const int chunk = blockDim.x * CPT;
+  for (int c0 = 0; c0 < dim_dn; c0 += chunk) {
+    C acc[NR][CPT];
+    // diagonal + T_dn from the staged tile
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int d = c0 + threadIdx.x + k * blockDim.x;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r][k] = czero<C>();
+      if (d < dim_dn) {
+        const uint32_t dw = __ldg(sd.dn_word + d);
+        const R de = sd.dn_eps ? (R)__ldg(sd.dn_eps + d) : (R)0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const R dg = U * (R)__popc(uw[r] & dw) + eu[r] + de;
+          const C xv = tile[(size_t)d * NR + r];
+          acc[r][k].x = dg * xv.x;
+          acc[r][k].y = dg * xv.y;
+        }
+        const int f0 = __ldg(sd.dn_off + d), f1 = __ldg(sd.dn_off + d + 1);
+        for (int f = f0; f < f1; ++f) {
+          const uint32_t ent = __ldg(sd.dn_ent + f);
+          const C c = coefS[((ent >> 15) & 0x1FEu) | (ent >> 31)];
+          const C* vsrc = tile + (size_t)(ent & kEntRankMask) * NR;
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const C v = vsrc[r];
+            acc[r][k].x += c.x * v.x - c.y * v.y;
+            acc[r][k].y += c.x * v.y + c.y * v.x;
+          }
+        }
+      }
+    }
+    // T_up: per row, uniform entry list, grouped sums
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nrows) {
+        const int u = u0 + r;
+        const int e0 = __ldg(sd.up_off + u), e1 = __ldg(sd.up_off + u + 1);
+        int e = e0;
+        while (e < e1) {
+          uint32_t ent = __ldg(sd.up_ent + e);
+          const uint32_t g = (ent >> kEntGroupShift) & 0xFFu;
+          C sum[CPT];
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) sum[k] = czero<C>();
+          while (true) {
+            const C* src = x + (size_t)(ent & kEntRankMask) * dim_dn;
+            const R sg = (ent & kEntSignBit) ? (R)-1 : (R)1;
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+              const int d = c0 + threadIdx.x + k * blockDim.x;
+              if (d < dim_dn) {
+                const C v = src[d];
+                sum[k].x += sg * v.x;
+                sum[k].y += sg * v.y;
+              }
+            }
+            ++e;
+            if (e >= e1) break;
+            ent = __ldg(sd.up_ent + e);
+            if (((ent >> kEntGroupShift) & 0xFFu) != g) break;
+          }
+          const C c = coefS[2 * g];
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) {
+            acc[r][k].x += c.x * sum[k].x - c.y * sum[k].y;
+            acc[r][k].y += c.x * sum[k].y + c.y * sum[k].x;
+          }
+        }
+      }
+    }
+    // epilogue: scale, three-term subtraction, store, inner product
+    R dot_acc = (R)0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nrows) {
+        const size_t rowoff = (size_t)(u0 + r) * dim_dn;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          const int d = c0 + threadIdx.x + k * blockDim.x;
+          if (d < dim_dn) {
+            C o;
+            o.x = s_in * acc[r][k].x;
+            o.y = s_in * acc[r][k].y;
+            if (xp) {
+              const C pv = xp[rowoff + d];
+              o.x -= s_prev * pv.x;
+              o.y -= s_prev * pv.y;
+            }
+            w[rowoff + d] = o;
+            const C xv = tile[(size_t)d * NR + r];
+            dot_acc += xv.x * o.x + xv.y * o.y;
+          }
+        }
+      }
+    }
+    dot_d += (double)dot_acc;
   }
   if (j == 0) return;
   double v[1] = {dot_d};
@@ -439,6 +473,7 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
   __shared__ double red[64];
   __shared__ int flag;
   __shared__ C cf[kMaxKrylov + 1];
+  __shared__ C cf_lo;   // c_1 - (R)c_1: the dominant coefficient in two parts
   const EwBlock eb = a.ew_map[blockIdx.x];
   const VecDev vd = a.vec[eb.vec];
   LanczosState* st = a.st + eb.vec;
@@ -448,6 +483,10 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
     for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
       cf[jj].x = (R)st->comb_re[jj + 1];
       cf[jj].y = (R)st->comb_im[jj + 1];
+    }
+    if (threadIdx.x == 0) {
+      cf_lo.x = (R)(st->comb_re[1] - (double)(R)st->comb_re[1]);
+      cf_lo.y = (R)(st->comb_im[1] - (double)(R)st->comb_im[1]);
     }
     __syncthreads();
   }
@@ -460,15 +499,20 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
   for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
     C p;
     if (COMBINE) {
+      // small terms first, the dominant c_1 x_1 (split hi + lo) last: in
+      // float32 this keeps the rounding of c_1 out of |psi| (the norm drifts
+      // otherwise by ~1e-7 per step)
       const C x = x1[i];
-      p.x = cf[0].x * x.x - cf[0].y * x.y;
-      p.y = cf[0].x * x.y + cf[0].y * x.x;
+      p.x = cf_lo.x * x.x - cf_lo.y * x.y;
+      p.y = cf_lo.x * x.y + cf_lo.y * x.x;
       for (int jj = 1; jj < n; ++jj) {
         const C v = V[(size_t)(jj - 1) * vd.D + i];
         const C c = cf[jj];
         p.x += c.x * v.x - c.y * v.y;
         p.y += c.x * v.y + c.y * v.x;
       }
+      p.x += cf[0].x * x.x - cf[0].y * x.y;
+      p.y += cf[0].x * x.y + cf[0].y * x.x;
       x1[i] = p;
     } else {
       p = x1[i];
@@ -754,43 +798,44 @@ static int grid_for(int64_t n, int threads) {
 }
 
 LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
-  // elements per thread: 16 (float) / 8 (double) for long rows, fewer for
-  // short rows; the block covers the row in chunks of threads * ept columns.
-  int ept = fp64 ? 8 : 16;
-  while (ept > 1 && (max_dim_dn + ept - 1) / ept < 32) ept /= 2;
-  const int bound = ept >= 16 ? 256 : (ept >= 8 ? 512 : 1024);
-  int threads = (max_dim_dn + ept - 1) / ept;
+  const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
+  // rows per CTA: as many as fit in ~110 KB of shared memory (two CTAs per
+  // SM), at most 4
+  int nr = (int)((110 * 1024) / ((size_t)max_dim_dn * csz));
+  if (nr > 4) nr = 4;
+  if (nr == 3) nr = 2;
+  if (nr < 1) nr = 1;
+  const int cpt = 2;
+  int nchunks = (max_dim_dn + cpt * 512 - 1) / (cpt * 512);
+  if (nchunks < 1) nchunks = 1;
+  int threads = (max_dim_dn + cpt * nchunks - 1) / (cpt * nchunks);
   threads = ((threads + 31) / 32) * 32;
   if (threads < 32) threads = 32;
-  if (threads > bound) threads = bound;
+  if (threads > 512) threads = 512;
   LaunchShape sh;
   sh.threads = threads;
-  sh.ept = ept;
-  const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
-  sh.smem = (size_t)(max_dim_dn + n_groups) * csz;
+  sh.ept = cpt;
+  sh.nr = nr;
+  sh.smem = ((size_t)max_dim_dn * nr + 2 * (size_t)n_groups) * csz;
   return sh;
 }
 
-template <typename R, int EPT>
+template <typename R, int NR>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
-  k_apply<R, EPT><<<nblk, sh.threads, sh.smem, s>>>(a, j);
+  k_apply<R, NR, 2><<<nblk, sh.threads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
 }
 
 template <typename R>
 static cudaError_t prepare_apply_r(const LaunchShape& sh) {
-  cudaError_t e = cudaSuccess;
   const int sm = (int)sh.smem;
-  switch (sh.ept) {
-    case 1: e = cudaFuncSetAttribute(k_apply<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
-    case 2: e = cudaFuncSetAttribute(k_apply<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
-    case 4: e = cudaFuncSetAttribute(k_apply<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
-    case 8: e = cudaFuncSetAttribute(k_apply<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
-    case 16: e = cudaFuncSetAttribute(k_apply<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
-    default: e = cudaErrorInvalidValue;
+  switch (sh.nr) {
+    case 1: return cudaFuncSetAttribute(k_apply<R, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    case 2: return cudaFuncSetAttribute(k_apply<R, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    case 4: return cudaFuncSetAttribute(k_apply<R, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    default: return cudaErrorInvalidValue;
   }
-  return e;
 }
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
@@ -801,12 +846,10 @@ cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
 template <typename R>
 static cudaError_t launch_apply_r(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
-  switch (sh.ept) {
+  switch (sh.nr) {
     case 1: return launch_apply_t<R, 1>(a, nblk, sh, j, s);
     case 2: return launch_apply_t<R, 2>(a, nblk, sh, j, s);
     case 4: return launch_apply_t<R, 4>(a, nblk, sh, j, s);
-    case 8: return launch_apply_t<R, 8>(a, nblk, sh, j, s);
-    case 16: return launch_apply_t<R, 16>(a, nblk, sh, j, s);
     default: return cudaErrorInvalidValue;
   }
 }

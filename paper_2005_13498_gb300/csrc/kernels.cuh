@@ -1,6 +1,8 @@
 // Kernel launchers (host-callable), implemented in kernels.cu.
 #pragma once
 
+#include <vector>
+
 #include "common.h"
 
 namespace ed {
@@ -10,9 +12,16 @@ enum KernelKind { KK_APPLY = 0, KK_UPDATE = 1, KK_EXPM = 2, KK_COMBINE = 3,
 
 struct LaunchShape {
   int threads;   // block size of the apply kernel
-  int ept;       // elements per thread in the apply kernel
+  int ept;       // columns per thread per chunk in the apply kernel
+  int nr;        // rows per CTA (apply blocks hold up to nr rows)
   size_t smem;   // dynamic shared memory of the apply kernel
 };
+
+// Apply blocks of nr rows covering rows [0, dim_up) of vector vec.
+inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_up, int nr) {
+  for (int r = 0; r < dim_up; r += nr)
+    map.push_back({vec, r, dim_up - r < nr ? dim_up - r : nr, 0});
+}
 
 // Pick block size / elements-per-thread for rows of length max_dim_dn.
 LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups);
