@@ -31,6 +31,15 @@ struct SectorDev {
   const uint32_t* dn_word;  // [dim_dn]
   const double* up_eps;     // [dim_up] sum of eps over occupied sites, or null
   const double* dn_eps;     // [dim_dn]
+  // up spin: group segments of each row (across-row gathers)
+  const int32_t* up_seg_off;   // [dim_up + 1]
+  const uint32_t* up_seg;      // group | begin << 8
+  const uint32_t* up_seg_end;  // end entry index
+  // down spin: warp-tiled ELL over columns (within-row gathers)
+  const int32_t* dn_tseg_off;  // [ceil(dim_dn/32) + 1]
+  const uint32_t* dn_tseg;     // group | K << 8
+  const int32_t* dn_tslot;     // first slot of the segment
+  const uint32_t* dn_ell;      // [slots][32]: rank | sign << 31, pad = dim_dn
 };
 
 // Per-vector Lanczos scalars, all float64, 1-based Krylov index j.

@@ -111,17 +111,22 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 // j >= 1: Lanczos pass j; j == 0: plain apply (coefs row 0, x1 -> w);
 // j == -1: energy of x1 with coefs_obs[step].
 // One CTA processes NR consecutive rows u0..u0+NR-1 of one vector.  The rows
-// are staged in shared memory transposed, tile[d*NR + r], so that the T_dn
-// gathers of one column d' fetch the NR values of all rows with one vector
-// load and each connection-table entry is decoded once for NR rows.  Threads
-// own columns d = c0 + tid + k*blockDim (k < CPT) of every chunk c0; T_up
-// reads whole rows Psi[u', d] of the gather source with coalesced loads along
-// d (the entry list of row u is uniform across the block, sorted by group, and
-// signed values of one group are summed before the complex multiply).  The
-// coefficient table in shared memory holds +c_g and -c_g so that an entry's
-// sign selects its coefficient directly.
+// are staged in shared memory transposed, tile[d*NR + r], with one extra zero
+// column (index dim_dn) that padding entries point to.  Threads own columns
+// d = c0 + tid + k*blockDim (k < CPT) of every chunk c0, so the 32 lanes of a
+// warp cover one aligned tile of 32 columns.
+//  * T_dn (within a row) walks the warp-tiled ELL of the down table: for each
+//    bond group the 32 lanes read one coalesced slot of entries at a time (the
+//    trip count is uniform over the warp), gather the NR row values of the
+//    source column from the tile, sum them with their signs and multiply by
+//    the group coefficient once.
+//  * T_up (across rows) walks the group segments of row u, uniform over the
+//    block; each entry is a coalesced load of the source row along d.
+#ifndef ED_APPLY_MINB
+#define ED_APPLY_MINB 1
+#endif
 template <typename R, int NR, int CPT>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, ED_APPLY_MINB)
 k_apply(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -136,22 +141,17 @@ k_apply(BatchArgs a, int j) {
   const int dim_dn = sd.dim_dn;
   const int u0 = ab.row0;
   const int nrows = ab.nrows;
+  const int lane = threadIdx.x & 31;
 
-  C* tile = reinterpret_cast<C*>(smem_raw);            // [max_dim_dn][NR]
-  C* coefS = tile + (size_t)a.max_dim_dn * NR;        // [2 * n_groups]
+  C* tile = reinterpret_cast<C*>(smem_raw);              // [max_dim_dn + 1][NR]
+  C* coefS = tile + (size_t)(a.max_dim_dn + 1) * NR;    // [n_groups]
 
   const void* cbase;
   if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
   else if (j == 0) cbase = a.coefs;
   else cbase = static_cast<const char*>(a.coefs_obs) + (size_t)st->step * a.n_groups * sizeof(C);
-  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) {
-    const C c = reinterpret_cast<const C*>(cbase)[g];
-    C m;
-    m.x = -c.x;
-    m.y = -c.y;
-    coefS[2 * g] = c;
-    coefS[2 * g + 1] = m;
-  }
+  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
+    coefS[g] = reinterpret_cast<const C*>(cbase)[g];
 
   const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
   const C* xp = (j >= 2) ? static_cast<const C*>(xptr(vd, j - 1, sizeof(C))) : nullptr;
@@ -160,12 +160,12 @@ k_apply(BatchArgs a, int j) {
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
 
-  // stage the NR rows, transposed
-  for (int d = threadIdx.x; d < dim_dn; d += blockDim.x) {
+  // stage the NR rows, transposed, plus the zero column
+  for (int d = threadIdx.x; d <= dim_dn; d += blockDim.x) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       C v = czero<C>();
-      if (r < nrows) v = x[(size_t)(u0 + r) * dim_dn + d];
+      if (r < nrows && d < dim_dn) v = x[(size_t)(u0 + r) * dim_dn + d];
       tile[(size_t)d * NR + r] = v;
     }
   }
@@ -181,52 +181,75 @@ k_apply(BatchArgs a, int j) {
 
   double dot_d = 0.0;
   const int chunk = blockDim.x * CPT;
+  const int warp_base = threadIdx.x - lane;
   for (int c0 = 0; c0 < dim_dn; c0 += chunk) {
     C acc[NR][CPT];
-    // diagonal + T_dn from the staged tile
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      const int d = c0 + threadIdx.x + k * blockDim.x;
+    for (int k = 0; k < CPT; ++k)
 #pragma unroll
       for (int r = 0; r < NR; ++r) acc[r][k] = czero<C>();
-      if (d < dim_dn) {
-        const uint32_t dw = __ldg(sd.dn_word + d);
-        const R de = sd.dn_eps ? (R)__ldg(sd.dn_eps + d) : (R)0;
+    // diagonal + T_dn through the warp-tiled ELL
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const R dg = U * (R)__popc(uw[r] & dw) + eu[r] + de;
-          const C xv = tile[(size_t)d * NR + r];
-          acc[r][k].x = dg * xv.x;
-          acc[r][k].y = dg * xv.y;
-        }
-        const int f0 = __ldg(sd.dn_off + d), f1 = __ldg(sd.dn_off + d + 1);
-        for (int f = f0; f < f1; ++f) {
-          const uint32_t ent = __ldg(sd.dn_ent + f);
-          const C c = coefS[((ent >> 15) & 0x1FEu) | (ent >> 31)];
-          const C* vsrc = tile + (size_t)(ent & kEntRankMask) * NR;
+    for (int k = 0; k < CPT; ++k) {
+      const int dw0 = c0 + warp_base + k * blockDim.x;   // first column of the warp tile
+      if (dw0 < dim_dn) {                                 // uniform over the warp
+        const int d = dw0 + lane;
+        if (d < dim_dn) {
+          const uint32_t dw = __ldg(sd.dn_word + d);
+          const R de = sd.dn_eps ? (R)__ldg(sd.dn_eps + d) : (R)0;
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
-            const C v = vsrc[r];
-            acc[r][k].x += c.x * v.x - c.y * v.y;
-            acc[r][k].y += c.x * v.y + c.y * v.x;
+            const R dg = U * (R)__popc(uw[r] & dw) + eu[r] + de;
+            const C xv = tile[(size_t)d * NR + r];
+            acc[r][k].x = dg * xv.x;
+            acc[r][k].y = dg * xv.y;
+          }
+        }
+        const int tw = dw0 >> 5;
+        const int s0 = __ldg(sd.dn_tseg_off + tw), s1 = __ldg(sd.dn_tseg_off + tw + 1);
+        for (int sgi = s0; sgi < s1; ++sgi) {
+          const uint32_t ts = __ldg(sd.dn_tseg + sgi);
+          const int K = (int)(ts >> 8);
+          const uint32_t* ep = sd.dn_ell + (size_t)__ldg(sd.dn_tslot + sgi) * 32 + lane;
+          C sum[NR];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) sum[r] = czero<C>();
+#pragma unroll 4
+          for (int kk = 0; kk < K; ++kk) {
+            const uint32_t ent = __ldg(ep + (size_t)kk * 32);
+            const R sg = (ent & kEntSignBit) ? (R)-1 : (R)1;
+            const C* vsrc = tile + (size_t)(ent & kEntRankMask) * NR;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              const C v = vsrc[r];
+              sum[r].x += sg * v.x;
+              sum[r].y += sg * v.y;
+            }
+          }
+          const C c = coefS[ts & 0xFFu];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            acc[r][k].x += c.x * sum[r].x - c.y * sum[r].y;
+            acc[r][k].y += c.x * sum[r].y + c.y * sum[r].x;
           }
         }
       }
     }
-    // T_up: per row, uniform entry list, grouped sums
+    // T_up: per row, group segments uniform over the block
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (r < nrows) {
         const int u = u0 + r;
-        const int e0 = __ldg(sd.up_off + u), e1 = __ldg(sd.up_off + u + 1);
-        int e = e0;
-        while (e < e1) {
-          uint32_t ent = __ldg(sd.up_ent + e);
-          const uint32_t g = (ent >> kEntGroupShift) & 0xFFu;
+        const int s0 = __ldg(sd.up_seg_off + u), s1 = __ldg(sd.up_seg_off + u + 1);
+        for (int sgi = s0; sgi < s1; ++sgi) {
+          const uint32_t sg0 = __ldg(sd.up_seg + sgi);
+          const int eb = (int)(sg0 >> 8), ee = (int)__ldg(sd.up_seg_end + sgi);
           C sum[CPT];
 #pragma unroll
           for (int k = 0; k < CPT; ++k) sum[k] = czero<C>();
-          while (true) {
+#pragma unroll 4
+          for (int e = eb; e < ee; ++e) {
+            const uint32_t ent = __ldg(sd.up_ent + e);
             const C* src = x + (size_t)(ent & kEntRankMask) * dim_dn;
             const R sg = (ent & kEntSignBit) ? (R)-1 : (R)1;
 #pragma unroll
@@ -238,12 +261,8 @@ k_apply(BatchArgs a, int j) {
                 sum[k].y += sg * v.y;
               }
             }
-            ++e;
-            if (e >= e1) break;
-            ent = __ldg(sd.up_ent + e);
-            if (((ent >> kEntGroupShift) & 0xFFu) != g) break;
           }
-          const C c = coefS[2 * g];
+          const C c = coefS[sg0 & 0xFFu];
 #pragma unroll
           for (int k = 0; k < CPT; ++k) {
             acc[r][k].x += c.x * sum[k].x - c.y * sum[k].y;
@@ -801,7 +820,7 @@ LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
   const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
   // rows per CTA: as many as fit in ~110 KB of shared memory (two CTAs per
   // SM), at most 4
-  int nr = (int)((110 * 1024) / ((size_t)max_dim_dn * csz));
+  int nr = (int)((110 * 1024) / ((size_t)(max_dim_dn + 1) * csz));
   if (nr > 4) nr = 4;
   if (nr == 3) nr = 2;
   if (nr < 1) nr = 1;
@@ -816,7 +835,7 @@ LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
   sh.threads = threads;
   sh.ept = cpt;
   sh.nr = nr;
-  sh.smem = ((size_t)max_dim_dn * nr + 2 * (size_t)n_groups) * csz;
+  sh.smem = ((size_t)(max_dim_dn + 1) * nr + (size_t)n_groups) * csz;
   return sh;
 }
 

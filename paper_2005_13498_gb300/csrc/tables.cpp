@@ -130,6 +130,59 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
       T.ent.push_back((e.src & 0xFFFFu) | (e.group << 16) | (e.neg << 31));
     T.off[r + 1] = (int32_t)T.ent.size();
   }
+  // row segments by group
+  T.seg_off.assign(T.dim + 1, 0);
+  for (int r = 0; r < T.dim; ++r) {
+    for (int e = T.off[r]; e < T.off[r + 1]; ++e) {
+      const uint32_t g = (T.ent[e] >> 16) & 0xFFu;
+      if (e == T.off[r] || g != ((T.ent[e - 1] >> 16) & 0xFFu)) {
+        if (e != T.off[r]) T.seg_end.push_back((uint32_t)e);
+        T.seg.push_back(g | ((uint32_t)e << 8));
+      }
+    }
+    if (T.off[r + 1] > T.off[r]) T.seg_end.push_back((uint32_t)T.off[r + 1]);
+    T.seg_off[r + 1] = (int32_t)T.seg.size();
+  }
+  // warp-tiled ELL over columns
+  const int ntile = (T.dim + 31) / 32;
+  T.tseg_off.assign(ntile + 1, 0);
+  const uint32_t pad = (uint32_t)T.dim;  // the zero column
+  for (int c = 0; c < ntile; ++c) {
+    int maxg = -1;
+    for (int l = 0; l < 32; ++l) {
+      const int d = c * 32 + l;
+      if (d >= T.dim) break;
+      if (T.off[d + 1] > T.off[d]) maxg = std::max(maxg, (int)((T.ent[T.off[d + 1] - 1] >> 16) & 0xFFu));
+    }
+    for (int g = 0; g <= maxg; ++g) {
+      int K = 0;
+      std::vector<int> first(32, -1), cnt(32, 0);
+      for (int l = 0; l < 32; ++l) {
+        const int d = c * 32 + l;
+        if (d >= T.dim) continue;
+        for (int e = T.off[d]; e < T.off[d + 1]; ++e)
+          if ((int)((T.ent[e] >> 16) & 0xFFu) == g) {
+            if (first[l] < 0) first[l] = e;
+            ++cnt[l];
+          }
+        K = std::max(K, cnt[l]);
+      }
+      if (K == 0) continue;
+      const int slot0 = (int)(T.ell.size() / 32);
+      T.tseg.push_back((uint32_t)g | ((uint32_t)K << 8));
+      T.tslot.push_back(slot0);
+      for (int k = 0; k < K; ++k)
+        for (int l = 0; l < 32; ++l) {
+          uint32_t v = pad;
+          if (k < cnt[l]) {
+            const uint32_t e = T.ent[first[l] + k];
+            v = (e & 0xFFFFu) | (e & 0x80000000u);
+          }
+          T.ell.push_back(v);
+        }
+    }
+    T.tseg_off[c + 1] = (int32_t)T.tseg.size();
+  }
   if (L.has_eps) {
     T.eps_sum.resize(T.dim);
     for (int r = 0; r < T.dim; ++r) {

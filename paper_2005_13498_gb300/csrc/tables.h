@@ -45,6 +45,21 @@ struct SpinTable {
   std::vector<int32_t> off;
   std::vector<uint32_t> ent;
   std::vector<double> eps_sum;   // per state: sum of eps over occupied sites
+  // Row segments (used for the across-row gathers): for row r the entries of
+  // group g occupy [seg_begin, seg_end); seg[s] = g | begin << 8 (begin is the
+  // entry index, < 2^24), segments of row r are seg_off[r]..seg_off[r+1].
+  std::vector<int32_t> seg_off;
+  std::vector<uint32_t> seg;     // packed (group, begin); end = next begin or off[r+1]
+  std::vector<uint32_t> seg_end;
+  // Warp-tiled ELL (used for the within-row gathers): columns in tiles of 32;
+  // tile c has segments tseg_off[c]..tseg_off[c+1], tseg[s] = (group, K, slot0)
+  // packed as group | K << 8 and slot0 in tslot[s]; slot k of segment s holds
+  // the entries of the 32 columns at ell[(slot0 + k) * 32 + lane], padded with
+  // (rank = dim, sign 0), i.e. a zero column.
+  std::vector<int32_t> tseg_off;
+  std::vector<uint32_t> tseg;
+  std::vector<int32_t> tslot;
+  std::vector<uint32_t> ell;
 };
 SpinTable build_spin_table(const LatticeHost& L, int n);
 
