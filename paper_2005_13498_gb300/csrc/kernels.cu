@@ -123,7 +123,7 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 //  * T_up (across rows) walks the group segments of row u, uniform over the
 //    block; each entry is a coalesced load of the source row along d.
 #ifndef ED_APPLY_MINB
-#define ED_APPLY_MINB 1
+#define ED_APPLY_MINB 2
 #endif
 template <typename R, int NR, int CPT>
 __global__ void __launch_bounds__(512, ED_APPLY_MINB)
@@ -315,7 +315,9 @@ k_apply(BatchArgs a, int j) {
 
 // ------------------------------------------------------------------ update
 // x_{j+1} = w - alpha_j s_j x_j ;  beta_j = |x_{j+1}| ;  breakdown test.
-template <typename R>
+// PAIR: complex64 vectors of even length are processed two elements per
+// 16-byte access (chunk boundaries are multiples of 256 elements).
+template <typename R, bool PAIR>
 __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
   __shared__ double red[32];
@@ -324,23 +326,51 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
   const VecDev vd = a.vec[eb.vec];
   LanczosState* st = a.st + eb.vec;
   if (st->stopped) return;
-  const C* w = static_cast<const C*>(vd.w);
-  const C* x = static_cast<const C*>(xptr(vd, j, sizeof(C)));
-  C* xn = static_cast<C*>(const_cast<void*>(xptr(vd, j + 1, sizeof(C))));
   const R as = (R)(st->alpha[j] * st->inv_scale[j]);
   double nrm_d = 0.0;
-  R nrm = (R)0;
-  int cnt = 0;
-  for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
-    const C wv = w[i], xv = x[i];
-    C o;
-    o.x = wv.x - as * xv.x;
-    o.y = wv.y - as * xv.y;
-    xn[i] = o;
-    nrm += o.x * o.x + o.y * o.y;
-    if (++cnt == 8) { nrm_d += (double)nrm; nrm = (R)0; cnt = 0; }
+  const void* pw = vd.w;
+  const void* px = xptr(vd, j, sizeof(C));
+  const void* pxn = xptr(vd, j + 1, sizeof(C));
+  const bool aligned = (((uintptr_t)pw | (uintptr_t)px | (uintptr_t)pxn) & 15u) == 0;
+  if (PAIR && aligned && (eb.begin & 1) == 0 && (eb.end & 1) == 0) {
+    const float4* w = static_cast<const float4*>(pw);
+    const float4* x = static_cast<const float4*>(px);
+    float4* xn = static_cast<float4*>(const_cast<void*>(pxn));
+    const int64_t b2 = eb.begin >> 1, e2 = eb.end >> 1;
+    float nrm = 0.f;
+    int cnt = 0;
+#pragma unroll 2
+    for (int64_t i = b2 + threadIdx.x; i < e2; i += blockDim.x) {
+      const float4 wv = w[i], xv = x[i];
+      float4 o;
+      o.x = wv.x - (float)as * xv.x;
+      o.y = wv.y - (float)as * xv.y;
+      o.z = wv.z - (float)as * xv.z;
+      o.w = wv.w - (float)as * xv.w;
+      xn[i] = o;
+      nrm += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+      if (++cnt == 4) { nrm_d += (double)nrm; nrm = 0.f; cnt = 0; }
+    }
+    nrm_d += (double)nrm;
+  } else {
+    const C* w = static_cast<const C*>(vd.w);
+    const C* x = static_cast<const C*>(xptr(vd, j, sizeof(C)));
+    C* xn = static_cast<C*>(const_cast<void*>(xptr(vd, j + 1, sizeof(C))));
+    R nrm = (R)0;
+    int cnt = 0;
+#pragma unroll 2
+    for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
+      const C wv = w[i], xv = x[i];
+      C o;
+      o.x = wv.x - as * xv.x;
+      o.y = wv.y - as * xv.y;
+      xn[i] = o;
+      nrm += o.x * o.x + o.y * o.y;
+      if (++cnt == 8) { nrm_d += (double)nrm; nrm = (R)0; cnt = 0; }
+    }
+    nrm_d += (double)nrm;
   }
-  double v[1] = {nrm_d + (double)nrm};
+  double v[1] = {nrm_d};
   if (reduce_last_block<1>(v, blockIdx.x, vd.ew_begin, vd.ew_end, a.partials,
                            a.counters + eb.vec, red, &flag)) {
     if (threadIdx.x == 0) {
@@ -524,6 +554,7 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
       const C x = x1[i];
       p.x = cf_lo.x * x.x - cf_lo.y * x.y;
       p.y = cf_lo.x * x.y + cf_lo.y * x.x;
+#pragma unroll 4
       for (int jj = 1; jj < n; ++jj) {
         const C v = V[(size_t)(jj - 1) * vd.D + i];
         const C c = cf[jj];
@@ -880,8 +911,8 @@ cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchSh
 }
 
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int nblk, int j, cudaStream_t s) {
-  if (fp64) k_update<double><<<nblk, 256, 0, s>>>(a, j);
-  else k_update<float><<<nblk, 256, 0, s>>>(a, j);
+  if (fp64) k_update<double, false><<<nblk, 256, 0, s>>>(a, j);
+  else k_update<float, true><<<nblk, 256, 0, s>>>(a, j);
   return cudaGetLastError();
 }
 

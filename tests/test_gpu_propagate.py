@@ -19,8 +19,9 @@ def run_gpu(ed, torch, lat, nu, nd, U, psi0, pulse, dt, n, m, dtype, energy=Fals
             host=False, profile=False):
     h = ed.Hubbard(lat, nu, nd, U)
     if host:
-        x = np.ascontiguousarray(psi0, dtype=np.complex128 if dtype == "c128"
-                                 else np.complex64)
+        # a private copy: the library writes the result into this buffer
+        x = np.array(psi0, dtype=np.complex128 if dtype == "c128" else np.complex64,
+                     copy=True)
         out = ed.ed_propagate(h.ctx, x, ed_dtype(ed, dtype), pulse, 0.0, dt, n, m,
                               energy=energy, profile=profile)
         psi = x.astype(np.complex128)
