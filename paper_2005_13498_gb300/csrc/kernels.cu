@@ -516,13 +516,34 @@ __global__ void __launch_bounds__(32) k_expm(BatchArgs a) {
 // ------------------------------------------------------ combine / observe
 // psi <- sum_j comb_j x_j (in place over x_1), fused with |psi|^2 and
 // sum_k w_d[k] |psi_k|^2 (Sec. 3.5), then the per-step bookkeeping.
+// In float32 the dominant coefficient c_1 is split hi + lo and its product is
+// added last, which keeps the rounding of c_1 out of |psi| (the norm would
+// otherwise drift by ~1e-7 per step).
+template <typename R, typename C>
+__device__ __forceinline__ C combine_one(const C* cf, C cf_lo, int n, const C* V,
+                                         int64_t D, int64_t i, C x) {
+  C p;
+  p.x = cf_lo.x * x.x - cf_lo.y * x.y;
+  p.y = cf_lo.x * x.y + cf_lo.y * x.x;
+#pragma unroll 4
+  for (int jj = 1; jj < n; ++jj) {
+    const C v = V[(size_t)(jj - 1) * D + i];
+    const C c = cf[jj];
+    p.x += c.x * v.x - c.y * v.y;
+    p.y += c.x * v.y + c.y * v.x;
+  }
+  p.x += cf[0].x * x.x - cf[0].y * x.y;
+  p.y += cf[0].x * x.y + cf[0].y * x.x;
+  return p;
+}
+
 template <typename R, bool COMBINE>
 __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
   using C = typename C2T<R>::T;
   __shared__ double red[64];
   __shared__ int flag;
   __shared__ C cf[kMaxKrylov + 1];
-  __shared__ C cf_lo;   // c_1 - (R)c_1: the dominant coefficient in two parts
+  __shared__ C cf_lo;
   const EwBlock eb = a.ew_map[blockIdx.x];
   const VecDev vd = a.vec[eb.vec];
   LanczosState* st = a.st + eb.vec;
@@ -546,26 +567,10 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
   R nl = (R)0, wl = (R)0;
   int cnt = 0;
   for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
-    C p;
+    C p = x1[i];
     if (COMBINE) {
-      // small terms first, the dominant c_1 x_1 (split hi + lo) last: in
-      // float32 this keeps the rounding of c_1 out of |psi| (the norm drifts
-      // otherwise by ~1e-7 per step)
-      const C x = x1[i];
-      p.x = cf_lo.x * x.x - cf_lo.y * x.y;
-      p.y = cf_lo.x * x.y + cf_lo.y * x.x;
-#pragma unroll 4
-      for (int jj = 1; jj < n; ++jj) {
-        const C v = V[(size_t)(jj - 1) * vd.D + i];
-        const C c = cf[jj];
-        p.x += c.x * v.x - c.y * v.y;
-        p.y += c.x * v.y + c.y * v.x;
-      }
-      p.x += cf[0].x * x.x - cf[0].y * x.y;
-      p.y += cf[0].x * x.y + cf[0].y * x.x;
+      p = combine_one<R, C>(cf, cf_lo, n, V, vd.D, i, p);
       x1[i] = p;
-    } else {
-      p = x1[i];
     }
     const int u = (int)(i / dim_dn);
     const int d = (int)(i - (int64_t)u * dim_dn);
