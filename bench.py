@@ -43,6 +43,8 @@ def parse():
                     help="only the headline timing (for profiler launch lists)")
     ap.add_argument("--random-start", action="store_true",
                     help="start from a seeded random state instead of the ground state")
+    ap.add_argument("--apply-only", choices=["c64", "c128"], default=None,
+                    help="run 4 plain applies at the bench size and exit (profiler target)")
     return ap.parse_args()
 
 
@@ -206,6 +208,19 @@ def main():
     lat = synth.lattice_from_name(w["lattice"])
     pulse = w["pulse_params"]
     dt, m = w["dt"], w["m"]
+    if args.apply_only:
+        h = ed.Hubbard(lat, w["n_up"], w["n_dn"], w["U"])
+        ed.ed_set_field(h.ctx, [0.3, 0.0, 0.0])
+        tt, code = ((torch.complex64, ed.ED_C64) if args.apply_only == "c64"
+                    else (torch.complex128, ed.ED_C128))
+        v = torch.from_numpy(synth.complex_normal(h.D, 0)).to(tt).cuda()
+        wv = torch.zeros_like(v)
+        for _ in range(4):
+            ed.ed_apply_H(h.ctx, v, wv, code)
+        torch.cuda.synchronize()
+        print(json.dumps({"apply_only": args.apply_only, "D": h.D}))
+        h.close()
+        return
     t_start = pulse["t0"] - 1.0        # inside the pulse: full Krylov dimension
     h = ed.Hubbard(lat, w["n_up"], w["n_dn"], w["U"])
     D = h.D

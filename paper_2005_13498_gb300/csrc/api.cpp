@@ -284,6 +284,8 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     P.args.Ns = ctx->Ns;
     P.args.max_dim_dn = (int)ctx->dim_dn;
     P.args.U = ctx->lat.U;
+    P.shape.vec = !fp64 && (ctx->dim_dn % 2 == 0) &&
+                  ((((uintptr_t)v) | ((uintptr_t)w)) & 15u) == 0;
     CK(ctx, prepare_apply(fp64, P.shape));
     P.nblk = (int)amap.size();
     P.nvec = nvec;

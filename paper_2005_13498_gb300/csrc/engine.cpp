@@ -137,6 +137,12 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   }
   n_apply_ = (int)amap.size();
   n_ew_ = (int)emap.size();
+  // 16-byte pair accesses for complex64 when every row and buffer allows it
+  shape_.vec = !cfg.fp64;
+  for (int i = 0; i < nv; ++i) {
+    if (sectors_[vecs_[i].sector].dim_dn & 1) shape_.vec = false;
+    if (((uintptr_t)vd[i].x1 | (uintptr_t)vd[i].V | (uintptr_t)vd[i].w) & 15u) shape_.vec = false;
+  }
   ED_TRY(prepare_apply(cfg.fp64, shape_));
 
   ED_TRY(d_sec_.alloc(sizeof(SectorDev) * sectors_.size()));

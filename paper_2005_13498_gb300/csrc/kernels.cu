@@ -125,10 +125,59 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 #ifndef ED_APPLY_MINB
 #define ED_APPLY_MINB 2
 #endif
-template <typename R, int NR, int CPT>
-__global__ void __launch_bounds__(512, ED_APPLY_MINB)
+constexpr int kApplyThreads = 256;
+
+// Column pair (2p, 2p+1) of a row: one 16-byte access for aligned complex64
+// rows (VEC), else two element accesses with the second column checked.
+template <typename C, bool VEC>
+__device__ __forceinline__ void load_pair(const C* row, int p, int dim, C& v0, C& v1) {
+  if constexpr (VEC) {
+    const float4 f = __ldg(reinterpret_cast<const float4*>(row) + p);
+    v0.x = f.x; v0.y = f.y; v1.x = f.z; v1.y = f.w;
+  } else {
+    const int d = 2 * p;
+    v0 = row[d];
+    if (d + 1 < dim) v1 = row[d + 1]; else v1 = czero<C>();
+  }
+}
+template <typename C, bool VEC>
+__device__ __forceinline__ void store_pair(C* row, int p, int dim, C v0, C v1) {
+  if constexpr (VEC) {
+    reinterpret_cast<float4*>(row)[p] = make_float4(v0.x, v0.y, v1.x, v1.y);
+  } else {
+    const int d = 2 * p;
+    row[d] = v0;
+    if (d + 1 < dim) row[d + 1] = v1;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R sign_of(uint32_t ent) {
+  // +1 or -1 from bit 31
+  if constexpr (sizeof(R) == 4) return __int_as_float((int)((ent & 0x80000000u) | 0x3f800000u));
+  else return (ent & 0x80000000u) ? -1.0 : 1.0;
+}
+
+// One CTA (256 threads) processes NR consecutive rows u0..u0+NR-1 of one
+// vector.  The rows are staged in shared memory transposed, tile[d*NR + r],
+// followed by two zero columns that padding entries point to.  Thread t owns
+// the column pairs p = pc + t + k*256 (k < PP) of every chunk pc, so a warp
+// covers 64 consecutive columns.
+//  * Diagonal: U * popcount(up & dn) (+ on-site energies).
+//  * T_dn (within a row): the warp walks the 64-column ELL tile of the down
+//    table group by group (uniform trip counts), each lane loading the two
+//    entries of its columns per slot, gathering the NR row values of each
+//    source column from the tile, summing them with their signs and
+//    multiplying by the group coefficient once.
+//  * T_up (across rows): the group segments of row u are uniform over the
+//    block; each entry is one coalesced pair load of the source row per k.
+//  * Epilogue: w = s_j acc - beta_{j-1} s_{j-1} x_{j-1}, stored in pairs,
+//    and the partial of Re<x_j, w>.
+template <typename R, int NR, int PP, bool VEC>
+__global__ void __launch_bounds__(kApplyThreads, ED_APPLY_MINB)
 k_apply(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
+  constexpr int T = kApplyThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32 * 2];
   __shared__ int flag;
@@ -139,19 +188,20 @@ k_apply(BatchArgs a, int j) {
   if (j >= 1 && st->stopped) return;   // uniform over the vector's blocks
   const SectorDev sd = a.sec[vd.sector];
   const int dim_dn = sd.dim_dn;
+  const int npairs = (dim_dn + 1) >> 1;
   const int u0 = ab.row0;
   const int nrows = ab.nrows;
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
 
-  C* tile = reinterpret_cast<C*>(smem_raw);              // [max_dim_dn + 1][NR]
-  C* coefS = tile + (size_t)(a.max_dim_dn + 1) * NR;    // [n_groups]
+  C* tile = reinterpret_cast<C*>(smem_raw);              // [max_dim_dn + 2][NR]
+  C* coefS = tile + (size_t)(a.max_dim_dn + 2) * NR;    // [n_groups]
 
   const void* cbase;
   if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
   else if (j == 0) cbase = a.coefs;
   else cbase = static_cast<const char*>(a.coefs_obs) + (size_t)st->step * a.n_groups * sizeof(C);
-  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
-    coefS[g] = reinterpret_cast<const C*>(cbase)[g];
+  for (int g = tid; g < a.n_groups; g += T) coefS[g] = reinterpret_cast<const C*>(cbase)[g];
 
   const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
   const C* xp = (j >= 2) ? static_cast<const C*>(xptr(vd, j - 1, sizeof(C))) : nullptr;
@@ -160,8 +210,8 @@ k_apply(BatchArgs a, int j) {
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
 
-  // stage the NR rows, transposed, plus the zero column
-  for (int d = threadIdx.x; d <= dim_dn; d += blockDim.x) {
+  // stage the NR rows transposed, plus two zero columns
+  for (int d = tid; d < dim_dn + 2; d += T) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       C v = czero<C>();
@@ -180,20 +230,14 @@ k_apply(BatchArgs a, int j) {
   __syncthreads();
 
   double dot_d = 0.0;
-  const int chunk = blockDim.x * CPT;
-  const int warp_base = threadIdx.x - lane;
-  for (int c0 = 0; c0 < dim_dn; c0 += chunk) {
-    C acc[NR][CPT];
+  for (int pc = 0; pc < npairs; pc += T * PP) {
+    C acc[NR][2 * PP];
+    // ---- diagonal
 #pragma unroll
-    for (int k = 0; k < CPT; ++k)
+    for (int k = 0; k < PP; ++k) {
 #pragma unroll
-      for (int r = 0; r < NR; ++r) acc[r][k] = czero<C>();
-    // diagonal + T_dn through the warp-tiled ELL
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      const int dw0 = c0 + warp_base + k * blockDim.x;   // first column of the warp tile
-      if (dw0 < dim_dn) {                                 // uniform over the warp
-        const int d = dw0 + lane;
+      for (int h = 0; h < 2; ++h) {
+        const int d = 2 * (pc + tid + k * T) + h;
         if (d < dim_dn) {
           const uint32_t dw = __ldg(sd.dn_word + d);
           const R de = sd.dn_eps ? (R)__ldg(sd.dn_eps + d) : (R)0;
@@ -201,41 +245,57 @@ k_apply(BatchArgs a, int j) {
           for (int r = 0; r < NR; ++r) {
             const R dg = U * (R)__popc(uw[r] & dw) + eu[r] + de;
             const C xv = tile[(size_t)d * NR + r];
-            acc[r][k].x = dg * xv.x;
-            acc[r][k].y = dg * xv.y;
+            acc[r][2 * k + h].x = dg * xv.x;
+            acc[r][2 * k + h].y = dg * xv.y;
           }
+        } else {
+#pragma unroll
+          for (int r = 0; r < NR; ++r) acc[r][2 * k + h] = czero<C>();
         }
-        const int tw = dw0 >> 5;
+      }
+    }
+    // ---- T_dn through the 64-column ELL tiles
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+      const int pw0 = pc + (tid - lane) + k * T;     // first pair of the warp
+      if (pw0 < npairs) {                             // uniform over the warp
+        const int tw = pw0 >> 5;
         const int s0 = __ldg(sd.dn_tseg_off + tw), s1 = __ldg(sd.dn_tseg_off + tw + 1);
         for (int sgi = s0; sgi < s1; ++sgi) {
           const uint32_t ts = __ldg(sd.dn_tseg + sgi);
           const int K = (int)(ts >> 8);
-          const uint32_t* ep = sd.dn_ell + (size_t)__ldg(sd.dn_tslot + sgi) * 32 + lane;
-          C sum[NR];
+          const uint2* ep = reinterpret_cast<const uint2*>(sd.dn_ell) +
+                            (size_t)__ldg(sd.dn_tslot + sgi) * 32 + lane;
+          C s0v[NR], s1v[NR];
 #pragma unroll
-          for (int r = 0; r < NR; ++r) sum[r] = czero<C>();
-#pragma unroll 4
+          for (int r = 0; r < NR; ++r) { s0v[r] = czero<C>(); s1v[r] = czero<C>(); }
+#pragma unroll 2
           for (int kk = 0; kk < K; ++kk) {
-            const uint32_t ent = __ldg(ep + (size_t)kk * 32);
-            const R sg = (ent & kEntSignBit) ? (R)-1 : (R)1;
-            const C* vsrc = tile + (size_t)(ent & kEntRankMask) * NR;
+            const uint2 e = __ldg(ep + (size_t)kk * 32);
+            const R g0 = sign_of<R>(e.x), g1 = sign_of<R>(e.y);
+            const C* v0 = tile + (size_t)(e.x & kEntRankMask) * NR;
+            const C* v1 = tile + (size_t)(e.y & kEntRankMask) * NR;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-              const C v = vsrc[r];
-              sum[r].x += sg * v.x;
-              sum[r].y += sg * v.y;
+              const C a0 = v0[r], a1 = v1[r];
+              s0v[r].x += g0 * a0.x;
+              s0v[r].y += g0 * a0.y;
+              s1v[r].x += g1 * a1.x;
+              s1v[r].y += g1 * a1.y;
             }
           }
           const C c = coefS[ts & 0xFFu];
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
-            acc[r][k].x += c.x * sum[r].x - c.y * sum[r].y;
-            acc[r][k].y += c.x * sum[r].y + c.y * sum[r].x;
+            acc[r][2 * k].x += c.x * s0v[r].x - c.y * s0v[r].y;
+            acc[r][2 * k].y += c.x * s0v[r].y + c.y * s0v[r].x;
+            acc[r][2 * k + 1].x += c.x * s1v[r].x - c.y * s1v[r].y;
+            acc[r][2 * k + 1].y += c.x * s1v[r].y + c.y * s1v[r].x;
           }
         }
       }
     }
-    // T_up: per row, group segments uniform over the block
+    // ---- T_up: group segments of each row, uniform over the block
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (r < nrows) {
@@ -244,54 +304,63 @@ k_apply(BatchArgs a, int j) {
         for (int sgi = s0; sgi < s1; ++sgi) {
           const uint32_t sg0 = __ldg(sd.up_seg + sgi);
           const int eb = (int)(sg0 >> 8), ee = (int)__ldg(sd.up_seg_end + sgi);
-          C sum[CPT];
+          C sum[2 * PP];
 #pragma unroll
-          for (int k = 0; k < CPT; ++k) sum[k] = czero<C>();
-#pragma unroll 4
+          for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
+#pragma unroll 2
           for (int e = eb; e < ee; ++e) {
             const uint32_t ent = __ldg(sd.up_ent + e);
+            const R g = sign_of<R>(ent);
             const C* src = x + (size_t)(ent & kEntRankMask) * dim_dn;
-            const R sg = (ent & kEntSignBit) ? (R)-1 : (R)1;
 #pragma unroll
-            for (int k = 0; k < CPT; ++k) {
-              const int d = c0 + threadIdx.x + k * blockDim.x;
-              if (d < dim_dn) {
-                const C v = src[d];
-                sum[k].x += sg * v.x;
-                sum[k].y += sg * v.y;
+            for (int k = 0; k < PP; ++k) {
+              const int p = pc + tid + k * T;
+              if (p < npairs) {
+                C v0, v1;
+                load_pair<C, VEC>(src, p, dim_dn, v0, v1);
+                sum[2 * k].x += g * v0.x;
+                sum[2 * k].y += g * v0.y;
+                sum[2 * k + 1].x += g * v1.x;
+                sum[2 * k + 1].y += g * v1.y;
               }
             }
           }
           const C c = coefS[sg0 & 0xFFu];
 #pragma unroll
-          for (int k = 0; k < CPT; ++k) {
+          for (int k = 0; k < 2 * PP; ++k) {
             acc[r][k].x += c.x * sum[k].x - c.y * sum[k].y;
             acc[r][k].y += c.x * sum[k].y + c.y * sum[k].x;
           }
         }
       }
     }
-    // epilogue: scale, three-term subtraction, store, inner product
+    // ---- epilogue: scale, three-term subtraction, store, inner product
     R dot_acc = (R)0;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (r < nrows) {
         const size_t rowoff = (size_t)(u0 + r) * dim_dn;
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-          const int d = c0 + threadIdx.x + k * blockDim.x;
-          if (d < dim_dn) {
-            C o;
-            o.x = s_in * acc[r][k].x;
-            o.y = s_in * acc[r][k].y;
+        for (int k = 0; k < PP; ++k) {
+          const int p = pc + tid + k * T;
+          if (p < npairs) {
+            C o0, o1;
+            o0.x = s_in * acc[r][2 * k].x;
+            o0.y = s_in * acc[r][2 * k].y;
+            o1.x = s_in * acc[r][2 * k + 1].x;
+            o1.y = s_in * acc[r][2 * k + 1].y;
             if (xp) {
-              const C pv = xp[rowoff + d];
-              o.x -= s_prev * pv.x;
-              o.y -= s_prev * pv.y;
+              C p0, p1;
+              load_pair<C, VEC>(xp + rowoff, p, dim_dn, p0, p1);
+              o0.x -= s_prev * p0.x;
+              o0.y -= s_prev * p0.y;
+              o1.x -= s_prev * p1.x;
+              o1.y -= s_prev * p1.y;
             }
-            w[rowoff + d] = o;
-            const C xv = tile[(size_t)d * NR + r];
-            dot_acc += xv.x * o.x + xv.y * o.y;
+            store_pair<C, VEC>(w + rowoff, p, dim_dn, o0, o1);
+            const C x0 = tile[(size_t)(2 * p) * NR + r];
+            const C x1 = tile[(size_t)(2 * p + 1) * NR + r];   // zero column past the end
+            dot_acc += x0.x * o0.x + x0.y * o0.y + x1.x * o1.x + x1.y * o1.y;
           }
         }
       }
@@ -302,7 +371,7 @@ k_apply(BatchArgs a, int j) {
   double v[1] = {dot_d};
   if (reduce_last_block<1>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
                            a.partials, a.counters + ab.vec, red, &flag)) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       if (j >= 1) {
         st->alpha[j] = v[0] * st->inv_scale[j];
         if (!isfinite(v[0])) { st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1; }
@@ -856,63 +925,67 @@ LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
   const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
   // rows per CTA: as many as fit in ~110 KB of shared memory (two CTAs per
   // SM), at most 4
-  int nr = (int)((110 * 1024) / ((size_t)(max_dim_dn + 1) * csz));
+  int nr = (int)((110 * 1024) / ((size_t)(max_dim_dn + 2) * csz));
   if (nr > 4) nr = 4;
   if (nr == 3) nr = 2;
   if (nr < 1) nr = 1;
-  const int cpt = 2;
-  int nchunks = (max_dim_dn + cpt * 512 - 1) / (cpt * 512);
-  if (nchunks < 1) nchunks = 1;
-  int threads = (max_dim_dn + cpt * nchunks - 1) / (cpt * nchunks);
-  threads = ((threads + 31) / 32) * 32;
-  if (threads < 32) threads = 32;
-  if (threads > 512) threads = 512;
   LaunchShape sh;
-  sh.threads = threads;
-  sh.ept = cpt;
+  sh.threads = kApplyThreads;
+  sh.ept = fp64 ? 1 : 2;      // column pairs per thread per chunk
   sh.nr = nr;
-  sh.smem = ((size_t)(max_dim_dn + 1) * nr + (size_t)n_groups) * csz;
+  sh.smem = ((size_t)(max_dim_dn + 2) * nr + (size_t)n_groups) * csz;
   return sh;
 }
 
-template <typename R, int NR>
+template <typename R, int NR, int PP>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
-  k_apply<R, NR, 2><<<nblk, sh.threads, sh.smem, s>>>(a, j);
+  if (sh.vec) k_apply<R, NR, PP, (sizeof(R) == 4)><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
+  else k_apply<R, NR, PP, false><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, int PP>
 static cudaError_t prepare_apply_r(const LaunchShape& sh) {
   const int sm = (int)sh.smem;
+  cudaError_t e = cudaErrorInvalidValue;
   switch (sh.nr) {
-    case 1: return cudaFuncSetAttribute(k_apply<R, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    case 2: return cudaFuncSetAttribute(k_apply<R, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    case 4: return cudaFuncSetAttribute(k_apply<R, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    default: return cudaErrorInvalidValue;
+    case 1:
+      e = cudaFuncSetAttribute(k_apply<R, 1, PP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<R, 1, PP, (sizeof(R) == 4)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(k_apply<R, 2, PP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<R, 2, PP, (sizeof(R) == 4)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      break;
+    case 4:
+      e = cudaFuncSetAttribute(k_apply<R, 4, PP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<R, 4, PP, (sizeof(R) == 4)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      break;
   }
+  return e;
 }
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
   if (sh.smem > 227 * 1024) return cudaErrorInvalidValue;
-  return fp64 ? prepare_apply_r<double>(sh) : prepare_apply_r<float>(sh);
+  return fp64 ? prepare_apply_r<double, 1>(sh) : prepare_apply_r<float, 2>(sh);
 }
 
-template <typename R>
+template <typename R, int PP>
 static cudaError_t launch_apply_r(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
   switch (sh.nr) {
-    case 1: return launch_apply_t<R, 1>(a, nblk, sh, j, s);
-    case 2: return launch_apply_t<R, 2>(a, nblk, sh, j, s);
-    case 4: return launch_apply_t<R, 4>(a, nblk, sh, j, s);
+    case 1: return launch_apply_t<R, 1, PP>(a, nblk, sh, j, s);
+    case 2: return launch_apply_t<R, 2, PP>(a, nblk, sh, j, s);
+    case 4: return launch_apply_t<R, 4, PP>(a, nblk, sh, j, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
                          int j, cudaStream_t s) {
-  return fp64 ? launch_apply_r<double>(a, nblk, sh, j, s)
-              : launch_apply_r<float>(a, nblk, sh, j, s);
+  return fp64 ? launch_apply_r<double, 1>(a, nblk, sh, j, s)
+              : launch_apply_r<float, 2>(a, nblk, sh, j, s);
 }
 
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int nblk, int j, cudaStream_t s) {

@@ -15,6 +15,7 @@ struct LaunchShape {
   int ept;       // columns per thread per chunk in the apply kernel
   int nr;        // rows per CTA (apply blocks hold up to nr rows)
   size_t smem;   // dynamic shared memory of the apply kernel
+  bool vec = false;  // complex64 rows accessed as 16-byte pairs
 };
 
 // Apply blocks of nr rows covering rows [0, dim_up) of vector vec.

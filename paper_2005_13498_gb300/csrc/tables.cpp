@@ -143,22 +143,22 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
     if (T.off[r + 1] > T.off[r]) T.seg_end.push_back((uint32_t)T.off[r + 1]);
     T.seg_off[r + 1] = (int32_t)T.seg.size();
   }
-  // warp-tiled ELL over columns
-  const int ntile = (T.dim + 31) / 32;
+  // warp-tiled ELL over columns (tiles of 64, two columns per lane)
+  const int ntile = (T.dim + 63) / 64;
   T.tseg_off.assign(ntile + 1, 0);
   const uint32_t pad = (uint32_t)T.dim;  // the zero column
   for (int c = 0; c < ntile; ++c) {
     int maxg = -1;
-    for (int l = 0; l < 32; ++l) {
-      const int d = c * 32 + l;
+    for (int l = 0; l < 64; ++l) {
+      const int d = c * 64 + l;
       if (d >= T.dim) break;
       if (T.off[d + 1] > T.off[d]) maxg = std::max(maxg, (int)((T.ent[T.off[d + 1] - 1] >> 16) & 0xFFu));
     }
     for (int g = 0; g <= maxg; ++g) {
       int K = 0;
-      std::vector<int> first(32, -1), cnt(32, 0);
-      for (int l = 0; l < 32; ++l) {
-        const int d = c * 32 + l;
+      std::vector<int> first(64, -1), cnt(64, 0);
+      for (int l = 0; l < 64; ++l) {
+        const int d = c * 64 + l;
         if (d >= T.dim) continue;
         for (int e = T.off[d]; e < T.off[d + 1]; ++e)
           if ((int)((T.ent[e] >> 16) & 0xFFu) == g) {
@@ -168,11 +168,11 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
         K = std::max(K, cnt[l]);
       }
       if (K == 0) continue;
-      const int slot0 = (int)(T.ell.size() / 32);
+      const int slot0 = (int)(T.ell.size() / 64);
       T.tseg.push_back((uint32_t)g | ((uint32_t)K << 8));
       T.tslot.push_back(slot0);
       for (int k = 0; k < K; ++k)
-        for (int l = 0; l < 32; ++l) {
+        for (int l = 0; l < 64; ++l) {   // l = 2 * lane + h
           uint32_t v = pad;
           if (k < cnt[l]) {
             const uint32_t e = T.ent[first[l] + k];

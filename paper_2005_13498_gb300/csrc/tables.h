@@ -51,11 +51,13 @@ struct SpinTable {
   std::vector<int32_t> seg_off;
   std::vector<uint32_t> seg;     // packed (group, begin); end = next begin or off[r+1]
   std::vector<uint32_t> seg_end;
-  // Warp-tiled ELL (used for the within-row gathers): columns in tiles of 32;
-  // tile c has segments tseg_off[c]..tseg_off[c+1], tseg[s] = (group, K, slot0)
-  // packed as group | K << 8 and slot0 in tslot[s]; slot k of segment s holds
-  // the entries of the 32 columns at ell[(slot0 + k) * 32 + lane], padded with
-  // (rank = dim, sign 0), i.e. a zero column.
+  // Warp-tiled ELL (used for the within-row gathers): columns in tiles of 64,
+  // lane l of a warp owning columns 64c + 2l and 64c + 2l + 1.  Tile c has
+  // segments tseg_off[c]..tseg_off[c+1], tseg[s] = group | K << 8 and first
+  // slot tslot[s]; slot k of segment s holds, for lane l, the two entries
+  // (rank | sign << 31) of its columns at ell[2 * ((slot0 + k) * 32 + l)] and
+  // [.. + 1], padded with rank = dim (a zero column).  K is the largest count
+  // of that group over the 64 columns.
   std::vector<int32_t> tseg_off;
   std::vector<uint32_t> tseg;
   std::vector<int32_t> tslot;
