@@ -180,6 +180,32 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype,
 ed_status ed_double_occupation(ed_ctx* ctx, const void* psi, ed_dtype dtype,
                                double* d_avg, double* d_site);
 
+/* Double occupancy without any device allocation: the same results as
+ * ed_double_occupation (average and, if d_site is not NULL, per-site values),
+ * for callers that must not allocate device memory while they run -- for
+ * example inside a loop whose device memory is fixed up front, or in a host
+ * application that enforces its own device-memory budget.  The paper has no
+ * counterpart; this is a deployment variant of the reduction above.
+ *   - Scratch: a fixed array of 139,400 bytes inside the library (one per
+ *     device that loads it, held until the process exits) replaces the
+ *     per-call partial-sum buffers.  The sector may have at most 67,108,864
+ *     elements (dim_up * dim_dn); larger sectors are rejected with
+ *     ED_ERR_UNSUPPORTED before anything runs.
+ *   - psi must be a DEVICE pointer of `dtype`; the context's tables must
+ *     already be on the device (any earlier GPU call on this context puts them
+ *     there), else ED_ERR_STATE.  The call itself allocates nothing: no
+ *     cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call uses the same array, whose contents persist between calls;
+ *     nothing in it needs to start at zero (each call overwrites every slot
+ *     it reads).  Calls that overlap on the GPU (other streams, other host
+ *     threads) race on the array and must not be issued.
+ *   - Runs on `stream` and synchronises it before returning (the results are
+ *     host values).                                                          */
+ed_status ed_double_occupation_static(ed_ctx* ctx, const void* psi, ed_dtype dtype,
+                                      double* d_avg, double* d_site, void* stream);
+
 /* Nonequilibrium Green's functions of Eq. (15) with reference time 0
  * (Sec. 2.5, 3.7): for every site i and spin s, phi = c_is psi0 and
  * phi' = c^+_is psi0 are built in the sectors with one electron fewer / more

@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libhubbard_ed.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels.cu"]
+CU_SOURCES = ["kernels.cu", "docc_static.cu"]
 CPP_SOURCES = ["tables.cpp", "engine.cpp", "api.cpp", "drivers.cpp"]
 
 

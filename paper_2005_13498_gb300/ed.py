@@ -67,6 +67,7 @@ def _load():
         "ed_propagate": [P, P, I, ctypes.POINTER(ed_pulse), D, D, I, I,
                          ctypes.POINTER(ed_observables), P],
         "ed_double_occupation": [P, P, I, ctypes.POINTER(D), P],
+        "ed_double_occupation_static": [P, P, I, ctypes.POINTER(D), P, P],
         "ed_spectral_propagate": [P, P, I, ctypes.POINTER(ed_pulse), D, I, I,
                                   P, P, P],
         "ed_apply_fermion_op": [P, P, I, I, I, P, P, I, P],
@@ -217,6 +218,16 @@ def ed_double_occupation(ctx, psi, dtype, Ns=None):
     site = np.zeros(16)
     _check(lib.ed_double_occupation(ctx, ptr(psi), dtype, ctypes.byref(d),
                                     ptr(site)), ctx)
+    return d.value, site
+
+
+def ed_double_occupation_static(ctx, psi, dtype, stream=None):
+    """Same results as ed_double_occupation, with no device allocation
+    (scratch in a fixed library array; psi must be on the device)."""
+    d = ctypes.c_double()
+    site = np.zeros(16)
+    _check(lib.ed_double_occupation_static(ctx, ptr(psi), dtype, ctypes.byref(d),
+                                           ptr(site), stream_ptr(stream)), ctx)
     return d.value, site
 
 
