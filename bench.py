@@ -120,6 +120,24 @@ def dist_env():
     return ws, rank, local
 
 
+def job_time_ms(t_ms, ws, device="cpu"):
+    """Wall time of the whole job: the maximum over ranks of each rank's
+    timed region (every rank runs an independent replica)."""
+    if ws <= 1:
+        return float(t_ms)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(t_ms, ws, steps):
+    """ms per propagated midpoint step over the whole job: N replicas of K
+    steps each finish in the max-over-ranks time."""
+    return t_ms / (ws * steps)
+
+
 def cpu_sample(w, lat, n_iter=2, reps=1):
     """Oracle (float64: scipy sparse Kronecker operator, numpy BLAS-1) on a
     bounded sample of one midpoint step, scaled to a full step:
@@ -253,12 +271,8 @@ def main():
                               stream=stream)
         e1.record(stream)
         barrier()
-    t_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = t_ms / (ws * args.steps)
+    t_ms = job_time_ms(e0.elapsed_time(e1), ws, device="cuda")
+    value = job_value(t_ms, ws, args.steps)
     ms_step = t_ms / args.steps
     m_eff = out["m_eff"]
     gpu_launches = 1 + args.steps * (2 * m + 1)

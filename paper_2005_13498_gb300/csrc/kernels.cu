@@ -132,7 +132,7 @@ constexpr int kApplyThreads = 256;
 template <typename C, bool VEC>
 __device__ __forceinline__ void load_pair(const C* row, int p, int dim, C& v0, C& v1) {
   if constexpr (VEC) {
-    const float4 f = __ldg(reinterpret_cast<const float4*>(row) + p);
+    const float4 f = *(reinterpret_cast<const float4*>(row) + p);
     v0.x = f.x; v0.y = f.y; v1.x = f.z; v1.y = f.w;
   } else {
     const int d = 2 * p;
@@ -158,8 +158,54 @@ __device__ __forceinline__ R sign_of(uint32_t ent) {
   else return (ent & 0x80000000u) ? -1.0 : 1.0;
 }
 
+// Shared-memory tile of NR rows, stored column by column.  When the NR values
+// of a column fill two 16-byte chunks (complex64 x 4 rows, complex128 x 2
+// rows) the two chunks of column d are swapped for d mod 8 >= 4, so that the
+// chunk a lane reads for a random column lands in any of the eight 16-byte
+// bank groups (bank conflicts of random column gathers drop by about half).
+template <typename C, int NR>
+struct TileIO {
+  static constexpr int kBytes = NR * (int)sizeof(C);
+  __device__ static __forceinline__ void load(const C* tile, int d, C (&v)[NR]) {
+    if constexpr (kBytes == 32) {
+      const float4* t = reinterpret_cast<const float4*>(tile);
+      const int sw = (d >> 2) & 1;
+      const float4 a = t[2 * d + sw], b = t[2 * d + (sw ^ 1)];
+      if constexpr (sizeof(C) == 8) {
+        v[0].x = a.x; v[0].y = a.y; v[1].x = a.z; v[1].y = a.w;
+        v[2].x = b.x; v[2].y = b.y; v[3].x = b.z; v[3].y = b.w;
+      } else {
+        v[0] = *reinterpret_cast<const C*>(&a);
+        v[1] = *reinterpret_cast<const C*>(&b);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) v[r] = tile[(size_t)d * NR + r];
+    }
+  }
+  __device__ static __forceinline__ void store(C* tile, int d, const C (&v)[NR]) {
+    if constexpr (kBytes == 32) {
+      float4* t = reinterpret_cast<float4*>(tile);
+      const int sw = (d >> 2) & 1;
+      float4 a, b;
+      if constexpr (sizeof(C) == 8) {
+        a = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        b = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+      } else {
+        a = *reinterpret_cast<const float4*>(&v[0]);
+        b = *reinterpret_cast<const float4*>(&v[1]);
+      }
+      t[2 * d + sw] = a;
+      t[2 * d + (sw ^ 1)] = b;
+    } else {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) tile[(size_t)d * NR + r] = v[r];
+    }
+  }
+};
+
 // One CTA (256 threads) processes NR consecutive rows u0..u0+NR-1 of one
-// vector.  The rows are staged in shared memory transposed, tile[d*NR + r],
+// vector.  The rows are staged in shared memory column by column (TileIO),
 // followed by two zero columns that padding entries point to.  Thread t owns
 // the column pairs p = pc + t + k*256 (k < PP) of every chunk pc, so a warp
 // covers 64 consecutive columns.
@@ -170,13 +216,15 @@ __device__ __forceinline__ R sign_of(uint32_t ent) {
 //    source column from the tile, summing them with their signs and
 //    multiplying by the group coefficient once.
 //  * T_up (across rows): the group segments of row u are uniform over the
-//    block; each entry is one coalesced pair load of the source row per k.
+//    block; each entry is one coalesced pair load of the source row per k,
+//    four entries in flight.
 //  * Epilogue: w = s_j acc - beta_{j-1} s_{j-1} x_{j-1}, stored in pairs,
 //    and the partial of Re<x_j, w>.
 template <typename R, int NR, int PP, bool VEC>
 __global__ void __launch_bounds__(kApplyThreads, ED_APPLY_MINB)
 k_apply(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
+  using TIO = TileIO<C, NR>;
   constexpr int T = kApplyThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32 * 2];
@@ -210,13 +258,32 @@ k_apply(BatchArgs a, int j) {
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
 
-  // stage the NR rows transposed, plus two zero columns
-  for (int d = tid; d < dim_dn + 2; d += T) {
+  // ---- stage the NR rows column by column (pairs of columns per thread,
+  // all NR row loads of two pairs in flight), plus two zero columns
+  {
+    const int np2 = npairs + 1;   // one extra pair: the zero columns
+#pragma unroll 2
+    for (int p = tid; p < np2; p += T) {
+      C va[NR], vb[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      C v = czero<C>();
-      if (r < nrows && d < dim_dn) v = x[(size_t)(u0 + r) * dim_dn + d];
-      tile[(size_t)d * NR + r] = v;
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrows && p < npairs) {
+          load_pair<C, VEC>(x + (size_t)(u0 + r) * dim_dn, p, dim_dn, va[r], vb[r]);
+        } else {
+          va[r] = czero<C>();
+          vb[r] = czero<C>();
+        }
+      }
+      int d = 2 * p;
+      if (p == npairs) d = dim_dn;              // zero columns dim_dn, dim_dn + 1
+      TIO::store(tile, d, va);
+      TIO::store(tile, d + 1, (p < npairs && 2 * p + 1 < dim_dn) ? vb : va);
+      if (p < npairs && 2 * p + 1 >= dim_dn) {  // odd dim: the pair's 2nd column is dim_dn
+        C z[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) z[r] = czero<C>();
+        TIO::store(tile, d + 1, z);
+      }
     }
   }
   uint32_t uw[NR];
@@ -241,12 +308,13 @@ k_apply(BatchArgs a, int j) {
         if (d < dim_dn) {
           const uint32_t dw = __ldg(sd.dn_word + d);
           const R de = sd.dn_eps ? (R)__ldg(sd.dn_eps + d) : (R)0;
+          C xv[NR];
+          TIO::load(tile, d, xv);
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             const R dg = U * (R)__popc(uw[r] & dw) + eu[r] + de;
-            const C xv = tile[(size_t)d * NR + r];
-            acc[r][2 * k + h].x = dg * xv.x;
-            acc[r][2 * k + h].y = dg * xv.y;
+            acc[r][2 * k + h].x = dg * xv[r].x;
+            acc[r][2 * k + h].y = dg * xv[r].y;
           }
         } else {
 #pragma unroll
@@ -273,15 +341,15 @@ k_apply(BatchArgs a, int j) {
           for (int kk = 0; kk < K; ++kk) {
             const uint2 e = __ldg(ep + (size_t)kk * 32);
             const R g0 = sign_of<R>(e.x), g1 = sign_of<R>(e.y);
-            const C* v0 = tile + (size_t)(e.x & kEntRankMask) * NR;
-            const C* v1 = tile + (size_t)(e.y & kEntRankMask) * NR;
+            C a0[NR], a1[NR];
+            TIO::load(tile, (int)(e.x & kEntRankMask), a0);
+            TIO::load(tile, (int)(e.y & kEntRankMask), a1);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-              const C a0 = v0[r], a1 = v1[r];
-              s0v[r].x += g0 * a0.x;
-              s0v[r].y += g0 * a0.y;
-              s1v[r].x += g1 * a1.x;
-              s1v[r].y += g1 * a1.y;
+              s0v[r].x += g0 * a0[r].x;
+              s0v[r].y += g0 * a0[r].y;
+              s1v[r].x += g1 * a1[r].x;
+              s1v[r].y += g1 * a1[r].y;
             }
           }
           const C c = coefS[ts & 0xFFu];
@@ -307,7 +375,7 @@ k_apply(BatchArgs a, int j) {
           C sum[2 * PP];
 #pragma unroll
           for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
-#pragma unroll 2
+#pragma unroll 4
           for (int e = eb; e < ee; ++e) {
             const uint32_t ent = __ldg(sd.up_ent + e);
             const R g = sign_of<R>(ent);
@@ -334,33 +402,35 @@ k_apply(BatchArgs a, int j) {
         }
       }
     }
-    // ---- epilogue: scale, three-term subtraction, store, inner product
+    // ---- epilogue: previous-vector loads first, then scale, subtract, store
+    C pv[NR][2 * PP];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int k = 0; k < PP; ++k) {
+        const int p = pc + tid + k * T;
+        if (xp && r < nrows && p < npairs)
+          load_pair<C, VEC>(xp + (size_t)(u0 + r) * dim_dn, p, dim_dn, pv[r][2 * k], pv[r][2 * k + 1]);
+        else { pv[r][2 * k] = czero<C>(); pv[r][2 * k + 1] = czero<C>(); }
+      }
     R dot_acc = (R)0;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (r < nrows) {
-        const size_t rowoff = (size_t)(u0 + r) * dim_dn;
+    for (int k = 0; k < PP; ++k) {
+      const int p = pc + tid + k * T;
+      if (p < npairs) {
+        C xa[NR], xb[NR];
+        TIO::load(tile, 2 * p, xa);
+        TIO::load(tile, 2 * p + 1, xb);    // zero column past the end
 #pragma unroll
-        for (int k = 0; k < PP; ++k) {
-          const int p = pc + tid + k * T;
-          if (p < npairs) {
+        for (int r = 0; r < NR; ++r) {
+          if (r < nrows) {
             C o0, o1;
-            o0.x = s_in * acc[r][2 * k].x;
-            o0.y = s_in * acc[r][2 * k].y;
-            o1.x = s_in * acc[r][2 * k + 1].x;
-            o1.y = s_in * acc[r][2 * k + 1].y;
-            if (xp) {
-              C p0, p1;
-              load_pair<C, VEC>(xp + rowoff, p, dim_dn, p0, p1);
-              o0.x -= s_prev * p0.x;
-              o0.y -= s_prev * p0.y;
-              o1.x -= s_prev * p1.x;
-              o1.y -= s_prev * p1.y;
-            }
-            store_pair<C, VEC>(w + rowoff, p, dim_dn, o0, o1);
-            const C x0 = tile[(size_t)(2 * p) * NR + r];
-            const C x1 = tile[(size_t)(2 * p + 1) * NR + r];   // zero column past the end
-            dot_acc += x0.x * o0.x + x0.y * o0.y + x1.x * o1.x + x1.y * o1.y;
+            o0.x = s_in * acc[r][2 * k].x - s_prev * pv[r][2 * k].x;
+            o0.y = s_in * acc[r][2 * k].y - s_prev * pv[r][2 * k].y;
+            o1.x = s_in * acc[r][2 * k + 1].x - s_prev * pv[r][2 * k + 1].x;
+            o1.y = s_in * acc[r][2 * k + 1].y - s_prev * pv[r][2 * k + 1].y;
+            store_pair<C, VEC>(w + (size_t)(u0 + r) * dim_dn, p, dim_dn, o0, o1);
+            dot_acc += xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
           }
         }
       }
