@@ -43,6 +43,8 @@ def parse():
                     help="only the headline timing (for profiler launch lists)")
     ap.add_argument("--random-start", action="store_true",
                     help="start from a seeded random state instead of the ground state")
+    ap.add_argument("--no-spectral", action="store_true")
+    ap.add_argument("--spectral-steps", type=int, default=2)
     ap.add_argument("--apply-only", choices=["c64", "c128"], default=None,
                     help="run 4 plain applies at the bench size and exit (profiler target)")
     return ap.parse_args()
@@ -173,6 +175,43 @@ def cpu_sample(w, lat, n_iter=2, reps=1):
         best = est if best is None else min(best, est)
     return best * 1e3, (f"H(t_mid) build + {n_iter} of {m} Lanczos iterations + 1 axpy, "
                         f"scaled to build + {m} iterations + {m} axpys")
+
+
+def spectral_bench(ed, torch, synth, lat, w, pulse, h, psi64, stream, barrier, steps):
+    m_spec = 20
+    t0 = pulse["t0"] - 1.0
+    gl = np.zeros(0)
+    # warm-up call builds the batch (sectors, maps, 100 GB of Krylov storage)
+    ed.ed_spectral_propagate(h.ctx, psi64, ed.ED_C64, pulse, w["dt"], 1, m_spec, 14,
+                             stream=stream)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ed.ed_spectral_propagate(h.ctx, psi64, ed.ED_C64, pulse, w["dt"], steps, m_spec, 14,
+                             stream=stream)
+    e1.record(stream)
+    barrier()
+    batched = e0.elapsed_time(e1) / steps
+    # one complex128 propagation of a c_i,up psi vector (sector (6,7)), per step
+    hs = ed.Hubbard(lat, w["n_up"] - 1, w["n_dn"], w["U"])
+    phi = torch.from_numpy(synth.complex_normal(hs.D, 5)).cuda()
+    ed.ed_propagate(hs.ctx, phi, ed.ED_C128, pulse, t0, w["dt"], 1, m_spec, stream=stream)
+    barrier()
+    e0.record(stream)
+    ed.ed_propagate(hs.ctx, phi, ed.ED_C128, pulse, t0, w["dt"], 2, m_spec, stream=stream)
+    e1.record(stream)
+    barrier()
+    one64 = e0.elapsed_time(e1) / 2
+    hs.close()
+    del gl
+    return {"workload": "Ns=14 ladder spectral batch: 56 c/c+ vectors of dim 10,306,296 + "
+                        "psi, m=20, dt=0.02",
+            "ms_per_step_batched_c64": batched, "steps": steps,
+            "ms_per_step_sequential_c128": 56 * one64,
+            "ms_per_vector_step_c128": one64,
+            "speedup_batched_c64_over_sequential_c128": 56 * one64 / batched,
+            "note": "sequential = 56 x one measured complex128 propagation step of "
+                    "a vector of the same dimension"}
 
 
 def reference_arm(args):
@@ -360,6 +399,13 @@ def main():
         fp64_ms = f0.elapsed_time(f1) / args.fp64_steps
         line["fp64"] = {"ms_per_step": fp64_ms, "steps": args.fp64_steps,
                         "speedup_c64_over_c128": fp64_ms / ms_step}
+        # spectral batch (Ns=14 ladder): c and c^+ on every site and spin of
+        # the state, 56 vectors of 3003x3432 / 3432x3003 plus psi, m=20,
+        # complex64, one batched launch per kernel; against 56 sequential
+        # complex128 propagations (one measured, times 56)
+        if not args.no_spectral:
+            line["spectral"] = spectral_bench(ed, torch, synth, lat, w, pulse, h, psi64,
+                                              stream, barrier, args.spectral_steps)
         # end to end through the C ABI with pinned host buffers: every step
         # copies psi in, propagates one step, copies psi and <d> out
         hostpsi = psi32.cpu().pin_memory()

@@ -44,12 +44,10 @@ cudaError_t upload_sector(SectorGPU& S) {
   if ((e = upload(S.dn_ent, S.dn.ent)) != cudaSuccess) return e;
   if ((e = upload(S.up_word, S.up.words)) != cudaSuccess) return e;
   if ((e = upload(S.dn_word, S.dn.words)) != cudaSuccess) return e;
-  if ((e = upload(S.up_seg_off, S.up.seg_off)) != cudaSuccess) return e;
-  if ((e = upload(S.up_seg, S.up.seg)) != cudaSuccess) return e;
-  if ((e = upload(S.up_seg_end, S.up.seg_end)) != cudaSuccess) return e;
-  if ((e = upload(S.dn_tseg_off, S.dn.tseg_off)) != cudaSuccess) return e;
-  if ((e = upload(S.dn_tseg, S.dn.tseg)) != cudaSuccess) return e;
-  if ((e = upload(S.dn_tslot, S.dn.tslot)) != cudaSuccess) return e;
+  if ((e = upload(S.up_pad_off, S.up.pad_off)) != cudaSuccess) return e;
+  if ((e = upload(S.up_pad_ent, S.up.pad_ent)) != cudaSuccess) return e;
+  if ((e = upload(S.dn_tslot_off, S.dn.tslot_off)) != cudaSuccess) return e;
+  if ((e = upload(S.dn_slot_grp, S.dn.slot_grp)) != cudaSuccess) return e;
   if ((e = upload(S.dn_ell, S.dn.ell)) != cudaSuccess) return e;
   if (S.has_eps) {
     if ((e = upload(S.up_eps, S.up.eps_sum)) != cudaSuccess) return e;
@@ -71,12 +69,10 @@ cudaError_t upload_sector(SectorGPU& S) {
   d.dn_word = static_cast<const uint32_t*>(S.dn_word.p);
   d.up_eps = S.has_eps ? static_cast<const double*>(S.up_eps.p) : nullptr;
   d.dn_eps = S.has_eps ? static_cast<const double*>(S.dn_eps.p) : nullptr;
-  d.up_seg_off = static_cast<const int32_t*>(S.up_seg_off.p);
-  d.up_seg = static_cast<const uint32_t*>(S.up_seg.p);
-  d.up_seg_end = static_cast<const uint32_t*>(S.up_seg_end.p);
-  d.dn_tseg_off = static_cast<const int32_t*>(S.dn_tseg_off.p);
-  d.dn_tseg = static_cast<const uint32_t*>(S.dn_tseg.p);
-  d.dn_tslot = static_cast<const int32_t*>(S.dn_tslot.p);
+  d.up_pad_off = static_cast<const int32_t*>(S.up_pad_off.p);
+  d.up_pad_ent = static_cast<const uint32_t*>(S.up_pad_ent.p);
+  d.dn_tslot_off = static_cast<const int32_t*>(S.dn_tslot_off.p);
+  d.dn_slot_grp = static_cast<const uint32_t*>(S.dn_slot_grp.p);
   d.dn_ell = static_cast<const uint32_t*>(S.dn_ell.p);
   S.uploaded = true;
   return cudaSuccess;
@@ -217,8 +213,8 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
   const SectorGPU& S = ctx->sec;
   int64_t b = S.up_off.bytes + S.up_ent.bytes + S.dn_off.bytes + S.dn_ent.bytes +
               S.up_word.bytes + S.dn_word.bytes + S.up_eps.bytes + S.dn_eps.bytes +
-              S.up_seg_off.bytes + S.up_seg.bytes + S.up_seg_end.bytes + S.dn_tseg_off.bytes +
-              S.dn_tseg.bytes + S.dn_tslot.bytes + S.dn_ell.bytes;
+              S.up_pad_off.bytes + S.up_pad_ent.bytes + S.dn_tslot_off.bytes +
+              S.dn_slot_grp.bytes + S.dn_ell.bytes;
   if (ctx->engine) b += ctx->engine->device_bytes();
   if (ctx->spec_engine) b += ctx->spec_engine->device_bytes();
   *bytes = b;

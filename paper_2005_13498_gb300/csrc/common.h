@@ -18,6 +18,7 @@ constexpr int kMaxGroups = 256;     // 2 * bond classes (group id is 8 bits)
 constexpr uint32_t kEntRankMask = 0xFFFFu;
 constexpr int kEntGroupShift = 16;
 constexpr uint32_t kEntSignBit = 0x80000000u;
+constexpr uint32_t kNullEntryBit = 0x40000000u;  // padding entry of a row list
 
 // Device view of one sector's tables (pointers into device memory).
 struct SectorDev {
@@ -31,15 +32,13 @@ struct SectorDev {
   const uint32_t* dn_word;  // [dim_dn]
   const double* up_eps;     // [dim_up] sum of eps over occupied sites, or null
   const double* dn_eps;     // [dim_dn]
-  // up spin: group segments of each row (across-row gathers)
-  const int32_t* up_seg_off;   // [dim_up + 1]
-  const uint32_t* up_seg;      // group | begin << 8
-  const uint32_t* up_seg_end;  // end entry index
-  // down spin: warp-tiled ELL over columns (within-row gathers)
-  const int32_t* dn_tseg_off;  // [ceil(dim_dn/32) + 1]
-  const uint32_t* dn_tseg;     // group | K << 8
-  const int32_t* dn_tslot;     // first slot of the segment
-  const uint32_t* dn_ell;      // [slots][32]: rank | sign << 31, pad = dim_dn
+  // up spin: rows padded to multiples of 4 entries (across-row gathers)
+  const int32_t* up_pad_off;   // [dim_up + 1]
+  const uint32_t* up_pad_ent;  // entries; bit 30 = null (contributes zero)
+  // down spin: warp-tiled ELL over 64-column tiles (within-row gathers)
+  const int32_t* dn_tslot_off; // [ceil(dim_dn/64) + 1], even slot counts
+  const uint32_t* dn_slot_grp; // group of each slot
+  const uint32_t* dn_ell;      // [slots][32 lanes][2]: rank | sign << 31, pad = dim_dn
 };
 
 // Per-vector Lanczos scalars, all float64, 1-based Krylov index j.

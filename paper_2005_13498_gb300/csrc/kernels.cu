@@ -210,14 +210,15 @@ struct TileIO {
 // the column pairs p = pc + t + k*256 (k < PP) of every chunk pc, so a warp
 // covers 64 consecutive columns.
 //  * Diagonal: U * popcount(up & dn) (+ on-site energies).
-//  * T_dn (within a row): the warp walks the 64-column ELL tile of the down
-//    table group by group (uniform trip counts), each lane loading the two
-//    entries of its columns per slot, gathering the NR row values of each
-//    source column from the tile, summing them with their signs and
-//    multiplying by the group coefficient once.
-//  * T_up (across rows): the group segments of row u are uniform over the
-//    block; each entry is one coalesced pair load of the source row per k,
-//    four entries in flight.
+//  * T_dn (within a row): the warp walks the flat slot list of its 64-column
+//    ELL tile (slots grouped by bond group, trip count uniform over the
+//    warp), each lane loading the two entries of its columns per slot and
+//    gathering the NR row values of each source column from the tile; the
+//    signed values of a group are summed and multiplied by the group
+//    coefficient once.
+//  * T_up (across rows): the padded entry list of row u is uniform over the
+//    block; four entries at a time, each a coalesced pair load of the source
+//    row per k, all in flight before they are summed by group.
 //  * Epilogue: w = s_j acc - beta_{j-1} s_{j-1} x_{j-1}, stored in pairs,
 //    and the partial of Re<x_j, w>.
 template <typename R, int NR, int PP, bool VEC>
@@ -322,37 +323,60 @@ k_apply(BatchArgs a, int j) {
         }
       }
     }
-    // ---- T_dn through the 64-column ELL tiles
+    // ---- T_dn through the 64-column ELL tiles: flat slot list (grouped by
+    // bond group, uniform over the warp), two slots of entries and their
+    // tile gathers in flight, coefficient applied when the group changes
 #pragma unroll
     for (int k = 0; k < PP; ++k) {
       const int pw0 = pc + (tid - lane) + k * T;     // first pair of the warp
       if (pw0 < npairs) {                             // uniform over the warp
         const int tw = pw0 >> 5;
-        const int s0 = __ldg(sd.dn_tseg_off + tw), s1 = __ldg(sd.dn_tseg_off + tw + 1);
-        for (int sgi = s0; sgi < s1; ++sgi) {
-          const uint32_t ts = __ldg(sd.dn_tseg + sgi);
-          const int K = (int)(ts >> 8);
-          const uint2* ep = reinterpret_cast<const uint2*>(sd.dn_ell) +
-                            (size_t)__ldg(sd.dn_tslot + sgi) * 32 + lane;
-          C s0v[NR], s1v[NR];
+        const int q0 = __ldg(sd.dn_tslot_off + tw), q1 = __ldg(sd.dn_tslot_off + tw + 1);
+        const uint2* ell2 = reinterpret_cast<const uint2*>(sd.dn_ell);
+        C s0v[NR], s1v[NR];
 #pragma unroll
-          for (int r = 0; r < NR; ++r) { s0v[r] = czero<C>(); s1v[r] = czero<C>(); }
-#pragma unroll 2
-          for (int kk = 0; kk < K; ++kk) {
-            const uint2 e = __ldg(ep + (size_t)kk * 32);
+        for (int r = 0; r < NR; ++r) { s0v[r] = czero<C>(); s1v[r] = czero<C>(); }
+        uint32_t gcur = q0 < q1 ? __ldg(sd.dn_slot_grp + q0) : 0u;
+        for (int q = q0; q < q1; q += 2) {
+          const uint2 ea = __ldg(ell2 + (size_t)q * 32 + lane);
+          const uint2 eb = __ldg(ell2 + (size_t)(q + 1) * 32 + lane);
+          const uint32_t ga = __ldg(sd.dn_slot_grp + q), gb = __ldg(sd.dn_slot_grp + q + 1);
+          C a0[NR], a1[NR], b0[NR], b1[NR];
+          TIO::load(tile, (int)(ea.x & kEntRankMask), a0);
+          TIO::load(tile, (int)(ea.y & kEntRankMask), a1);
+          TIO::load(tile, (int)(eb.x & kEntRankMask), b0);
+          TIO::load(tile, (int)(eb.y & kEntRankMask), b1);
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const uint32_t g = half ? gb : ga;
+            if (g != gcur) {                            // uniform over the warp
+              const C c = coefS[gcur];
+#pragma unroll
+              for (int r = 0; r < NR; ++r) {
+                acc[r][2 * k].x += c.x * s0v[r].x - c.y * s0v[r].y;
+                acc[r][2 * k].y += c.x * s0v[r].y + c.y * s0v[r].x;
+                acc[r][2 * k + 1].x += c.x * s1v[r].x - c.y * s1v[r].y;
+                acc[r][2 * k + 1].y += c.x * s1v[r].y + c.y * s1v[r].x;
+                s0v[r] = czero<C>();
+                s1v[r] = czero<C>();
+              }
+              gcur = g;
+            }
+            const uint2 e = half ? eb : ea;
             const R g0 = sign_of<R>(e.x), g1 = sign_of<R>(e.y);
-            C a0[NR], a1[NR];
-            TIO::load(tile, (int)(e.x & kEntRankMask), a0);
-            TIO::load(tile, (int)(e.y & kEntRankMask), a1);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-              s0v[r].x += g0 * a0[r].x;
-              s0v[r].y += g0 * a0[r].y;
-              s1v[r].x += g1 * a1[r].x;
-              s1v[r].y += g1 * a1[r].y;
+              const C v0 = half ? b0[r] : a0[r];
+              const C v1 = half ? b1[r] : a1[r];
+              s0v[r].x += g0 * v0.x;
+              s0v[r].y += g0 * v0.y;
+              s1v[r].x += g1 * v1.x;
+              s1v[r].y += g1 * v1.y;
             }
           }
-          const C c = coefS[ts & 0xFFu];
+        }
+        if (q0 < q1) {
+          const C c = coefS[gcur];
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             acc[r][2 * k].x += c.x * s0v[r].x - c.y * s0v[r].y;
@@ -363,37 +387,55 @@ k_apply(BatchArgs a, int j) {
         }
       }
     }
-    // ---- T_up: group segments of each row, uniform over the block
+    // ---- T_up: the padded entry list of each row (uniform over the block),
+    // four entries per batch with all their row loads in flight, coefficient
+    // applied when the group changes
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (r < nrows) {
         const int u = u0 + r;
-        const int s0 = __ldg(sd.up_seg_off + u), s1 = __ldg(sd.up_seg_off + u + 1);
-        for (int sgi = s0; sgi < s1; ++sgi) {
-          const uint32_t sg0 = __ldg(sd.up_seg + sgi);
-          const int eb = (int)(sg0 >> 8), ee = (int)__ldg(sd.up_seg_end + sgi);
-          C sum[2 * PP];
+        const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
+        C sum[2 * PP];
 #pragma unroll
-          for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
-#pragma unroll 4
-          for (int e = eb; e < ee; ++e) {
-            const uint32_t ent = __ldg(sd.up_ent + e);
-            const R g = sign_of<R>(ent);
-            const C* src = x + (size_t)(ent & kEntRankMask) * dim_dn;
+        for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
+        uint32_t gcur = e0 < e1 ? ((__ldg(sd.up_pad_ent + e0) >> kEntGroupShift) & 0xFFu) : 0u;
+        for (int e = e0; e < e1; e += 4) {
+          const uint4 ent4 = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_ent + e));
+          const uint32_t ents[4] = {ent4.x, ent4.y, ent4.z, ent4.w};
+          C v[4][2 * PP];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const C* src = x + (size_t)(ents[qq] & kEntRankMask) * dim_dn;
 #pragma unroll
             for (int k = 0; k < PP; ++k) {
               const int p = pc + tid + k * T;
-              if (p < npairs) {
-                C v0, v1;
-                load_pair<C, VEC>(src, p, dim_dn, v0, v1);
-                sum[2 * k].x += g * v0.x;
-                sum[2 * k].y += g * v0.y;
-                sum[2 * k + 1].x += g * v1.x;
-                sum[2 * k + 1].y += g * v1.y;
-              }
+              if (p < npairs) load_pair<C, VEC>(src, p, dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
+              else { v[qq][2 * k] = czero<C>(); v[qq][2 * k + 1] = czero<C>(); }
             }
           }
-          const C c = coefS[sg0 & 0xFFu];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const uint32_t g = (ents[qq] >> kEntGroupShift) & 0xFFu;
+            if (g != gcur) {                              // uniform over the block
+              const C c = coefS[gcur];
+#pragma unroll
+              for (int k = 0; k < 2 * PP; ++k) {
+                acc[r][k].x += c.x * sum[k].x - c.y * sum[k].y;
+                acc[r][k].y += c.x * sum[k].y + c.y * sum[k].x;
+                sum[k] = czero<C>();
+              }
+              gcur = g;
+            }
+            const R sg = (ents[qq] & kNullEntryBit) ? (R)0 : sign_of<R>(ents[qq]);
+#pragma unroll
+            for (int k = 0; k < 2 * PP; ++k) {
+              sum[k].x += sg * v[qq][k].x;
+              sum[k].y += sg * v[qq][k].y;
+            }
+          }
+        }
+        if (e0 < e1) {
+          const C c = coefS[gcur];
 #pragma unroll
           for (int k = 0; k < 2 * PP; ++k) {
             acc[r][k].x += c.x * sum[k].x - c.y * sum[k].y;
@@ -476,21 +518,31 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
     const float4* x = static_cast<const float4*>(px);
     float4* xn = static_cast<float4*>(const_cast<void*>(pxn));
     const int64_t b2 = eb.begin >> 1, e2 = eb.end >> 1;
-    float nrm = 0.f;
-    int cnt = 0;
-#pragma unroll 2
-    for (int64_t i = b2 + threadIdx.x; i < e2; i += blockDim.x) {
-      const float4 wv = w[i], xv = x[i];
-      float4 o;
-      o.x = wv.x - (float)as * xv.x;
-      o.y = wv.y - (float)as * xv.y;
-      o.z = wv.z - (float)as * xv.z;
-      o.w = wv.w - (float)as * xv.w;
-      xn[i] = o;
-      nrm += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
-      if (++cnt == 4) { nrm_d += (double)nrm; nrm = 0.f; cnt = 0; }
+    const float af = (float)as;
+    const int bd = blockDim.x;
+    // four pairs per thread and iteration: eight 16-byte loads in flight
+    for (int64_t i0 = b2 + threadIdx.x; i0 < e2; i0 += 4 * (int64_t)bd) {
+      float4 wv[4], xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t i = i0 + (int64_t)q * bd;
+        if (i < e2) { wv[q] = w[i]; xv[q] = x[i]; }
+        else { wv[q] = make_float4(0.f, 0.f, 0.f, 0.f); xv[q] = wv[q]; }
+      }
+      float nrm = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t i = i0 + (int64_t)q * bd;
+        float4 o;
+        o.x = wv[q].x - af * xv[q].x;
+        o.y = wv[q].y - af * xv[q].y;
+        o.z = wv[q].z - af * xv[q].z;
+        o.w = wv[q].w - af * xv[q].w;
+        if (i < e2) xn[i] = o;
+        nrm += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+      }
+      nrm_d += (double)nrm;
     }
-    nrm_d += (double)nrm;
   } else {
     const C* w = static_cast<const C*>(vd.w);
     const C* x = static_cast<const C*>(xptr(vd, j, sizeof(C)));
@@ -705,18 +757,66 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
   double nd = 0.0, wd = 0.0;
   R nl = (R)0, wl = (R)0;
   int cnt = 0;
-  for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
-    C p = x1[i];
-    if (COMBINE) {
-      p = combine_one<R, C>(cf, cf_lo, n, V, vd.D, i, p);
-      x1[i] = p;
+  const bool pairs = sizeof(R) == 4 && (dim_dn & 1) == 0 && (eb.begin & 1) == 0 &&
+                     (eb.end & 1) == 0 && (((uintptr_t)x1 | (uintptr_t)V) & 15u) == 0 &&
+                     (vd.D & 1) == 0;
+  if (pairs) {
+    // two elements (one row, since dim_dn is even) per 16-byte access; the
+    // coefficient loop keeps eight vector loads in flight
+    float4* x4 = reinterpret_cast<float4*>(x1);
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    const int64_t D2 = vd.D >> 1;
+    for (int64_t i = (eb.begin >> 1) + threadIdx.x; i < (eb.end >> 1); i += blockDim.x) {
+      float4 xv = x4[i];
+      float4 p;
+      if (COMBINE) {
+        const float2 lo = *reinterpret_cast<const float2*>(&cf_lo);
+        p.x = lo.x * xv.x - lo.y * xv.y;
+        p.y = lo.x * xv.y + lo.y * xv.x;
+        p.z = lo.x * xv.z - lo.y * xv.w;
+        p.w = lo.x * xv.w + lo.y * xv.z;
+#pragma unroll 8
+        for (int jj = 1; jj < n; ++jj) {
+          const float4 v = V4[(size_t)(jj - 1) * D2 + i];
+          const float2 c = *reinterpret_cast<const float2*>(&cf[jj]);
+          p.x += c.x * v.x - c.y * v.y;
+          p.y += c.x * v.y + c.y * v.x;
+          p.z += c.x * v.z - c.y * v.w;
+          p.w += c.x * v.w + c.y * v.z;
+        }
+        const float2 c0 = *reinterpret_cast<const float2*>(&cf[0]);
+        p.x += c0.x * xv.x - c0.y * xv.y;
+        p.y += c0.x * xv.y + c0.y * xv.x;
+        p.z += c0.x * xv.z - c0.y * xv.w;
+        p.w += c0.x * xv.w + c0.y * xv.z;
+        x4[i] = p;
+      } else {
+        p = xv;
+      }
+      const int64_t e = 2 * i;
+      const int u = (int)(e / dim_dn);
+      const int d = (int)(e - (int64_t)u * dim_dn);
+      const uint32_t uwd = __ldg(sd.up_word + u);
+      const R q0 = p.x * p.x + p.y * p.y, q1 = p.z * p.z + p.w * p.w;
+      nl += q0 + q1;
+      wl += (R)__popc(uwd & __ldg(sd.dn_word + d)) * q0 +
+            (R)__popc(uwd & __ldg(sd.dn_word + d + 1)) * q1;
+      if (++cnt == 4) { nd += (double)nl; wd += (double)wl; nl = wl = (R)0; cnt = 0; }
     }
-    const int u = (int)(i / dim_dn);
-    const int d = (int)(i - (int64_t)u * dim_dn);
-    const R q = p.x * p.x + p.y * p.y;
-    nl += q;
-    wl += (R)__popc(__ldg(sd.up_word + u) & __ldg(sd.dn_word + d)) * q;
-    if (++cnt == 8) { nd += (double)nl; wd += (double)wl; nl = wl = (R)0; cnt = 0; }
+  } else {
+    for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
+      C p = x1[i];
+      if (COMBINE) {
+        p = combine_one<R, C>(cf, cf_lo, n, V, vd.D, i, p);
+        x1[i] = p;
+      }
+      const int u = (int)(i / dim_dn);
+      const int d = (int)(i - (int64_t)u * dim_dn);
+      const R q = p.x * p.x + p.y * p.y;
+      nl += q;
+      wl += (R)__popc(__ldg(sd.up_word + u) & __ldg(sd.dn_word + d)) * q;
+      if (++cnt == 8) { nd += (double)nl; wd += (double)wl; nl = wl = (R)0; cnt = 0; }
+    }
   }
   double v[2] = {nd + (double)nl, wd + (double)wl};
   if (reduce_last_block<2>(v, blockIdx.x, vd.ew_begin, vd.ew_end, a.partials,

@@ -130,23 +130,24 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
       T.ent.push_back((e.src & 0xFFFFu) | (e.group << 16) | (e.neg << 31));
     T.off[r + 1] = (int32_t)T.ent.size();
   }
-  // row segments by group
-  T.seg_off.assign(T.dim + 1, 0);
+  // rows padded to a multiple of 4 entries
+  T.pad_off.assign(T.dim + 1, 0);
   for (int r = 0; r < T.dim; ++r) {
-    for (int e = T.off[r]; e < T.off[r + 1]; ++e) {
-      const uint32_t g = (T.ent[e] >> 16) & 0xFFu;
-      if (e == T.off[r] || g != ((T.ent[e - 1] >> 16) & 0xFFu)) {
-        if (e != T.off[r]) T.seg_end.push_back((uint32_t)e);
-        T.seg.push_back(g | ((uint32_t)e << 8));
-      }
+    const int n = T.off[r + 1] - T.off[r];
+    for (int e = T.off[r]; e < T.off[r + 1]; ++e) T.pad_ent.push_back(T.ent[e]);
+    if (n > 0) {
+      const uint32_t last_group = T.ent[T.off[r + 1] - 1] & (0xFFu << 16);
+      for (int k = n; k % 4 != 0; ++k)
+        T.pad_ent.push_back((uint32_t)r | last_group | kNullEntry);
     }
-    if (T.off[r + 1] > T.off[r]) T.seg_end.push_back((uint32_t)T.off[r + 1]);
-    T.seg_off[r + 1] = (int32_t)T.seg.size();
+    T.pad_off[r + 1] = (int32_t)T.pad_ent.size();
   }
-  // warp-tiled ELL over columns (tiles of 64, two columns per lane)
+  // warp-tiled ELL over columns (tiles of 64, two columns per lane), flat
+  // slot list per tile grouped by bond group, padded to an even slot count
   const int ntile = (T.dim + 63) / 64;
-  T.tseg_off.assign(ntile + 1, 0);
+  T.tslot_off.assign(ntile + 1, 0);
   const uint32_t pad = (uint32_t)T.dim;  // the zero column
+  int nslots = 0;
   for (int c = 0; c < ntile; ++c) {
     int maxg = -1;
     for (int l = 0; l < 64; ++l) {
@@ -154,6 +155,7 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
       if (d >= T.dim) break;
       if (T.off[d + 1] > T.off[d]) maxg = std::max(maxg, (int)((T.ent[T.off[d + 1] - 1] >> 16) & 0xFFu));
     }
+    int tile_slots = 0;
     for (int g = 0; g <= maxg; ++g) {
       int K = 0;
       std::vector<int> first(64, -1), cnt(64, 0);
@@ -167,11 +169,8 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
           }
         K = std::max(K, cnt[l]);
       }
-      if (K == 0) continue;
-      const int slot0 = (int)(T.ell.size() / 64);
-      T.tseg.push_back((uint32_t)g | ((uint32_t)K << 8));
-      T.tslot.push_back(slot0);
-      for (int k = 0; k < K; ++k)
+      for (int k = 0; k < K; ++k) {
+        T.slot_grp.push_back((uint32_t)g);
         for (int l = 0; l < 64; ++l) {   // l = 2 * lane + h
           uint32_t v = pad;
           if (k < cnt[l]) {
@@ -180,8 +179,16 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
           }
           T.ell.push_back(v);
         }
+        ++tile_slots;
+      }
     }
-    T.tseg_off[c + 1] = (int32_t)T.tseg.size();
+    if (tile_slots % 2) {   // padding slot: every entry points to the zero column
+      T.slot_grp.push_back(T.slot_grp.empty() ? 0u : T.slot_grp.back());
+      for (int l = 0; l < 64; ++l) T.ell.push_back(pad);
+      ++tile_slots;
+    }
+    nslots += tile_slots;
+    T.tslot_off[c + 1] = nslots;
   }
   if (L.has_eps) {
     T.eps_sum.resize(T.dim);

@@ -7,6 +7,9 @@
 
 namespace ed {
 
+// Null entry of a padded row: contributes zero (bit 30; no rank uses it).
+constexpr uint32_t kNullEntry = 0x40000000u;
+
 // Spin basis of n electrons on Ns sites: all Ns-bit words with n ones in
 // ascending order (Sec. 3.1; the order of the hash of Eq. (36)).
 std::vector<uint32_t> spin_basis(int Ns, int n);
@@ -45,22 +48,21 @@ struct SpinTable {
   std::vector<int32_t> off;
   std::vector<uint32_t> ent;
   std::vector<double> eps_sum;   // per state: sum of eps over occupied sites
-  // Row segments (used for the across-row gathers): for row r the entries of
-  // group g occupy [seg_begin, seg_end); seg[s] = g | begin << 8 (begin is the
-  // entry index, < 2^24), segments of row r are seg_off[r]..seg_off[r+1].
-  std::vector<int32_t> seg_off;
-  std::vector<uint32_t> seg;     // packed (group, begin); end = next begin or off[r+1]
-  std::vector<uint32_t> seg_end;
+  // Padded rows (used for the across-row gathers): the entries of row r,
+  // sorted by group, padded to a multiple of 4 with null entries (bit 30 set,
+  // sign 0, source = row r itself, group of the last real entry); row r
+  // occupies pad_ent[pad_off[r] .. pad_off[r+1]).
+  std::vector<int32_t> pad_off;
+  std::vector<uint32_t> pad_ent;
   // Warp-tiled ELL (used for the within-row gathers): columns in tiles of 64,
-  // lane l of a warp owning columns 64c + 2l and 64c + 2l + 1.  Tile c has
-  // segments tseg_off[c]..tseg_off[c+1], tseg[s] = group | K << 8 and first
-  // slot tslot[s]; slot k of segment s holds, for lane l, the two entries
-  // (rank | sign << 31) of its columns at ell[2 * ((slot0 + k) * 32 + l)] and
-  // [.. + 1], padded with rank = dim (a zero column).  K is the largest count
-  // of that group over the 64 columns.
-  std::vector<int32_t> tseg_off;
-  std::vector<uint32_t> tseg;
-  std::vector<int32_t> tslot;
+  // lane l of a warp owning columns 64c + 2l and 64c + 2l + 1.  Tile c owns
+  // slots tslot_off[c] .. tslot_off[c+1] (a multiple of 2, grouped by bond
+  // group, slot_grp[s] = group of slot s); slot s holds for lane l the two
+  // entries (rank | sign << 31) of its columns at ell[2 * (s * 32 + l)] and
+  // [.. + 1].  Missing entries (a column with fewer hops of that group, and the
+  // padding slot) point to rank = dim, a zero column.
+  std::vector<int32_t> tslot_off;
+  std::vector<uint32_t> slot_grp;
   std::vector<uint32_t> ell;
 };
 SpinTable build_spin_table(const LatticeHost& L, int n);
