@@ -46,6 +46,12 @@ cudaError_t upload_sector(SectorGPU& S) {
   if ((e = upload(S.dn_word, S.dn.words)) != cudaSuccess) return e;
   if ((e = upload(S.up_pad_off, S.up.pad_off)) != cudaSuccess) return e;
   if ((e = upload(S.up_pad_ent, S.up.pad_ent)) != cudaSuccess) return e;
+  {
+    std::vector<uint32_t> rows(S.up.pad_ent.size());
+    for (size_t i = 0; i < rows.size(); ++i)
+      rows[i] = (S.up.pad_ent[i] & kEntRankMask) * (uint32_t)S.dn.dim;
+    if ((e = upload(S.up_pad_row, rows)) != cudaSuccess) return e;
+  }
   if ((e = upload(S.dn_tslot_off, S.dn.tslot_off)) != cudaSuccess) return e;
   if ((e = upload(S.dn_slot_grp, S.dn.slot_grp)) != cudaSuccess) return e;
   if ((e = upload(S.dn_ell, S.dn.ell)) != cudaSuccess) return e;
@@ -71,6 +77,7 @@ cudaError_t upload_sector(SectorGPU& S) {
   d.dn_eps = S.has_eps ? static_cast<const double*>(S.dn_eps.p) : nullptr;
   d.up_pad_off = static_cast<const int32_t*>(S.up_pad_off.p);
   d.up_pad_ent = static_cast<const uint32_t*>(S.up_pad_ent.p);
+  d.up_pad_row = static_cast<const uint32_t*>(S.up_pad_row.p);
   d.dn_tslot_off = static_cast<const int32_t*>(S.dn_tslot_off.p);
   d.dn_slot_grp = static_cast<const uint32_t*>(S.dn_slot_grp.p);
   d.dn_ell = static_cast<const uint32_t*>(S.dn_ell.p);
@@ -213,7 +220,7 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
   const SectorGPU& S = ctx->sec;
   int64_t b = S.up_off.bytes + S.up_ent.bytes + S.dn_off.bytes + S.dn_ent.bytes +
               S.up_word.bytes + S.dn_word.bytes + S.up_eps.bytes + S.dn_eps.bytes +
-              S.up_pad_off.bytes + S.up_pad_ent.bytes + S.dn_tslot_off.bytes +
+              S.up_pad_off.bytes + S.up_pad_ent.bytes + S.up_pad_row.bytes + S.dn_tslot_off.bytes +
               S.dn_slot_grp.bytes + S.dn_ell.bytes;
   if (ctx->engine) b += ctx->engine->device_bytes();
   if (ctx->spec_engine) b += ctx->spec_engine->device_bytes();

@@ -35,10 +35,11 @@ struct SectorDev {
   // up spin: rows padded to multiples of 4 entries (across-row gathers)
   const int32_t* up_pad_off;   // [dim_up + 1]
   const uint32_t* up_pad_ent;  // entries; bit 30 = null (contributes zero)
+  const uint32_t* up_pad_row;  // element offset of the source row: rank * dim_dn
   // down spin: warp-tiled ELL over 64-column tiles (within-row gathers)
   const int32_t* dn_tslot_off; // [ceil(dim_dn/64) + 1], even slot counts
   const uint32_t* dn_slot_grp; // group of each slot
-  const uint32_t* dn_ell;      // [slots][32 lanes][2]: rank | sign << 31, pad = dim_dn
+  const uint32_t* dn_ell;      // [slots][32 lanes][2]: tile_offset(rank) | sign << 31
 };
 
 // Per-vector Lanczos scalars, all float64, 1-based Krylov index j.

@@ -183,6 +183,27 @@ struct TileIO {
       for (int r = 0; r < NR; ++r) v[r] = tile[(size_t)d * NR + r];
     }
   }
+  // load by a table entry: the precomputed byte offset of the column's first
+  // chunk for 32-byte columns, else rank = offset >> 5
+  __device__ static __forceinline__ void load_ent(const C* tile, uint32_t ent, C (&v)[NR]) {
+    const uint32_t off = ent & 0x7FFFFFFFu;
+    if constexpr (kBytes == 32) {
+      const char* base = reinterpret_cast<const char*>(tile);
+      const float4 a = *reinterpret_cast<const float4*>(base + off);
+      const float4 b = *reinterpret_cast<const float4*>(base + (off ^ 16u));
+      if constexpr (sizeof(C) == 8) {
+        v[0].x = a.x; v[0].y = a.y; v[1].x = a.z; v[1].y = a.w;
+        v[2].x = b.x; v[2].y = b.y; v[3].x = b.z; v[3].y = b.w;
+      } else {
+        v[0].x = __longlong_as_double(((long long)__float_as_int(a.y) << 32) | (unsigned)__float_as_int(a.x));
+        v[0].y = __longlong_as_double(((long long)__float_as_int(a.w) << 32) | (unsigned)__float_as_int(a.z));
+        v[1].x = __longlong_as_double(((long long)__float_as_int(b.y) << 32) | (unsigned)__float_as_int(b.x));
+        v[1].y = __longlong_as_double(((long long)__float_as_int(b.w) << 32) | (unsigned)__float_as_int(b.z));
+      }
+    } else {
+      load(tile, (int)(off >> 5), v);
+    }
+  }
   __device__ static __forceinline__ void store(C* tile, int d, const C (&v)[NR]) {
     if constexpr (kBytes == 32) {
       float4* t = reinterpret_cast<float4*>(tile);
@@ -342,10 +363,10 @@ k_apply(BatchArgs a, int j) {
           const uint2 eb = __ldg(ell2 + (size_t)(q + 1) * 32 + lane);
           const uint32_t ga = __ldg(sd.dn_slot_grp + q), gb = __ldg(sd.dn_slot_grp + q + 1);
           C a0[NR], a1[NR], b0[NR], b1[NR];
-          TIO::load(tile, (int)(ea.x & kEntRankMask), a0);
-          TIO::load(tile, (int)(ea.y & kEntRankMask), a1);
-          TIO::load(tile, (int)(eb.x & kEntRankMask), b0);
-          TIO::load(tile, (int)(eb.y & kEntRankMask), b1);
+          TIO::load_ent(tile, ea.x, a0);
+          TIO::load_ent(tile, ea.y, a1);
+          TIO::load_ent(tile, eb.x, b0);
+          TIO::load_ent(tile, eb.y, b1);
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
             const uint32_t g = half ? gb : ga;
@@ -387,6 +408,15 @@ k_apply(BatchArgs a, int j) {
         }
       }
     }
+    // per-thread pair bases of this chunk
+    bool pvalid[PP];
+    const float4* xb4[PP];
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+      const int p = pc + tid + k * T;
+      pvalid[k] = p < npairs;
+      xb4[k] = reinterpret_cast<const float4*>(x) + p;
+    }
     // ---- T_up: the padded entry list of each row (uniform over the block),
     // four entries per batch with all their row loads in flight, coefficient
     // applied when the group changes
@@ -401,16 +431,27 @@ k_apply(BatchArgs a, int j) {
         uint32_t gcur = e0 < e1 ? ((__ldg(sd.up_pad_ent + e0) >> kEntGroupShift) & 0xFFu) : 0u;
         for (int e = e0; e < e1; e += 4) {
           const uint4 ent4 = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_ent + e));
+          const uint4 row4 = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_row + e));
           const uint32_t ents[4] = {ent4.x, ent4.y, ent4.z, ent4.w};
+          const uint32_t rows[4] = {row4.x, row4.y, row4.z, row4.w};
           C v[4][2 * PP];
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) {
-            const C* src = x + (size_t)(ents[qq] & kEntRankMask) * dim_dn;
 #pragma unroll
             for (int k = 0; k < PP; ++k) {
-              const int p = pc + tid + k * T;
-              if (p < npairs) load_pair<C, VEC>(src, p, dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
-              else { v[qq][2 * k] = czero<C>(); v[qq][2 * k + 1] = czero<C>(); }
+              if constexpr (VEC) {
+                // rows are 16-byte aligned: one 16-byte load per pair at the
+                // per-thread pair base plus the source row's offset
+                if (pvalid[k]) {
+                  const float4 f = xb4[k][rows[qq] >> 1];
+                  v[qq][2 * k].x = f.x; v[qq][2 * k].y = f.y;
+                  v[qq][2 * k + 1].x = f.z; v[qq][2 * k + 1].y = f.w;
+                } else { v[qq][2 * k] = czero<C>(); v[qq][2 * k + 1] = czero<C>(); }
+              } else {
+                const int p = pc + tid + k * T;
+                if (pvalid[k]) load_pair<C, false>(x + rows[qq], p, dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
+                else { v[qq][2 * k] = czero<C>(); v[qq][2 * k + 1] = czero<C>(); }
+              }
             }
           }
 #pragma unroll

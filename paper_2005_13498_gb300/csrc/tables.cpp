@@ -172,19 +172,20 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
       for (int k = 0; k < K; ++k) {
         T.slot_grp.push_back((uint32_t)g);
         for (int l = 0; l < 64; ++l) {   // l = 2 * lane + h
-          uint32_t v = pad;
+          uint32_t rank = pad, sgn = 0;
           if (k < cnt[l]) {
             const uint32_t e = T.ent[first[l] + k];
-            v = (e & 0xFFFFu) | (e & 0x80000000u);
+            rank = e & 0xFFFFu;
+            sgn = e & 0x80000000u;
           }
-          T.ell.push_back(v);
+          T.ell.push_back(tile_offset(rank) | sgn);
         }
         ++tile_slots;
       }
     }
     if (tile_slots % 2) {   // padding slot: every entry points to the zero column
       T.slot_grp.push_back(T.slot_grp.empty() ? 0u : T.slot_grp.back());
-      for (int l = 0; l < 64; ++l) T.ell.push_back(pad);
+      for (int l = 0; l < 64; ++l) T.ell.push_back(tile_offset(pad));
       ++tile_slots;
     }
     nslots += tile_slots;

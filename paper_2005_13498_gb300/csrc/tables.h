@@ -10,6 +10,13 @@ namespace ed {
 // Null entry of a padded row: contributes zero (bit 30; no rank uses it).
 constexpr uint32_t kNullEntry = 0x40000000u;
 
+// Byte offset of column `rank` in the shared-memory tile of the apply kernel
+// when a column holds 32 bytes (two 16-byte chunks, swapped for columns with
+// bit 2 set to spread random gathers over all bank groups); the second chunk
+// is at offset ^ 16.  Layouts with other column sizes recover the rank as
+// offset >> 5.
+inline uint32_t tile_offset(uint32_t rank) { return 32u * rank + 16u * ((rank >> 2) & 1u); }
+
 // Spin basis of n electrons on Ns sites: all Ns-bit words with n ones in
 // ascending order (Sec. 3.1; the order of the hash of Eq. (36)).
 std::vector<uint32_t> spin_basis(int Ns, int n);
@@ -58,9 +65,10 @@ struct SpinTable {
   // lane l of a warp owning columns 64c + 2l and 64c + 2l + 1.  Tile c owns
   // slots tslot_off[c] .. tslot_off[c+1] (a multiple of 2, grouped by bond
   // group, slot_grp[s] = group of slot s); slot s holds for lane l the two
-  // entries (rank | sign << 31) of its columns at ell[2 * (s * 32 + l)] and
-  // [.. + 1].  Missing entries (a column with fewer hops of that group, and the
-  // padding slot) point to rank = dim, a zero column.
+  // entries tile_offset(rank) | sign << 31 of its columns at
+  // ell[2 * (s * 32 + l)] and [.. + 1].  Missing entries (a column with fewer
+  // hops of that group, and the padding slot) point to rank = dim, a zero
+  // column.
   std::vector<int32_t> tslot_off;
   std::vector<uint32_t> slot_grp;
   std::vector<uint32_t> ell;
