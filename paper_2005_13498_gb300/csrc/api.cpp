@@ -246,18 +246,13 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     const int64_t D = ctx->dim_up * ctx->dim_dn;
     const size_t esz = fp64 ? 16 : 8;
     const int ng = 2 * ctx->lat.n_classes;
-    P.shape = apply_shape((int)ctx->dim_dn, fp64, ng);
     std::vector<VecDev> vd(nvec);
-    std::vector<ApplyBlock> amap;
     for (int b = 0; b < nvec; ++b) {
       std::memset(&vd[b], 0, sizeof(VecDev));
       vd[b].sector = 0;
       vd[b].D = D;
       vd[b].x1 = const_cast<char*>(static_cast<const char*>(v)) + (size_t)b * D * esz;
       vd[b].w = static_cast<char*>(w) + (size_t)b * D * esz;
-      vd[b].apply_begin = (int)amap.size();
-      append_apply_blocks(amap, b, (int)ctx->dim_up, P.shape.nr);
-      vd[b].apply_end = (int)amap.size();
     }
     std::vector<double> cf(std::max(1, ng) * 2, 0.0);
     group_coefficients(ctx->lat, ctx->A, cf.data());
@@ -268,8 +263,6 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     CK(ctx, upload(P.sec, secs));
     CK(ctx, upload(P.vec, vd));
     CK(ctx, upload(P.st, st));
-    CK(ctx, upload(P.amap, amap));
-    CK(ctx, P.partials.alloc(sizeof(double) * 4 * amap.size()));
     CK(ctx, P.counters.alloc(sizeof(unsigned) * nvec));
     CK(ctx, cudaMemset(P.counters.p, 0, sizeof(unsigned) * nvec));
     if (fp64) CK(ctx, upload(P.coefs, cf));
@@ -287,9 +280,29 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     P.args.Ns = ctx->Ns;
     P.args.max_dim_dn = (int)ctx->dim_dn;
     P.args.U = ctx->lat.U;
-    P.shape.vec = !fp64 && (ctx->dim_dn % 2 == 0) &&
-                  ((((uintptr_t)v) | ((uintptr_t)w)) & 15u) == 0;
+    ApplyTuneTarget tt;
+    tt.fp64 = fp64;
+    tt.vec_ok = !fp64 && (ctx->dim_dn % 2 == 0) &&
+                ((((uintptr_t)v) | ((uintptr_t)w)) & 15u) == 0;
+    tt.max_dim_dn = (int)ctx->dim_dn;
+    tt.n_groups = ng;
+    tt.dim_up.assign(nvec, (int)ctx->dim_up);
+    tt.dim_dn.assign(nvec, (int)ctx->dim_dn);
+    tt.args = P.args;
+    std::vector<ApplyBlock> amap;
+    CKS(ctx, tune_apply(tt, s, &P.shape, &amap));
     CK(ctx, prepare_apply(fp64, P.shape));
+    for (int b = 0; b < (int)amap.size(); ++b) {
+      VecDev& vv = vd[amap[b].vec];
+      if (b == 0 || amap[b - 1].vec != amap[b].vec) vv.apply_begin = b;
+      vv.apply_end = b + 1;
+    }
+    CK(ctx, upload(P.vec, vd));
+    CK(ctx, upload(P.amap, amap));
+    CK(ctx, P.partials.alloc(sizeof(double) * 4 * amap.size()));
+    P.args.vec = static_cast<VecDev*>(P.vec.p);
+    P.args.apply_map = static_cast<const ApplyBlock*>(P.amap.p);
+    P.args.partials = static_cast<double*>(P.partials.p);
     P.nblk = (int)amap.size();
     P.nvec = nvec;
     P.v = v;

@@ -96,37 +96,31 @@ struct GsApply {
   int nblk = 0;
 };
 
-cudaError_t gs_apply_setup(GsApply& G, ed_ctx* ctx) {
+// x, w: device buffers of length D the autotuner may read and overwrite.
+std::string gs_apply_setup(GsApply& G, ed_ctx* ctx, const double2* x, double2* w,
+                           cudaStream_t s) {
   std::vector<SectorDev> secs = {ctx->sec.dev};
   std::vector<VecDev> vd(1);
   std::memset(vd.data(), 0, sizeof(VecDev));
   vd[0].D = ctx->dim_up * ctx->dim_dn;
+  vd[0].x1 = const_cast<double2*>(x);
+  vd[0].w = w;
   const int ng = 2 * ctx->lat.n_classes;
-  G.shape = apply_shape((int)ctx->dim_dn, true, ng);
-  std::vector<ApplyBlock> amap;
-  append_apply_blocks(amap, 0, (int)ctx->dim_up, G.shape.nr);
-  vd[0].apply_begin = 0;
-  vd[0].apply_end = (int)amap.size();
   std::vector<double> cf(std::max(1, ng) * 2, 0.0);
   const double A0[3] = {0, 0, 0};
   group_coefficients(ctx->lat, A0, cf.data());
   std::vector<LanczosState> st(1);
   std::memset(st.data(), 0, sizeof(LanczosState));
-  cudaError_t e;
-  if ((e = upload(G.sec, secs)) != cudaSuccess) return e;
-  if ((e = upload(G.vec, vd)) != cudaSuccess) return e;
-  if ((e = upload(G.st, st)) != cudaSuccess) return e;
-  if ((e = upload(G.amap, amap)) != cudaSuccess) return e;
-  if ((e = upload(G.coefs, cf)) != cudaSuccess) return e;
-  if ((e = G.partials.alloc(sizeof(double) * 4 * amap.size())) != cudaSuccess) return e;
-  if ((e = G.counters.alloc(sizeof(unsigned))) != cudaSuccess) return e;
-  if ((e = cudaMemset(G.counters.p, 0, sizeof(unsigned))) != cudaSuccess) return e;
+  ED_TRY(upload(G.sec, secs));
+  ED_TRY(upload(G.vec, vd));
+  ED_TRY(upload(G.st, st));
+  ED_TRY(upload(G.coefs, cf));
+  ED_TRY(G.counters.alloc(sizeof(unsigned)));
+  ED_TRY(cudaMemset(G.counters.p, 0, sizeof(unsigned)));
   std::memset(&G.args, 0, sizeof(G.args));
   G.args.sec = static_cast<const SectorDev*>(G.sec.p);
   G.args.vec = static_cast<VecDev*>(G.vec.p);
   G.args.st = static_cast<LanczosState*>(G.st.p);
-  G.args.apply_map = static_cast<const ApplyBlock*>(G.amap.p);
-  G.args.partials = static_cast<double*>(G.partials.p);
   G.args.counters = static_cast<unsigned*>(G.counters.p);
   G.args.coefs = G.coefs.p;
   G.args.n_groups = ng;
@@ -134,8 +128,28 @@ cudaError_t gs_apply_setup(GsApply& G, ed_ctx* ctx) {
   G.args.Ns = ctx->Ns;
   G.args.max_dim_dn = (int)ctx->dim_dn;
   G.args.U = ctx->lat.U;
+  ApplyTuneTarget tt;
+  tt.fp64 = true;
+  tt.vec_ok = false;
+  tt.max_dim_dn = (int)ctx->dim_dn;
+  tt.n_groups = ng;
+  tt.dim_up = {(int)ctx->dim_up};
+  tt.dim_dn = {(int)ctx->dim_dn};
+  tt.args = G.args;
+  std::vector<ApplyBlock> amap;
+  std::string err = tune_apply(tt, s, &G.shape, &amap);
+  if (!err.empty()) return err;
+  vd[0].apply_begin = 0;
+  vd[0].apply_end = (int)amap.size();
+  ED_TRY(upload(G.vec, vd));
+  ED_TRY(upload(G.amap, amap));
+  ED_TRY(G.partials.alloc(sizeof(double) * 4 * amap.size()));
+  G.args.vec = static_cast<VecDev*>(G.vec.p);
+  G.args.apply_map = static_cast<const ApplyBlock*>(G.amap.p);
+  G.args.partials = static_cast<double*>(G.partials.p);
   G.nblk = (int)amap.size();
-  return prepare_apply(true, G.shape);
+  ED_TRY(prepare_apply(true, G.shape));
+  return "";
 }
 
 cudaError_t gs_apply(GsApply& G, const double2* x, double2* w, cudaStream_t s) {
@@ -180,7 +194,8 @@ ed_status ed_ground_state(ed_ctx* ctx, void* psi, double* E0, double tol, int ma
   CK(ctx, cdev.alloc(sizeof(double2) * (K + 1)));
   CK(ctx, sdev.alloc(sizeof(double) * (K + 1)));
   GsApply G;
-  CK(ctx, gs_apply_setup(G, ctx));
+  CKS(ctx, gs_apply_setup(G, ctx, static_cast<const double2*>(V.p),
+                         static_cast<double2*>(w.p), s));
   double2* Vp = static_cast<double2*>(V.p);
   double2* wp = static_cast<double2*>(w.p);
   double2* yp = static_cast<double2*>(y.p);

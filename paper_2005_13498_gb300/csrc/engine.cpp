@@ -3,15 +3,11 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 namespace ed {
 
-#define ED_TRY(call)                                                    \
-  do {                                                                  \
-    cudaError_t e_ = (call);                                            \
-    if (e_ != cudaSuccess)                                              \
-      return std::string(#call) + ": " + cudaGetErrorString(e_);        \
-  } while (0)
 
 cudaError_t DevMem::alloc(size_t n) {
   release();
@@ -54,6 +50,79 @@ bool Engine::compatible(const EngineConfig& cfg, const std::vector<EngineVector>
     if (vecs[i].owned_x1 != vecs_[i].owned_x1) return false;
   }
   return true;
+}
+
+std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* shape,
+                       std::vector<ApplyBlock>* map) {
+  static std::mutex mu;
+  static std::map<std::string, int> cache;
+  std::vector<LaunchShape> cands = apply_candidates(t.max_dim_dn, t.fp64, t.n_groups);
+  if (cands.empty()) return "apply kernel: rows too long for shared memory";
+  for (auto& c : cands) c.vec = t.vec_ok;
+  auto build = [&](const LaunchShape& sh) {
+    map->clear();
+    for (size_t i = 0; i < t.dim_up.size(); ++i)
+      append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr);
+  };
+  std::string key = (t.fp64 ? "d" : "f") + std::string(t.vec_ok ? "v" : "s");
+  for (size_t i = 0; i < t.dim_up.size(); ++i)
+    key += ":" + std::to_string(t.dim_up[i]) + "x" + std::to_string(t.dim_dn[i]);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end())
+      for (auto& c : cands)
+        if (c.cfg == it->second) {
+          *shape = c;
+          build(c);
+          return "";
+        }
+  }
+  int64_t elems = 0;
+  for (size_t i = 0; i < t.dim_up.size(); ++i) elems += (int64_t)t.dim_up[i] * t.dim_dn[i];
+  if (cands.size() == 1 || elems < (1 << 20)) {   // small problems: the default
+    *shape = cands.front();
+    build(*shape);
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = shape->cfg;
+    return "";
+  }
+  cudaEvent_t e0, e1;
+  ED_TRY(cudaEventCreate(&e0));
+  ED_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  LaunchShape best_sh = cands.front();
+  std::string err;
+  for (const LaunchShape& c : cands) {
+    build(c);
+    DevMem dmap;
+    if (dmap.alloc(map->size() * sizeof(ApplyBlock)) != cudaSuccess ||
+        cudaMemcpy(dmap.p, map->data(), map->size() * sizeof(ApplyBlock),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        prepare_apply(t.fp64, c) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    BatchArgs a = t.args;
+    a.apply_map = static_cast<const ApplyBlock*>(dmap.p);
+    const int nblk = (int)map->size();
+    if (launch_apply(t.fp64, a, nblk, c, 0, s) != cudaSuccess) { cudaGetLastError(); continue; }
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) launch_apply(t.fp64, a, nblk, c, 0, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { err = "autotune: apply failed"; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_sh = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!err.empty()) return err;
+  *shape = best_sh;
+  build(best_sh);
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = best_sh.cfg;
+  return "";
 }
 
 static int64_t ew_chunk(int64_t D) {
@@ -103,8 +172,6 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   std::vector<VecDev> vd(nv);
   int max_dim_dn = 1;
   for (int i = 0; i < nv; ++i) max_dim_dn = std::max(max_dim_dn, sectors_[vecs_[i].sector].dim_dn);
-  shape_ = apply_shape(max_dim_dn, cfg.fp64, n_groups);
-  const int shape_nr = shape_.nr;
   int64_t voff = 0;
   const int ncap = cfg.n_steps_cap;
   // outputs per vector: docc, norm2, energy [ncap+1], delta [ncap], meff [ncap]
@@ -121,9 +188,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     v.V = static_cast<char*>(d_V_.p) + (size_t)std::max(0, m - 1) * voff * esz;
     v.w = static_cast<char*>(d_w_.p) + (size_t)voff * esz;
     voff += v.D;
-    v.apply_begin = (int)amap.size();
-    append_apply_blocks(amap, i, sd.dim_up, shape_nr);
-    v.apply_end = (int)amap.size();
+
     v.ew_begin = (int)emap.size();
     const int64_t ch = ew_chunk(v.D);
     for (int64_t b = 0; b < v.D; b += ch) emap.push_back({i, 0, b, std::min(v.D, b + ch)});
@@ -135,22 +200,18 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     v.out_delta = base + 3 * (ncap + 1);
     v.out_meff = reinterpret_cast<int*>(base + 4 * (ncap + 1));
   }
-  n_apply_ = (int)amap.size();
   n_ew_ = (int)emap.size();
   // 16-byte pair accesses for complex64 when every row and buffer allows it
-  shape_.vec = !cfg.fp64;
+  bool vec_ok = !cfg.fp64;
   for (int i = 0; i < nv; ++i) {
-    if (sectors_[vecs_[i].sector].dim_dn & 1) shape_.vec = false;
-    if (((uintptr_t)vd[i].x1 | (uintptr_t)vd[i].V | (uintptr_t)vd[i].w) & 15u) shape_.vec = false;
+    if (sectors_[vecs_[i].sector].dim_dn & 1) vec_ok = false;
+    if (((uintptr_t)vd[i].x1 | (uintptr_t)vd[i].V | (uintptr_t)vd[i].w) & 15u) vec_ok = false;
   }
-  ED_TRY(prepare_apply(cfg.fp64, shape_));
 
   ED_TRY(d_sec_.alloc(sizeof(SectorDev) * sectors_.size()));
   ED_TRY(d_vec_.alloc(sizeof(VecDev) * nv));
   ED_TRY(d_st_.alloc(sizeof(LanczosState) * nv));
-  ED_TRY(d_amap_.alloc(sizeof(ApplyBlock) * amap.size()));
   ED_TRY(d_emap_.alloc(sizeof(EwBlock) * emap.size()));
-  ED_TRY(d_partials_.alloc(sizeof(double) * 4 * std::max(n_apply_, n_ew_)));
   ED_TRY(d_counters_.alloc(sizeof(unsigned) * nv));
   ED_TRY(d_coefs_.alloc(esz * (size_t)n_groups * std::max(1, ncap)));
   if (cfg.energy) ED_TRY(d_coefs_obs_.alloc(esz * (size_t)n_groups * (ncap + 1)));
@@ -159,11 +220,8 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
                          cudaMemcpyHostToDevice, stream));
   ED_TRY(cudaMemcpyAsync(d_vec_.p, vd.data(), sizeof(VecDev) * nv, cudaMemcpyHostToDevice,
                          stream));
-  ED_TRY(cudaMemcpyAsync(d_amap_.p, amap.data(), sizeof(ApplyBlock) * amap.size(),
-                         cudaMemcpyHostToDevice, stream));
   ED_TRY(cudaMemcpyAsync(d_emap_.p, emap.data(), sizeof(EwBlock) * emap.size(),
                          cudaMemcpyHostToDevice, stream));
-  ED_TRY(cudaMemsetAsync(d_counters_.p, 0, sizeof(unsigned) * nv, stream));
   ED_TRY(cudaStreamSynchronize(stream));
 
   std::memset(&args_, 0, sizeof(args_));
@@ -183,6 +241,41 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   args_.U = U;
   args_.tau = 0.0;
   args_.break_tol = break_tol;
+
+  // apply configuration (autotuned) and its block map
+  ApplyTuneTarget tt;
+  tt.fp64 = cfg.fp64;
+  tt.vec_ok = vec_ok;
+  tt.max_dim_dn = max_dim_dn;
+  tt.n_groups = n_groups;
+  for (int i = 0; i < nv; ++i) {
+    tt.dim_up.push_back(sectors_[vecs_[i].sector].dim_up);
+    tt.dim_dn.push_back(sectors_[vecs_[i].sector].dim_dn);
+  }
+  tt.args = args_;
+  std::string err = tune_apply(tt, stream, &shape_, &amap);
+  if (!err.empty()) return err;
+  ED_TRY(prepare_apply(cfg.fp64, shape_));
+  n_apply_ = (int)amap.size();
+  for (int i = 0; i < nv; ++i) {
+    vd[i].apply_begin = -1;
+    vd[i].apply_end = -1;
+  }
+  for (int b = 0; b < n_apply_; ++b) {
+    VecDev& v = vd[amap[b].vec];
+    if (v.apply_begin < 0) v.apply_begin = b;
+    v.apply_end = b + 1;
+  }
+  ED_TRY(d_amap_.alloc(sizeof(ApplyBlock) * amap.size()));
+  ED_TRY(d_partials_.alloc(sizeof(double) * 4 * std::max(n_apply_, n_ew_)));
+  ED_TRY(cudaMemcpyAsync(d_vec_.p, vd.data(), sizeof(VecDev) * nv, cudaMemcpyHostToDevice,
+                         stream));
+  ED_TRY(cudaMemcpyAsync(d_amap_.p, amap.data(), sizeof(ApplyBlock) * amap.size(),
+                         cudaMemcpyHostToDevice, stream));
+  ED_TRY(cudaMemsetAsync(d_counters_.p, 0, sizeof(unsigned) * nv, stream));
+  ED_TRY(cudaStreamSynchronize(stream));
+  args_.apply_map = static_cast<const ApplyBlock*>(d_amap_.p);
+  args_.partials = static_cast<double*>(d_partials_.p);
   return "";
 }
 

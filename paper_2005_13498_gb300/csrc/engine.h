@@ -9,6 +9,15 @@
 #include "common.h"
 #include "kernels.cuh"
 
+// Returns the failing call and CUDA's message as a string from a function
+// that reports errors as std::string (empty on success).
+#define ED_TRY(call)                                                    \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess)                                              \
+      return std::string(#call) + ": " + cudaGetErrorString(e_);        \
+  } while (0)
+
 namespace ed {
 
 struct DevMem {
@@ -33,6 +42,22 @@ struct EngineConfig {
   bool overlaps = false;
   int n_steps_cap = 0;
 };
+
+// Autotuner of the apply kernel: times the feasible configurations (rows per
+// CTA, column pairs per thread, occupancy target) with plain applies on the
+// caller's buffers and keeps the fastest.  Decisions are cached per
+// (precision, vector shapes) for the life of the process.
+struct ApplyTuneTarget {
+  bool fp64 = false;
+  bool vec_ok = false;          // complex64 rows may be read as 16-byte pairs
+  int max_dim_dn = 1;
+  int n_groups = 0;
+  std::vector<int> dim_up;      // per vector
+  std::vector<int> dim_dn;      // per vector
+  BatchArgs args{};             // vec / sec / coefs valid; apply_map is set here
+};
+std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* shape,
+                       std::vector<ApplyBlock>* map);
 
 class Engine {
  public:

@@ -122,9 +122,6 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 //    the group coefficient once.
 //  * T_up (across rows) walks the group segments of row u, uniform over the
 //    block; each entry is a coalesced load of the source row along d.
-#ifndef ED_APPLY_MINB
-#define ED_APPLY_MINB 2
-#endif
 constexpr int kApplyThreads = 256;
 
 // Column pair (2p, 2p+1) of a row: one 16-byte access for aligned complex64
@@ -242,8 +239,8 @@ struct TileIO {
 //    row per k, all in flight before they are summed by group.
 //  * Epilogue: w = s_j acc - beta_{j-1} s_{j-1} x_{j-1}, stored in pairs,
 //    and the partial of Re<x_j, w>.
-template <typename R, int NR, int PP, bool VEC>
-__global__ void __launch_bounds__(kApplyThreads, ED_APPLY_MINB)
+template <typename R, int NR, int PP, bool VEC, int MINB>
+__global__ void __launch_bounds__(kApplyThreads, MINB)
 k_apply(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
   using TIO = TileIO<C, NR>;
@@ -1132,71 +1129,106 @@ static int grid_for(int64_t n, int threads) {
   return (int)g;
 }
 
-LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
+// Configurations of the apply kernel: rows per CTA (NR), column pairs per
+// thread per chunk (PP) and the occupancy target (MINB CTAs per SM, which
+// sets the register budget).  The autotuner times the feasible ones.
+struct ApplyCfg { bool fp64; int nr, pp, minb; };
+static const ApplyCfg kApplyCfgs[] = {
+    {false, 4, 2, 2}, {false, 2, 2, 3}, {false, 2, 1, 4}, {false, 1, 2, 2},
+    {true, 2, 1, 2}, {true, 1, 1, 4}, {true, 1, 1, 2},
+};
+static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
+
+std::vector<LaunchShape> apply_candidates(int max_dim_dn, bool fp64, int n_groups) {
   const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
-  // rows per CTA: as many as fit in ~110 KB of shared memory (two CTAs per
-  // SM), at most 4
-  int nr = (int)((110 * 1024) / ((size_t)(max_dim_dn + 2) * csz));
-  if (nr > 4) nr = 4;
-  if (nr == 3) nr = 2;
-  if (nr < 1) nr = 1;
-  LaunchShape sh;
-  sh.threads = kApplyThreads;
-  sh.ept = fp64 ? 1 : 2;      // column pairs per thread per chunk
-  sh.nr = nr;
-  sh.smem = ((size_t)(max_dim_dn + 2) * nr + (size_t)n_groups) * csz;
-  return sh;
+  std::vector<LaunchShape> out;
+  for (int i = 0; i < kNumApplyCfgs; ++i) {
+    const ApplyCfg& c = kApplyCfgs[i];
+    if (c.fp64 != fp64) continue;
+    LaunchShape sh;
+    sh.threads = kApplyThreads;
+    sh.ept = c.pp;
+    sh.nr = c.nr;
+    sh.cfg = i;
+    sh.smem = ((size_t)(max_dim_dn + 2) * c.nr + (size_t)n_groups) * csz;
+    // the CTAs per SM the configuration aims at must fit in shared memory
+    if (sh.smem * (size_t)c.minb > 228 * 1024) continue;
+    if (sh.smem > 227 * 1024) continue;
+    out.push_back(sh);
+  }
+  if (out.empty()) {   // very long rows: one row per CTA, one CTA per SM
+    for (int i = 0; i < kNumApplyCfgs; ++i) {
+      const ApplyCfg& c = kApplyCfgs[i];
+      if (c.fp64 != fp64 || c.nr != 1) continue;
+      LaunchShape sh;
+      sh.threads = kApplyThreads;
+      sh.ept = c.pp;
+      sh.nr = 1;
+      sh.cfg = i;
+      sh.smem = ((size_t)(max_dim_dn + 2) + (size_t)n_groups) * csz;
+      if (sh.smem <= 227 * 1024) out.push_back(sh);
+      break;
+    }
+  }
+  return out;
 }
 
-template <typename R, int NR, int PP>
+LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
+  std::vector<LaunchShape> c = apply_candidates(max_dim_dn, fp64, n_groups);
+  if (c.empty()) {
+    LaunchShape sh{};
+    sh.nr = 0;   // no feasible configuration
+    return sh;
+  }
+  return c.front();
+}
+
+template <typename R, int NR, int PP, int MINB>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
-  if (sh.vec) k_apply<R, NR, PP, (sizeof(R) == 4)><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
-  else k_apply<R, NR, PP, false><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
+  if (sh.vec) k_apply<R, NR, PP, (sizeof(R) == 4), MINB><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
+  else k_apply<R, NR, PP, false, MINB><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
 }
 
-template <typename R, int PP>
-static cudaError_t prepare_apply_r(const LaunchShape& sh) {
+template <typename R, int NR, int PP, int MINB>
+static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   const int sm = (int)sh.smem;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (sh.nr) {
-    case 1:
-      e = cudaFuncSetAttribute(k_apply<R, 1, PP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<R, 1, PP, (sizeof(R) == 4)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(k_apply<R, 2, PP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<R, 2, PP, (sizeof(R) == 4)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      break;
-    case 4:
-      e = cudaFuncSetAttribute(k_apply<R, 4, PP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<R, 4, PP, (sizeof(R) == 4)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      break;
-  }
-  return e;
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_apply<R, NR, PP, (sizeof(R) == 4), MINB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
-  if (sh.smem > 227 * 1024) return cudaErrorInvalidValue;
-  return fp64 ? prepare_apply_r<double, 1>(sh) : prepare_apply_r<float, 2>(sh);
-}
-
-template <typename R, int PP>
-static cudaError_t launch_apply_r(const BatchArgs& a, int nblk, const LaunchShape& sh,
-                                  int j, cudaStream_t s) {
-  switch (sh.nr) {
-    case 1: return launch_apply_t<R, 1, PP>(a, nblk, sh, j, s);
-    case 2: return launch_apply_t<R, 2, PP>(a, nblk, sh, j, s);
-    case 4: return launch_apply_t<R, 4, PP>(a, nblk, sh, j, s);
+  if (sh.nr < 1 || sh.smem > 227 * 1024) return cudaErrorInvalidValue;
+  switch (sh.cfg) {
+    case 0: return prepare_apply_t<float, 4, 2, 2>(sh);
+    case 1: return prepare_apply_t<float, 2, 2, 3>(sh);
+    case 2: return prepare_apply_t<float, 2, 1, 4>(sh);
+    case 3: return prepare_apply_t<float, 1, 2, 2>(sh);
+    case 4: return prepare_apply_t<double, 2, 1, 2>(sh);
+    case 5: return prepare_apply_t<double, 1, 1, 4>(sh);
+    case 6: return prepare_apply_t<double, 1, 1, 2>(sh);
     default: return cudaErrorInvalidValue;
   }
+  (void)fp64;
 }
 
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
                          int j, cudaStream_t s) {
-  return fp64 ? launch_apply_r<double, 1>(a, nblk, sh, j, s)
-              : launch_apply_r<float, 2>(a, nblk, sh, j, s);
+  (void)fp64;
+  switch (sh.cfg) {
+    case 0: return launch_apply_t<float, 4, 2, 2>(a, nblk, sh, j, s);
+    case 1: return launch_apply_t<float, 2, 2, 3>(a, nblk, sh, j, s);
+    case 2: return launch_apply_t<float, 2, 1, 4>(a, nblk, sh, j, s);
+    case 3: return launch_apply_t<float, 1, 2, 2>(a, nblk, sh, j, s);
+    case 4: return launch_apply_t<double, 2, 1, 2>(a, nblk, sh, j, s);
+    case 5: return launch_apply_t<double, 1, 1, 4>(a, nblk, sh, j, s);
+    case 6: return launch_apply_t<double, 1, 1, 2>(a, nblk, sh, j, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int nblk, int j, cudaStream_t s) {

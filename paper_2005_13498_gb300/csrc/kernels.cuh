@@ -16,7 +16,12 @@ struct LaunchShape {
   int nr;        // rows per CTA (apply blocks hold up to nr rows)
   size_t smem;   // dynamic shared memory of the apply kernel
   bool vec = false;  // complex64 rows accessed as 16-byte pairs
+  int cfg = 0;       // index of the kernel configuration (rows, pairs, occupancy)
 };
+
+// Feasible apply configurations for rows of length max_dim_dn (the first is
+// the default); the autotuner in engine.cpp times them on the real data.
+std::vector<LaunchShape> apply_candidates(int max_dim_dn, bool fp64, int n_groups);
 
 // Apply blocks of nr rows covering rows [0, dim_up) of vector vec.
 inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_up, int nr) {
