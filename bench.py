@@ -314,7 +314,11 @@ def main():
     value = job_value(t_ms, ws, args.steps)
     ms_step = t_ms / args.steps
     m_eff = out["m_eff"]
-    gpu_launches = 1 + args.steps * (2 * m + 1)
+    # kernels per step: m applies (two kernels each for the split apply),
+    # m - 1 updates, expm, combine; plus the observation launch
+    acfg = ed.ed_get_apply_config(h.ctx)[0]
+    ainfo = ed.ed_apply_config_info(acfg)
+    gpu_launches = 1 + args.steps * ((2 + ainfo["split"]) * m + 1)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -328,6 +332,7 @@ def main():
                        "l2": "no flush: per-step working set 2.9 GB (31 Krylov vectors of "
                              "94 MB) > 129 MB L2"},
             "clocks": clk.summary(), "gpu_launches": gpu_launches,
+            "apply_kernel": dict(ainfo, config=acfg),
             "ground_state": {"E0": E0, "residual": resid}}
 
     if not args.no_extras:
@@ -344,8 +349,10 @@ def main():
         for k in kern:
             kern[k]["share"] = kern[k]["ms_total"] / tot
         line["kernels"] = kern
-        # dominant kernel: the fused Lanczos apply; algorithmic bytes per launch
-        # averaged over j = 1..m: read x_j (+ x_{j-1} for j >= 2), write w.
+        # dominant kernel: the Lanczos apply (one kernel, or column pass + row
+        # pass for the split configuration, timed together); algorithmic bytes
+        # per launch averaged over j = 1..m: read x_j (+ x_{j-1} for j >= 2),
+        # write w.
         s = 8
         bytes_apply = (2 + 3 * (m - 1)) / m * D * s
         a_ms = kern["apply"]["ms_per_launch"]
@@ -356,7 +363,9 @@ def main():
             traffic = json.load(open(tp)).get("bytes_per_launch_c64_ladder")
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                            "kernel": "k_apply<float,16> (fused H x_j - beta s x_{j-1}, <v_j,w>)",
+                            "kernel": ("k_apply_up + k_apply (split" if ainfo["split"]
+                                       else "k_apply (one kernel") +
+                                      ": w = s_j H x_j - beta s x_{j-1}, <v_j,w>)",
                             "algorithmic_bytes_per_launch": bytes_apply,
                             "peak_kind": peak_kind + " (burst copy)"}
         # H.v bandwidth: 100 back-to-back plain applies (read v, write w)

@@ -233,6 +233,35 @@ ed_status ed_apply_fermion_op(ed_ctx* ctx, ed_ctx* ctx_dst, int site, int spin,
                               int create, const void* psi, void* out,
                               ed_dtype dtype, void* stream);
 
+/* Kernel configurations of H v (the matrix-vector product inside Lanczos,
+ * Eq. (18) applied as T_up (x) 1 + 1 (x) T_dn + diagonal, Sec. 3.2).  Each
+ * entry of the library's table fixes the precision, the rows of Psi one
+ * thread block owns (rows_per_cta), the column pairs per thread, the target
+ * thread blocks per SM, and whether the product runs as one kernel (split =
+ * 0: the T_up rows are gathered across the matrix) or as a column pass for
+ * T_up followed by a row pass for the diagonal and T_dn (split = 1).
+ * ed_apply_config_count returns the number of entries; ed_apply_config_info
+ * describes entry `config` (ED_ERR_ARG if out of range; any output pointer
+ * may be NULL).                                                              */
+int ed_apply_config_count(void);
+ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
+                               int* pairs_per_thread, int* ctas_per_sm,
+                               int* split);
+
+/* Process-wide choice of the H v configuration for every propagation,
+ * ed_apply_H plan and ground-state solve set up after the call (contexts
+ * rebuild their plans when it changes).  config = -1 (the default): an
+ * autotuner times the feasible entries once per precision and sector shape
+ * (sectors under 2^20 elements keep the first feasible entry); otherwise the
+ * given entry is used, and calls whose precision or sector it does not fit
+ * fail with ED_ERR_CUDA and a message naming it.  ED_ERR_ARG if config is
+ * not -1 and not a table index.                                             */
+ed_status ed_set_apply_config(int config);
+
+/* The configuration the context's propagation engine (*propagate) and its
+ * ed_apply_H plan (*apply) use, or -1 where none has been set up yet.        */
+ed_status ed_get_apply_config(const ed_ctx* ctx, int* propagate, int* apply);
+
 /* Bytes of device memory the context currently holds (tables + workspace).  */
 ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes);
 

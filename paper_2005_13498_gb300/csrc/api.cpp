@@ -55,6 +55,9 @@ cudaError_t upload_sector(SectorGPU& S) {
   if ((e = upload(S.dn_tslot_off, S.dn.tslot_off)) != cudaSuccess) return e;
   if ((e = upload(S.dn_slot_grp, S.dn.slot_grp)) != cudaSuccess) return e;
   if ((e = upload(S.dn_ell, S.dn.ell)) != cudaSuccess) return e;
+  if ((e = upload(S.up_tslot_off, S.up.tslot_off)) != cudaSuccess) return e;
+  if ((e = upload(S.up_slot_grp, S.up.slot_grp)) != cudaSuccess) return e;
+  if ((e = upload(S.up_ell, S.up.ell)) != cudaSuccess) return e;
   if (S.has_eps) {
     if ((e = upload(S.up_eps, S.up.eps_sum)) != cudaSuccess) return e;
     if ((e = upload(S.dn_eps, S.dn.eps_sum)) != cudaSuccess) return e;
@@ -81,6 +84,9 @@ cudaError_t upload_sector(SectorGPU& S) {
   d.dn_tslot_off = static_cast<const int32_t*>(S.dn_tslot_off.p);
   d.dn_slot_grp = static_cast<const uint32_t*>(S.dn_slot_grp.p);
   d.dn_ell = static_cast<const uint32_t*>(S.dn_ell.p);
+  d.up_tslot_off = static_cast<const int32_t*>(S.up_tslot_off.p);
+  d.up_slot_grp = static_cast<const uint32_t*>(S.up_slot_grp.p);
+  d.up_ell = static_cast<const uint32_t*>(S.up_ell.p);
   S.uploaded = true;
   return cudaSuccess;
 }
@@ -221,10 +227,40 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
   int64_t b = S.up_off.bytes + S.up_ent.bytes + S.dn_off.bytes + S.dn_ent.bytes +
               S.up_word.bytes + S.dn_word.bytes + S.up_eps.bytes + S.dn_eps.bytes +
               S.up_pad_off.bytes + S.up_pad_ent.bytes + S.up_pad_row.bytes + S.dn_tslot_off.bytes +
-              S.dn_slot_grp.bytes + S.dn_ell.bytes;
+              S.dn_slot_grp.bytes + S.dn_ell.bytes + S.up_tslot_off.bytes + S.up_slot_grp.bytes +
+              S.up_ell.bytes;
   if (ctx->engine) b += ctx->engine->device_bytes();
   if (ctx->spec_engine) b += ctx->spec_engine->device_bytes();
   *bytes = b;
+  return ED_OK;
+}
+
+int ed_apply_config_count(void) { return apply_config_count(); }
+
+ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
+                               int* pairs_per_thread, int* ctas_per_sm, int* split) {
+  int f, nr, pp, mb, sp;
+  if (!apply_config_info(config, &f, &nr, &pp, &mb, &sp))
+    return fail(nullptr, ED_ERR_ARG, "no apply configuration " + std::to_string(config));
+  if (fp64) *fp64 = f;
+  if (rows_per_cta) *rows_per_cta = nr;
+  if (pairs_per_thread) *pairs_per_thread = pp;
+  if (ctas_per_sm) *ctas_per_sm = mb;
+  if (split) *split = sp;
+  return ED_OK;
+}
+
+ed_status ed_set_apply_config(int config) {
+  if (config < -1 || config >= apply_config_count())
+    return fail(nullptr, ED_ERR_ARG, "apply configuration must be -1 or a table index");
+  set_forced_apply_config(config);
+  return ED_OK;
+}
+
+ed_status ed_get_apply_config(const ed_ctx* ctx, int* propagate, int* apply) {
+  if (!ctx || !propagate || !apply) return fail(nullptr, ED_ERR_ARG, "NULL argument");
+  *propagate = ctx->engine ? ctx->engine->apply_config() : -1;
+  *apply = ctx->plan.valid ? ctx->plan.shape.cfg : -1;
   return ED_OK;
 }
 
@@ -239,7 +275,10 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
   const bool fp64 = dtype == ED_C128;
   ApplyPlan& P = ctx->plan;
   const bool same_field = P.A[0] == ctx->A[0] && P.A[1] == ctx->A[1] && P.A[2] == ctx->A[2];
-  if (!(P.valid && P.nvec == nvec && P.v == v && P.w == w && P.fp64 == fp64 && same_field)) {
+  const int forced = forced_apply_config();
+  const bool same_cfg = forced < 0 || forced == P.shape.cfg;
+  if (!(P.valid && P.nvec == nvec && P.v == v && P.w == w && P.fp64 == fp64 && same_field &&
+        same_cfg)) {
     if (!is_device_ptr(v) || !is_device_ptr(w))
       return fail(ctx, ED_ERR_ARG, "ed_apply_H needs device pointers");
     P.valid = false;
@@ -279,18 +318,20 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     P.args.nvec = nvec;
     P.args.Ns = ctx->Ns;
     P.args.max_dim_dn = (int)ctx->dim_dn;
+    P.args.max_dim_up = (int)ctx->dim_up;
     P.args.U = ctx->lat.U;
     ApplyTuneTarget tt;
     tt.fp64 = fp64;
     tt.vec_ok = !fp64 && (ctx->dim_dn % 2 == 0) &&
                 ((((uintptr_t)v) | ((uintptr_t)w)) & 15u) == 0;
+    tt.max_dim_up = (int)ctx->dim_up;
     tt.max_dim_dn = (int)ctx->dim_dn;
     tt.n_groups = ng;
     tt.dim_up.assign(nvec, (int)ctx->dim_up);
     tt.dim_dn.assign(nvec, (int)ctx->dim_dn);
     tt.args = P.args;
-    std::vector<ApplyBlock> amap;
-    CKS(ctx, tune_apply(tt, s, &P.shape, &amap));
+    std::vector<ApplyBlock> amap, cmap;
+    CKS(ctx, tune_apply(tt, s, &P.shape, &amap, &cmap));
     CK(ctx, prepare_apply(fp64, P.shape));
     for (int b = 0; b < (int)amap.size(); ++b) {
       VecDev& vv = vd[amap[b].vec];
@@ -299,9 +340,12 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     }
     CK(ctx, upload(P.vec, vd));
     CK(ctx, upload(P.amap, amap));
+    CK(ctx, upload(P.cmap, cmap));
     CK(ctx, P.partials.alloc(sizeof(double) * 4 * amap.size()));
     P.args.vec = static_cast<VecDev*>(P.vec.p);
     P.args.apply_map = static_cast<const ApplyBlock*>(P.amap.p);
+    P.args.col_map = static_cast<const ApplyBlock*>(P.cmap.p);
+    P.args.n_col_blocks = (int)cmap.size();
     P.args.partials = static_cast<double*>(P.partials.p);
     P.nblk = (int)amap.size();
     P.nvec = nvec;

@@ -19,6 +19,7 @@ constexpr uint32_t kEntRankMask = 0xFFFFu;
 constexpr int kEntGroupShift = 16;
 constexpr uint32_t kEntSignBit = 0x80000000u;
 constexpr uint32_t kNullEntryBit = 0x40000000u;  // padding entry of a row list
+constexpr uint32_t kEllNull = 0x7FFFFFFFu;       // empty ELL slot of a lane (no load)
 
 // Device view of one sector's tables (pointers into device memory).
 struct SectorDev {
@@ -40,6 +41,10 @@ struct SectorDev {
   const int32_t* dn_tslot_off; // [ceil(dim_dn/64) + 1], even slot counts
   const uint32_t* dn_slot_grp; // group of each slot
   const uint32_t* dn_ell;      // [slots][32 lanes][2]: tile_offset(rank) | sign << 31
+  // up spin, same layout over 64-row tiles (the column pass of the split apply)
+  const int32_t* up_tslot_off;
+  const uint32_t* up_slot_grp;
+  const uint32_t* up_ell;
 };
 
 // Per-vector Lanczos scalars, all float64, 1-based Krylov index j.
@@ -88,7 +93,8 @@ struct EwBlock {
   int64_t begin, end;
 };
 
-// Apply block: rows [row0, row0 + nrows) of vector vec.
+// Apply block: rows [row0, row0 + nrows) of vector vec (for the column pass
+// of the split apply: columns [row0, row0 + nrows)).
 struct ApplyBlock {
   int vec;
   int row0;
@@ -102,6 +108,7 @@ struct BatchArgs {
   VecDev* vec;
   LanczosState* st;
   const ApplyBlock* apply_map;
+  const ApplyBlock* col_map;  // split apply: column blocks (row0 = first column)
   const EwBlock* ew_map;
   double* partials;       // >= 4 * max(#apply blocks, #ew blocks)
   unsigned* counters;     // [nvec], zero between kernels
@@ -111,6 +118,8 @@ struct BatchArgs {
   int nvec;
   int Ns;
   int max_dim_dn;
+  int max_dim_up;
+  int n_col_blocks;
   double U;
   double tau;
   double break_tol;

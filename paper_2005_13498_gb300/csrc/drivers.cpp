@@ -90,7 +90,7 @@ void lowest_eigenpair(const std::vector<double>& a, const std::vector<double>& b
 }
 
 struct GsApply {
-  DevMem sec, vec, st, amap, partials, counters, coefs;
+  DevMem sec, vec, st, amap, cmap, partials, counters, coefs;
   BatchArgs args{};
   LaunchShape shape{};
   int nblk = 0;
@@ -127,25 +127,30 @@ std::string gs_apply_setup(GsApply& G, ed_ctx* ctx, const double2* x, double2* w
   G.args.nvec = 1;
   G.args.Ns = ctx->Ns;
   G.args.max_dim_dn = (int)ctx->dim_dn;
+  G.args.max_dim_up = (int)ctx->dim_up;
   G.args.U = ctx->lat.U;
   ApplyTuneTarget tt;
   tt.fp64 = true;
   tt.vec_ok = false;
+  tt.max_dim_up = (int)ctx->dim_up;
   tt.max_dim_dn = (int)ctx->dim_dn;
   tt.n_groups = ng;
   tt.dim_up = {(int)ctx->dim_up};
   tt.dim_dn = {(int)ctx->dim_dn};
   tt.args = G.args;
-  std::vector<ApplyBlock> amap;
-  std::string err = tune_apply(tt, s, &G.shape, &amap);
+  std::vector<ApplyBlock> amap, cmap;
+  std::string err = tune_apply(tt, s, &G.shape, &amap, &cmap);
   if (!err.empty()) return err;
   vd[0].apply_begin = 0;
   vd[0].apply_end = (int)amap.size();
   ED_TRY(upload(G.vec, vd));
   ED_TRY(upload(G.amap, amap));
+  ED_TRY(upload(G.cmap, cmap));
   ED_TRY(G.partials.alloc(sizeof(double) * 4 * amap.size()));
   G.args.vec = static_cast<VecDev*>(G.vec.p);
   G.args.apply_map = static_cast<const ApplyBlock*>(G.amap.p);
+  G.args.col_map = static_cast<const ApplyBlock*>(G.cmap.p);
+  G.args.n_col_blocks = (int)cmap.size();
   G.args.partials = static_cast<double*>(G.partials.p);
   G.nblk = (int)amap.size();
   ED_TRY(prepare_apply(true, G.shape));

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -33,13 +34,20 @@ Engine::~Engine() {
 }
 
 size_t Engine::device_bytes() const {
-  return d_sec_.bytes + d_vec_.bytes + d_st_.bytes + d_amap_.bytes + d_emap_.bytes +
+  return d_sec_.bytes + d_vec_.bytes + d_st_.bytes + d_amap_.bytes + d_cmap_.bytes +
+         d_emap_.bytes +
          d_partials_.bytes + d_counters_.bytes + d_coefs_.bytes + d_coefs_obs_.bytes +
          d_V_.bytes + d_w_.bytes + d_out_.bytes + d_owned_x1_.bytes + d_maps_.bytes +
          d_map_off_.bytes + d_map_spin_.bytes + d_ovl_.bytes;
 }
 
+static std::atomic<int> g_forced_cfg{-1};
+void set_forced_apply_config(int cfg) { g_forced_cfg.store(cfg); }
+int forced_apply_config() { return g_forced_cfg.load(); }
+
 bool Engine::compatible(const EngineConfig& cfg, const std::vector<EngineVector>& vecs) const {
+  const int forced = forced_apply_config();
+  if (forced >= 0 && forced != shape_.cfg) return false;
   if (cfg.fp64 != cfg_.fp64 || cfg.m != cfg_.m || cfg.energy != cfg_.energy ||
       cfg.overlaps != cfg_.overlaps || cfg.n_steps_cap > cfg_.n_steps_cap)
     return false;
@@ -53,17 +61,32 @@ bool Engine::compatible(const EngineConfig& cfg, const std::vector<EngineVector>
 }
 
 std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* shape,
-                       std::vector<ApplyBlock>* map) {
+                       std::vector<ApplyBlock>* map, std::vector<ApplyBlock>* cmap) {
   static std::mutex mu;
   static std::map<std::string, int> cache;
-  std::vector<LaunchShape> cands = apply_candidates(t.max_dim_dn, t.fp64, t.n_groups);
+  std::vector<LaunchShape> cands =
+      apply_candidates(t.max_dim_up, t.max_dim_dn, t.fp64, t.n_groups);
   if (cands.empty()) return "apply kernel: rows too long for shared memory";
   for (auto& c : cands) c.vec = t.vec_ok;
   auto build = [&](const LaunchShape& sh) {
     map->clear();
-    for (size_t i = 0; i < t.dim_up.size(); ++i)
+    cmap->clear();
+    for (size_t i = 0; i < t.dim_up.size(); ++i) {
       append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr);
+      if (sh.split) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64);
+    }
   };
+  const int forced = forced_apply_config();
+  if (forced >= 0) {
+    for (const LaunchShape& c : cands)
+      if (c.cfg == forced) {
+        *shape = c;
+        build(c);
+        return "";
+      }
+    return "apply configuration " + std::to_string(forced) +
+           " does not fit this precision and sector";
+  }
   std::string key = (t.fp64 ? "d" : "f") + std::string(t.vec_ok ? "v" : "s");
   for (size_t i = 0; i < t.dim_up.size(); ++i)
     key += ":" + std::to_string(t.dim_up[i]) + "x" + std::to_string(t.dim_dn[i]);
@@ -95,16 +118,22 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
   std::string err;
   for (const LaunchShape& c : cands) {
     build(c);
-    DevMem dmap;
+    DevMem dmap, dcmap;
     if (dmap.alloc(map->size() * sizeof(ApplyBlock)) != cudaSuccess ||
         cudaMemcpy(dmap.p, map->data(), map->size() * sizeof(ApplyBlock),
                    cudaMemcpyHostToDevice) != cudaSuccess ||
+        dcmap.alloc(std::max<size_t>(1, cmap->size()) * sizeof(ApplyBlock)) != cudaSuccess ||
+        (!cmap->empty() &&
+         cudaMemcpy(dcmap.p, cmap->data(), cmap->size() * sizeof(ApplyBlock),
+                    cudaMemcpyHostToDevice) != cudaSuccess) ||
         prepare_apply(t.fp64, c) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     BatchArgs a = t.args;
     a.apply_map = static_cast<const ApplyBlock*>(dmap.p);
+    a.col_map = static_cast<const ApplyBlock*>(dcmap.p);
+    a.n_col_blocks = (int)cmap->size();
     const int nblk = (int)map->size();
     if (launch_apply(t.fp64, a, nblk, c, 0, s) != cudaSuccess) { cudaGetLastError(); continue; }
     cudaEventRecord(e0, s);
@@ -170,8 +199,11 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   std::vector<ApplyBlock> amap;
   std::vector<EwBlock> emap;
   std::vector<VecDev> vd(nv);
-  int max_dim_dn = 1;
-  for (int i = 0; i < nv; ++i) max_dim_dn = std::max(max_dim_dn, sectors_[vecs_[i].sector].dim_dn);
+  int max_dim_dn = 1, max_dim_up = 1;
+  for (int i = 0; i < nv; ++i) {
+    max_dim_dn = std::max(max_dim_dn, sectors_[vecs_[i].sector].dim_dn);
+    max_dim_up = std::max(max_dim_up, sectors_[vecs_[i].sector].dim_up);
+  }
   int64_t voff = 0;
   const int ncap = cfg.n_steps_cap;
   // outputs per vector: docc, norm2, energy [ncap+1], delta [ncap], meff [ncap]
@@ -238,6 +270,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   args_.nvec = nv;
   args_.Ns = Ns;
   args_.max_dim_dn = max_dim_dn;
+  args_.max_dim_up = max_dim_up;
   args_.U = U;
   args_.tau = 0.0;
   args_.break_tol = break_tol;
@@ -246,6 +279,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   ApplyTuneTarget tt;
   tt.fp64 = cfg.fp64;
   tt.vec_ok = vec_ok;
+  tt.max_dim_up = max_dim_up;
   tt.max_dim_dn = max_dim_dn;
   tt.n_groups = n_groups;
   for (int i = 0; i < nv; ++i) {
@@ -253,7 +287,8 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     tt.dim_dn.push_back(sectors_[vecs_[i].sector].dim_dn);
   }
   tt.args = args_;
-  std::string err = tune_apply(tt, stream, &shape_, &amap);
+  std::vector<ApplyBlock> cmap;
+  std::string err = tune_apply(tt, stream, &shape_, &amap, &cmap);
   if (!err.empty()) return err;
   ED_TRY(prepare_apply(cfg.fp64, shape_));
   n_apply_ = (int)amap.size();
@@ -267,6 +302,10 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     v.apply_end = b + 1;
   }
   ED_TRY(d_amap_.alloc(sizeof(ApplyBlock) * amap.size()));
+  ED_TRY(d_cmap_.alloc(sizeof(ApplyBlock) * std::max<size_t>(1, cmap.size())));
+  if (!cmap.empty())
+    ED_TRY(cudaMemcpyAsync(d_cmap_.p, cmap.data(), sizeof(ApplyBlock) * cmap.size(),
+                           cudaMemcpyHostToDevice, stream));
   ED_TRY(d_partials_.alloc(sizeof(double) * 4 * std::max(n_apply_, n_ew_)));
   ED_TRY(cudaMemcpyAsync(d_vec_.p, vd.data(), sizeof(VecDev) * nv, cudaMemcpyHostToDevice,
                          stream));
@@ -275,6 +314,8 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   ED_TRY(cudaMemsetAsync(d_counters_.p, 0, sizeof(unsigned) * nv, stream));
   ED_TRY(cudaStreamSynchronize(stream));
   args_.apply_map = static_cast<const ApplyBlock*>(d_amap_.p);
+  args_.col_map = static_cast<const ApplyBlock*>(d_cmap_.p);
+  args_.n_col_blocks = (int)cmap.size();
   args_.partials = static_cast<double*>(d_partials_.p);
   return "";
 }

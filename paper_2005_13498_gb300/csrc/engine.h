@@ -50,14 +50,23 @@ struct EngineConfig {
 struct ApplyTuneTarget {
   bool fp64 = false;
   bool vec_ok = false;          // complex64 rows may be read as 16-byte pairs
+  int max_dim_up = 1;
   int max_dim_dn = 1;
   int n_groups = 0;
   std::vector<int> dim_up;      // per vector
   std::vector<int> dim_dn;      // per vector
-  BatchArgs args{};             // vec / sec / coefs valid; apply_map is set here
+  BatchArgs args{};             // vec / sec / coefs valid; the block maps are set here
 };
+// Process-wide choice of the apply configuration: -1 lets the autotuner pick
+// (default), otherwise the index into the configuration table is used for
+// every engine and plan set up afterwards (tune_apply fails if that
+// configuration does not fit the precision or sector).
+void set_forced_apply_config(int cfg);
+int forced_apply_config();
+// Picks the apply configuration and returns its row-block map and (split
+// shapes) its column-block map.
 std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* shape,
-                       std::vector<ApplyBlock>* map);
+                       std::vector<ApplyBlock>* map, std::vector<ApplyBlock>* cmap);
 
 class Engine {
  public:
@@ -67,6 +76,7 @@ class Engine {
                     const std::vector<EngineVector>& vecs, int n_groups, int Ns,
                     double U, double break_tol, cudaStream_t stream);
   bool compatible(const EngineConfig& cfg, const std::vector<EngineVector>& vecs) const;
+  int apply_config() const { return shape_.cfg; }
   // Upload per-step coefficients ([n_steps][n_groups] complex double; energy
   // coefficients [n_steps+1][n_groups] or empty) and reset the Lanczos state.
   std::string begin(const std::vector<double>& coefs, const std::vector<double>& coefs_obs,
@@ -101,7 +111,7 @@ class Engine {
   BatchArgs args_{};
   OverlapArgs oargs_{};
   bool have_overlaps_ = false;
-  DevMem d_sec_, d_vec_, d_st_, d_amap_, d_emap_, d_partials_, d_counters_;
+  DevMem d_sec_, d_vec_, d_st_, d_amap_, d_cmap_, d_emap_, d_partials_, d_counters_;
   DevMem d_coefs_, d_coefs_obs_, d_V_, d_w_, d_out_, d_owned_x1_;
   DevMem d_maps_, d_map_off_, d_map_spin_, d_ovl_;
   cudaGraph_t graph_ = nullptr;

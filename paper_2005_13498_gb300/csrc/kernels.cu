@@ -126,25 +126,31 @@ constexpr int kApplyThreads = 256;
 
 // Column pair (2p, 2p+1) of a row: one 16-byte access for aligned complex64
 // rows (VEC), else two element accesses with the second column checked.
-template <typename C, bool VEC>
+// STREAM: data read or written once in this pass (the previous Krylov vector,
+// the output w): evict-first cache hints, so that the vector whose rows are
+// gathered stays in L2.
+template <typename C, bool VEC, bool STREAM = false>
 __device__ __forceinline__ void load_pair(const C* row, int p, int dim, C& v0, C& v1) {
   if constexpr (VEC) {
-    const float4 f = *(reinterpret_cast<const float4*>(row) + p);
+    const float4* a = reinterpret_cast<const float4*>(row) + p;
+    const float4 f = STREAM ? __ldcs(a) : *a;
     v0.x = f.x; v0.y = f.y; v1.x = f.z; v1.y = f.w;
   } else {
     const int d = 2 * p;
-    v0 = row[d];
-    if (d + 1 < dim) v1 = row[d + 1]; else v1 = czero<C>();
+    v0 = STREAM ? __ldcs(row + d) : row[d];
+    if (d + 1 < dim) v1 = STREAM ? __ldcs(row + d + 1) : row[d + 1]; else v1 = czero<C>();
   }
 }
-template <typename C, bool VEC>
+template <typename C, bool VEC, bool STREAM = false>
 __device__ __forceinline__ void store_pair(C* row, int p, int dim, C v0, C v1) {
   if constexpr (VEC) {
-    reinterpret_cast<float4*>(row)[p] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    float4* a = reinterpret_cast<float4*>(row) + p;
+    const float4 f = make_float4(v0.x, v0.y, v1.x, v1.y);
+    if (STREAM) __stcs(a, f); else *a = f;
   } else {
     const int d = 2 * p;
-    row[d] = v0;
-    if (d + 1 < dim) row[d + 1] = v1;
+    if (STREAM) __stcs(row + d, v0); else row[d] = v0;
+    if (d + 1 < dim) { if (STREAM) __stcs(row + d + 1, v1); else row[d + 1] = v1; }
   }
 }
 
@@ -175,6 +181,10 @@ struct TileIO {
         v[0] = *reinterpret_cast<const C*>(&a);
         v[1] = *reinterpret_cast<const C*>(&b);
       }
+    } else if constexpr (kBytes == 16) {
+      const float4 a = reinterpret_cast<const float4*>(tile)[d];
+      v[0] = *reinterpret_cast<const C*>(&a);
+      if constexpr (NR == 2) v[1] = *(reinterpret_cast<const C*>(&a) + 1);
     } else {
 #pragma unroll
       for (int r = 0; r < NR; ++r) v[r] = tile[(size_t)d * NR + r];
@@ -184,6 +194,11 @@ struct TileIO {
   // chunk for 32-byte columns, else rank = offset >> 5
   __device__ static __forceinline__ void load_ent(const C* tile, uint32_t ent, C (&v)[NR]) {
     const uint32_t off = ent & 0x7FFFFFFFu;
+    if (off == kEllNull) {   // empty slot of this lane: no shared-memory access
+#pragma unroll
+      for (int r = 0; r < NR; ++r) v[r] = czero<C>();
+      return;
+    }
     if constexpr (kBytes == 32) {
       const char* base = reinterpret_cast<const char*>(tile);
       const float4 a = *reinterpret_cast<const float4*>(base + off);
@@ -196,6 +211,14 @@ struct TileIO {
         v[0].y = __longlong_as_double(((long long)__float_as_int(a.w) << 32) | (unsigned)__float_as_int(a.z));
         v[1].x = __longlong_as_double(((long long)__float_as_int(b.y) << 32) | (unsigned)__float_as_int(b.x));
         v[1].y = __longlong_as_double(((long long)__float_as_int(b.w) << 32) | (unsigned)__float_as_int(b.z));
+      }
+    } else if constexpr (kBytes == 16) {
+      const float4 a = reinterpret_cast<const float4*>(tile)[off >> 5];
+      if constexpr (sizeof(C) == 8) {
+        v[0].x = a.x; v[0].y = a.y; v[1].x = a.z; v[1].y = a.w;
+      } else {
+        v[0].x = __longlong_as_double(((long long)__float_as_int(a.y) << 32) | (unsigned)__float_as_int(a.x));
+        v[0].y = __longlong_as_double(((long long)__float_as_int(a.w) << 32) | (unsigned)__float_as_int(a.z));
       }
     } else {
       load(tile, (int)(off >> 5), v);
@@ -215,6 +238,11 @@ struct TileIO {
       }
       t[2 * d + sw] = a;
       t[2 * d + (sw ^ 1)] = b;
+    } else if constexpr (kBytes == 16) {
+      float4 a;
+      *reinterpret_cast<C*>(&a) = v[0];
+      if constexpr (NR == 2) *(reinterpret_cast<C*>(&a) + 1) = v[1];
+      reinterpret_cast<float4*>(tile)[d] = a;
     } else {
 #pragma unroll
       for (int r = 0; r < NR; ++r) tile[(size_t)d * NR + r] = v[r];
@@ -239,7 +267,7 @@ struct TileIO {
 //    row per k, all in flight before they are summed by group.
 //  * Epilogue: w = s_j acc - beta_{j-1} s_{j-1} x_{j-1}, stored in pairs,
 //    and the partial of Re<x_j, w>.
-template <typename R, int NR, int PP, bool VEC, int MINB>
+template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT>
 __global__ void __launch_bounds__(kApplyThreads, MINB)
 k_apply(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
@@ -355,10 +383,24 @@ k_apply(BatchArgs a, int j) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) { s0v[r] = czero<C>(); s1v[r] = czero<C>(); }
         uint32_t gcur = q0 < q1 ? __ldg(sd.dn_slot_grp + q0) : 0u;
+        // entries of the next two slots are loaded while this pair is gathered
+        uint2 na = make_uint2(0u, 0u), nb = na;
+        uint32_t nga = 0u, ngb = 0u;
+        if (q0 < q1) {
+          na = __ldg(ell2 + (size_t)q0 * 32 + lane);
+          nb = __ldg(ell2 + (size_t)(q0 + 1) * 32 + lane);
+          nga = __ldg(sd.dn_slot_grp + q0);
+          ngb = __ldg(sd.dn_slot_grp + q0 + 1);
+        }
         for (int q = q0; q < q1; q += 2) {
-          const uint2 ea = __ldg(ell2 + (size_t)q * 32 + lane);
-          const uint2 eb = __ldg(ell2 + (size_t)(q + 1) * 32 + lane);
-          const uint32_t ga = __ldg(sd.dn_slot_grp + q), gb = __ldg(sd.dn_slot_grp + q + 1);
+          const uint2 ea = na, eb = nb;
+          const uint32_t ga = nga, gb = ngb;
+          if (q + 2 < q1) {
+            na = __ldg(ell2 + (size_t)(q + 2) * 32 + lane);
+            nb = __ldg(ell2 + (size_t)(q + 3) * 32 + lane);
+            nga = __ldg(sd.dn_slot_grp + q + 2);
+            ngb = __ldg(sd.dn_slot_grp + q + 3);
+          }
           C a0[NR], a1[NR], b0[NR], b1[NR];
           TIO::load_ent(tile, ea.x, a0);
           TIO::load_ent(tile, ea.y, a1);
@@ -414,21 +456,49 @@ k_apply(BatchArgs a, int j) {
       pvalid[k] = p < npairs;
       xb4[k] = reinterpret_cast<const float4*>(x) + p;
     }
+    // ---- split apply: the column pass stored (T_up x) in w; add its rows
+    if constexpr (SPLIT) {
+      C tv[NR][2 * PP];
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+          if (r < nrows && pvalid[k])
+            load_pair<C, VEC, true>(w + (size_t)(u0 + r) * dim_dn, pc + tid + k * T, dim_dn,
+                                    tv[r][2 * k], tv[r][2 * k + 1]);
+          else { tv[r][2 * k] = czero<C>(); tv[r][2 * k + 1] = czero<C>(); }
+        }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int k = 0; k < 2 * PP; ++k) {
+          acc[r][k].x += tv[r][k].x;
+          acc[r][k].y += tv[r][k].y;
+        }
+    }
     // ---- T_up: the padded entry list of each row (uniform over the block),
     // four entries per batch with all their row loads in flight, coefficient
     // applied when the group changes
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      if (r < nrows) {
+      if (!SPLIT && r < nrows) {
         const int u = u0 + r;
         const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
         C sum[2 * PP];
 #pragma unroll
         for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
         uint32_t gcur = e0 < e1 ? ((__ldg(sd.up_pad_ent + e0) >> kEntGroupShift) & 0xFFu) : 0u;
+        uint4 nent = make_uint4(0u, 0u, 0u, 0u), nrow = nent;
+        if (e0 < e1) {
+          nent = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_ent + e0));
+          nrow = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_row + e0));
+        }
         for (int e = e0; e < e1; e += 4) {
-          const uint4 ent4 = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_ent + e));
-          const uint4 row4 = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_row + e));
+          const uint4 ent4 = nent, row4 = nrow;
+          if (e + 4 < e1) {   // the next batch's entries load under this batch's rows
+            nent = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_ent + e + 4));
+            nrow = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_row + e + 4));
+          }
           const uint32_t ents[4] = {ent4.x, ent4.y, ent4.z, ent4.w};
           const uint32_t rows[4] = {row4.x, row4.y, row4.z, row4.w};
           C v[4][2 * PP];
@@ -490,7 +560,8 @@ k_apply(BatchArgs a, int j) {
       for (int k = 0; k < PP; ++k) {
         const int p = pc + tid + k * T;
         if (xp && r < nrows && p < npairs)
-          load_pair<C, VEC>(xp + (size_t)(u0 + r) * dim_dn, p, dim_dn, pv[r][2 * k], pv[r][2 * k + 1]);
+          load_pair<C, VEC, true>(xp + (size_t)(u0 + r) * dim_dn, p, dim_dn, pv[r][2 * k],
+                                  pv[r][2 * k + 1]);
         else { pv[r][2 * k] = czero<C>(); pv[r][2 * k + 1] = czero<C>(); }
       }
     R dot_acc = (R)0;
@@ -509,7 +580,7 @@ k_apply(BatchArgs a, int j) {
             o0.y = s_in * acc[r][2 * k].y - s_prev * pv[r][2 * k].y;
             o1.x = s_in * acc[r][2 * k + 1].x - s_prev * pv[r][2 * k + 1].x;
             o1.y = s_in * acc[r][2 * k + 1].y - s_prev * pv[r][2 * k + 1].y;
-            store_pair<C, VEC>(w + (size_t)(u0 + r) * dim_dn, p, dim_dn, o0, o1);
+            store_pair<C, VEC, true>(w + (size_t)(u0 + r) * dim_dn, p, dim_dn, o0, o1);
             dot_acc += xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
           }
         }
@@ -527,6 +598,195 @@ k_apply(BatchArgs a, int j) {
         if (!isfinite(v[0])) { st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1; }
       } else {
         if (vd.out_energy) vd.out_energy[st->step] = v[0] / a.Ns;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- split apply: columns
+// Column pass of the split apply: w[u, d] = sum_u' T_up[u, u'] x[u', d] for
+// the NC = 32 bytes / sizeof(C) columns d0 .. d0 + ncols - 1 of every row u
+// (4 complex64 or 2 complex128 columns).  Those columns of all dim_up rows
+// are staged in shared memory in the TileIO layout with the row index u in
+// the role of the column (32 bytes per u, two zero rows past the end that
+// padding entries point to), then each warp walks the warp-tiled ELL of the
+// up table over 64 target rows exactly like the within-row T_dn gathers.
+// Reading and writing 32-byte row segments keeps the whole pass at one read
+// of x and one write of w; the row pass (k_apply with SPLIT) adds the
+// diagonal and T_dn and finishes the Lanczos epilogue.
+template <typename R, int PP, bool VEC, int MINB>
+__global__ void __launch_bounds__(kApplyThreads, MINB)
+k_apply_up(BatchArgs a, int j) {
+  using C = typename C2T<R>::T;
+  constexpr int NC = 32 / (int)sizeof(C);
+  using TIO = TileIO<C, NC>;
+  constexpr int T = kApplyThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+
+  const ApplyBlock cb = a.col_map[blockIdx.x];
+  const VecDev vd = a.vec[cb.vec];
+  const LanczosState* st = a.st + cb.vec;
+  if (j >= 1 && st->stopped) return;   // uniform over the vector's blocks
+  const SectorDev sd = a.sec[vd.sector];
+  const int dim_up = sd.dim_up, dim_dn = sd.dim_dn;
+  const int d0 = cb.row0, ncols = cb.nrows;
+  const int npairs = (dim_up + 1) >> 1;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+
+  C* tile = reinterpret_cast<C*>(smem_raw);               // [max_dim_up + 2][NC]
+  C* coefS = tile + (size_t)(a.max_dim_up + 2) * NC;     // [n_groups]
+  const void* cbase;
+  if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
+  else if (j == 0) cbase = a.coefs;
+  else cbase = static_cast<const char*>(a.coefs_obs) + (size_t)st->step * a.n_groups * sizeof(C);
+  for (int g = tid; g < a.n_groups; g += T) coefS[g] = reinterpret_cast<const C*>(cbase)[g];
+
+  const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
+  C* w = static_cast<C*>(vd.w);
+
+  // ---- stage: 16-byte halves h of the 32-byte segment of each row u; half
+  // h holds columns h*NC/2 .. h*NC/2 + NC/2 - 1, stored at byte
+  // 32u + 16 (sw(u) ^ h) of the tile.  Four halves per thread in flight.
+  {
+    char* tb = reinterpret_cast<char*>(tile);
+    const int nunits = 2 * (dim_up + 2);
+    for (int i0 = tid; i0 < nunits; i0 += 4 * T) {
+      float4 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q * T;
+        const int u = i >> 1, h = i & 1;
+        v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < nunits && u < dim_up) {
+          const C* src = x + (size_t)u * dim_dn + d0 + h * (NC / 2);
+          if constexpr (sizeof(C) == 16) {
+            if (h < ncols) v[q] = __ldg(reinterpret_cast<const float4*>(src));
+          } else if constexpr (VEC) {
+            if (2 * h < ncols) v[q] = __ldg(reinterpret_cast<const float4*>(src));
+          } else {
+            if (2 * h < ncols) { const C e = src[0]; v[q].x = e.x; v[q].y = e.y; }
+            if (2 * h + 1 < ncols) { const C e = src[1]; v[q].z = e.x; v[q].w = e.y; }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q * T;
+        if (i < nunits) {
+          const int u = i >> 1, h = i & 1;
+          *reinterpret_cast<float4*>(tb + 32 * (size_t)u + 16 * (((u >> 2) & 1) ^ h)) = v[q];
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  for (int pc = 0; pc < npairs; pc += T * PP) {
+    C acc[NC][2 * PP];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int k = 0; k < 2 * PP; ++k) acc[c][k] = czero<C>();
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+      const int pw0 = pc + (tid - lane) + k * T;     // first pair of the warp
+      if (pw0 < npairs) {                             // uniform over the warp
+        const int tw = pw0 >> 5;
+        const int q0 = __ldg(sd.up_tslot_off + tw), q1 = __ldg(sd.up_tslot_off + tw + 1);
+        const uint2* ell2 = reinterpret_cast<const uint2*>(sd.up_ell);
+        C s0v[NC], s1v[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { s0v[c] = czero<C>(); s1v[c] = czero<C>(); }
+        uint32_t gcur = q0 < q1 ? __ldg(sd.up_slot_grp + q0) : 0u;
+        uint2 na = make_uint2(0u, 0u), nb = na;
+        uint32_t nga = 0u, ngb = 0u;
+        if (q0 < q1) {
+          na = __ldg(ell2 + (size_t)q0 * 32 + lane);
+          nb = __ldg(ell2 + (size_t)(q0 + 1) * 32 + lane);
+          nga = __ldg(sd.up_slot_grp + q0);
+          ngb = __ldg(sd.up_slot_grp + q0 + 1);
+        }
+        for (int q = q0; q < q1; q += 2) {
+          const uint2 ea = na, eb = nb;
+          const uint32_t ga = nga, gb = ngb;
+          if (q + 2 < q1) {
+            na = __ldg(ell2 + (size_t)(q + 2) * 32 + lane);
+            nb = __ldg(ell2 + (size_t)(q + 3) * 32 + lane);
+            nga = __ldg(sd.up_slot_grp + q + 2);
+            ngb = __ldg(sd.up_slot_grp + q + 3);
+          }
+          C a0[NC], a1[NC], b0[NC], b1[NC];
+          TIO::load_ent(tile, ea.x, a0);
+          TIO::load_ent(tile, ea.y, a1);
+          TIO::load_ent(tile, eb.x, b0);
+          TIO::load_ent(tile, eb.y, b1);
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const uint32_t g = half ? gb : ga;
+            if (g != gcur) {                            // uniform over the warp
+              const C cf = coefS[gcur];
+#pragma unroll
+              for (int c = 0; c < NC; ++c) {
+                acc[c][2 * k].x += cf.x * s0v[c].x - cf.y * s0v[c].y;
+                acc[c][2 * k].y += cf.x * s0v[c].y + cf.y * s0v[c].x;
+                acc[c][2 * k + 1].x += cf.x * s1v[c].x - cf.y * s1v[c].y;
+                acc[c][2 * k + 1].y += cf.x * s1v[c].y + cf.y * s1v[c].x;
+                s0v[c] = czero<C>();
+                s1v[c] = czero<C>();
+              }
+              gcur = g;
+            }
+            const uint2 e = half ? eb : ea;
+            const R g0 = sign_of<R>(e.x), g1 = sign_of<R>(e.y);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              const C v0 = half ? b0[c] : a0[c];
+              const C v1 = half ? b1[c] : a1[c];
+              s0v[c].x += g0 * v0.x;
+              s0v[c].y += g0 * v0.y;
+              s1v[c].x += g1 * v1.x;
+              s1v[c].y += g1 * v1.y;
+            }
+          }
+        }
+        if (q0 < q1) {
+          const C cf = coefS[gcur];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            acc[c][2 * k].x += cf.x * s0v[c].x - cf.y * s0v[c].y;
+            acc[c][2 * k].y += cf.x * s0v[c].y + cf.y * s0v[c].x;
+            acc[c][2 * k + 1].x += cf.x * s1v[c].x - cf.y * s1v[c].y;
+            acc[c][2 * k + 1].y += cf.x * s1v[c].y + cf.y * s1v[c].x;
+          }
+        }
+      }
+    }
+    // ---- store the 32-byte segment of each of the thread's rows
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int u = 2 * (pc + tid + k * T) + hh;
+        if (u < dim_up) {
+          C* dst = w + (size_t)u * dim_dn + d0;
+          if constexpr (sizeof(C) == 16) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              if (c < ncols) dst[c] = acc[c][2 * k + hh];
+          } else if constexpr (VEC) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              if (2 * h < ncols)
+                reinterpret_cast<float4*>(dst)[h] =
+                    make_float4(acc[2 * h][2 * k + hh].x, acc[2 * h][2 * k + hh].y,
+                                acc[2 * h + 1][2 * k + hh].x, acc[2 * h + 1][2 * k + hh].y);
+          } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              if (c < ncols) dst[c] = acc[c][2 * k + hh];
+          }
+        }
       }
     }
   }
@@ -558,13 +818,16 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
     const int64_t b2 = eb.begin >> 1, e2 = eb.end >> 1;
     const float af = (float)as;
     const int bd = blockDim.x;
-    // four pairs per thread and iteration: eight 16-byte loads in flight
+    // four pairs per thread and iteration: eight 16-byte loads in flight.
+    // w and x_j are not read again before the combine at the end of the
+    // step: evict-first loads leave x_{j+1}, whose rows the next apply
+    // gathers, in L2.
     for (int64_t i0 = b2 + threadIdx.x; i0 < e2; i0 += 4 * (int64_t)bd) {
       float4 wv[4], xv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int64_t i = i0 + (int64_t)q * bd;
-        if (i < e2) { wv[q] = w[i]; xv[q] = x[i]; }
+        if (i < e2) { wv[q] = __ldcs(w + i); xv[q] = __ldcs(x + i); }
         else { wv[q] = make_float4(0.f, 0.f, 0.f, 0.f); xv[q] = wv[q]; }
       }
       float nrm = 0.f;
@@ -589,7 +852,7 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
     int cnt = 0;
 #pragma unroll 2
     for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
-      const C wv = w[i], xv = x[i];
+      const C wv = __ldcs(w + i), xv = __ldcs(x + i);
       C o;
       o.x = wv.x - as * xv.x;
       o.y = wv.y - as * xv.y;
@@ -1129,43 +1392,65 @@ static int grid_for(int64_t n, int threads) {
   return (int)g;
 }
 
-// Configurations of the apply kernel: rows per CTA (NR), column pairs per
-// thread per chunk (PP) and the occupancy target (MINB CTAs per SM, which
-// sets the register budget).  The autotuner times the feasible ones.
-struct ApplyCfg { bool fp64; int nr, pp, minb; };
+// Configurations of the apply: rows per CTA (NR), column pairs per thread per
+// chunk (PP) and the occupancy target (MINB CTAs per SM, which sets the
+// register budget) of the row kernel; for the split apply also the pairs per
+// thread and occupancy of the column pass.  The autotuner times the feasible
+// ones.
+struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc; };
 static const ApplyCfg kApplyCfgs[] = {
-    {false, 4, 2, 2}, {false, 2, 2, 3}, {false, 2, 1, 4}, {false, 1, 2, 2},
-    {true, 2, 1, 2}, {true, 1, 1, 4}, {true, 1, 1, 2},
+    {false, 4, 2, 2, false, 0, 0}, {false, 2, 2, 3, false, 0, 0},
+    {false, 2, 1, 4, false, 0, 0}, {false, 1, 2, 2, false, 0, 0},
+    {true, 2, 1, 2, false, 0, 0},  {true, 1, 1, 4, false, 0, 0},
+    {true, 1, 1, 2, false, 0, 0},
+    {false, 4, 2, 2, true, 1, 2},  {false, 2, 2, 3, true, 1, 2},
+    {false, 2, 1, 4, true, 1, 2},  {false, 4, 2, 2, true, 2, 2},
+    {true, 2, 1, 2, true, 1, 2},   {true, 1, 1, 4, true, 1, 2},
 };
 static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
 
-std::vector<LaunchShape> apply_candidates(int max_dim_dn, bool fp64, int n_groups) {
+int apply_config_count() { return kNumApplyCfgs; }
+bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split) {
+  if (i < 0 || i >= kNumApplyCfgs) return false;
+  const ApplyCfg& c = kApplyCfgs[i];
+  *fp64 = c.fp64;
+  *nr = c.nr;
+  *pp = c.pp;
+  *minb = c.minb;
+  *split = c.split;
+  return true;
+}
+
+std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool fp64,
+                                          int n_groups) {
   const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
   std::vector<LaunchShape> out;
-  for (int i = 0; i < kNumApplyCfgs; ++i) {
+  auto make = [&](int i) {
     const ApplyCfg& c = kApplyCfgs[i];
-    if (c.fp64 != fp64) continue;
     LaunchShape sh;
     sh.threads = kApplyThreads;
     sh.ept = c.pp;
     sh.nr = c.nr;
     sh.cfg = i;
+    sh.split = c.split;
     sh.smem = ((size_t)(max_dim_dn + 2) * c.nr + (size_t)n_groups) * csz;
-    // the CTAs per SM the configuration aims at must fit in shared memory
-    if (sh.smem * (size_t)c.minb > 228 * 1024) continue;
-    if (sh.smem > 227 * 1024) continue;
+    sh.smem_c = c.split ? (size_t)(max_dim_up + 2) * 32 + (size_t)n_groups * csz : 0;
+    return sh;
+  };
+  for (int i = 0; i < kNumApplyCfgs; ++i) {
+    const ApplyCfg& c = kApplyCfgs[i];
+    if (c.fp64 != fp64) continue;
+    LaunchShape sh = make(i);
+    // the CTAs per SM each kernel aims at must fit in shared memory
+    if (sh.smem * (size_t)c.minb > 228 * 1024 || sh.smem > 227 * 1024) continue;
+    if (c.split && (sh.smem_c * (size_t)c.minbc > 228 * 1024 || sh.smem_c > 227 * 1024)) continue;
     out.push_back(sh);
   }
   if (out.empty()) {   // very long rows: one row per CTA, one CTA per SM
     for (int i = 0; i < kNumApplyCfgs; ++i) {
       const ApplyCfg& c = kApplyCfgs[i];
-      if (c.fp64 != fp64 || c.nr != 1) continue;
-      LaunchShape sh;
-      sh.threads = kApplyThreads;
-      sh.ept = c.pp;
-      sh.nr = 1;
-      sh.cfg = i;
-      sh.smem = ((size_t)(max_dim_dn + 2) + (size_t)n_groups) * csz;
+      if (c.fp64 != fp64 || c.nr != 1 || c.split) continue;
+      LaunchShape sh = make(i);
       if (sh.smem <= 227 * 1024) out.push_back(sh);
       break;
     }
@@ -1173,8 +1458,8 @@ std::vector<LaunchShape> apply_candidates(int max_dim_dn, bool fp64, int n_group
   return out;
 }
 
-LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
-  std::vector<LaunchShape> c = apply_candidates(max_dim_dn, fp64, n_groups);
+LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups) {
+  std::vector<LaunchShape> c = apply_candidates(max_dim_up, max_dim_dn, fp64, n_groups);
   if (c.empty()) {
     LaunchShape sh{};
     sh.nr = 0;   // no feasible configuration
@@ -1183,52 +1468,80 @@ LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups) {
   return c.front();
 }
 
-template <typename R, int NR, int PP, int MINB>
+template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
-  if (sh.vec) k_apply<R, NR, PP, (sizeof(R) == 4), MINB><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
-  else k_apply<R, NR, PP, false, MINB><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
+  constexpr bool V = sizeof(R) == 4;
+  if constexpr (SPLIT) {
+    if (sh.vec) k_apply_up<R, PPC, V, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
+    else k_apply_up<R, PPC, false, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
+  else k_apply<R, NR, PP, false, MINB, SPLIT><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
 }
 
-template <typename R, int NR, int PP, int MINB>
+template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC>
 static cudaError_t prepare_apply_t(const LaunchShape& sh) {
+  constexpr bool V = sizeof(R) == 4;
   const int sm = (int)sh.smem;
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB>,
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, SPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_apply<R, NR, PP, (sizeof(R) == 4), MINB>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
+  if constexpr (SPLIT) {
+    const int smc = (int)sh.smem_c;
+    e = cudaFuncSetAttribute(k_apply_up<R, PPC, false, MINBC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_apply_up<R, PPC, V, MINBC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
+  }
+  return e;
 }
 
+// One switch over the configuration table for both prepare and launch.
+#define ED_APPLY_CONFIGS(X)                    \
+  X(0, float, 4, 2, 2, false, 1, 1)            \
+  X(1, float, 2, 2, 3, false, 1, 1)            \
+  X(2, float, 2, 1, 4, false, 1, 1)            \
+  X(3, float, 1, 2, 2, false, 1, 1)            \
+  X(4, double, 2, 1, 2, false, 1, 1)           \
+  X(5, double, 1, 1, 4, false, 1, 1)           \
+  X(6, double, 1, 1, 2, false, 1, 1)           \
+  X(7, float, 4, 2, 2, true, 1, 2)             \
+  X(8, float, 2, 2, 3, true, 1, 2)             \
+  X(9, float, 2, 1, 4, true, 1, 2)             \
+  X(10, float, 4, 2, 2, true, 2, 2)            \
+  X(11, double, 2, 1, 2, true, 1, 2)           \
+  X(12, double, 1, 1, 4, true, 1, 2)
+
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
-  if (sh.nr < 1 || sh.smem > 227 * 1024) return cudaErrorInvalidValue;
+  (void)fp64;
+  if (sh.nr < 1 || sh.smem > 227 * 1024 || sh.smem_c > 227 * 1024) return cudaErrorInvalidValue;
+#define X(i, R, NR, PP, MB, SP, PPC, MBC) \
+  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC>(sh);
   switch (sh.cfg) {
-    case 0: return prepare_apply_t<float, 4, 2, 2>(sh);
-    case 1: return prepare_apply_t<float, 2, 2, 3>(sh);
-    case 2: return prepare_apply_t<float, 2, 1, 4>(sh);
-    case 3: return prepare_apply_t<float, 1, 2, 2>(sh);
-    case 4: return prepare_apply_t<double, 2, 1, 2>(sh);
-    case 5: return prepare_apply_t<double, 1, 1, 4>(sh);
-    case 6: return prepare_apply_t<double, 1, 1, 2>(sh);
+    ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;
   }
-  (void)fp64;
+#undef X
 }
 
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
                          int j, cudaStream_t s) {
   (void)fp64;
+#define X(i, R, NR, PP, MB, SP, PPC, MBC) \
+  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC>(a, nblk, sh, j, s);
   switch (sh.cfg) {
-    case 0: return launch_apply_t<float, 4, 2, 2>(a, nblk, sh, j, s);
-    case 1: return launch_apply_t<float, 2, 2, 3>(a, nblk, sh, j, s);
-    case 2: return launch_apply_t<float, 2, 1, 4>(a, nblk, sh, j, s);
-    case 3: return launch_apply_t<float, 1, 2, 2>(a, nblk, sh, j, s);
-    case 4: return launch_apply_t<double, 2, 1, 2>(a, nblk, sh, j, s);
-    case 5: return launch_apply_t<double, 1, 1, 4>(a, nblk, sh, j, s);
-    case 6: return launch_apply_t<double, 1, 1, 2>(a, nblk, sh, j, s);
+    ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;
   }
+#undef X
 }
 
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int nblk, int j, cudaStream_t s) {

@@ -17,11 +17,23 @@ struct LaunchShape {
   size_t smem;   // dynamic shared memory of the apply kernel
   bool vec = false;  // complex64 rows accessed as 16-byte pairs
   int cfg = 0;       // index of the kernel configuration (rows, pairs, occupancy)
+  bool split = false;  // column pass (T_up) + row pass instead of one kernel
+  size_t smem_c = 0;   // dynamic shared memory of the column pass
 };
 
-// Feasible apply configurations for rows of length max_dim_dn (the first is
-// the default); the autotuner in engine.cpp times them on the real data.
-std::vector<LaunchShape> apply_candidates(int max_dim_dn, bool fp64, int n_groups);
+// Feasible apply configurations for sectors of at most max_dim_up rows of
+// length max_dim_dn (the first is the default); the autotuner in engine.cpp
+// times them on the real data.
+std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool fp64,
+                                          int n_groups);
+
+// Column blocks of the split apply: 32 bytes of columns (4 complex64 or 2
+// complex128) covering columns [0, dim_dn) of vector vec.
+inline void append_col_blocks(std::vector<ApplyBlock>& map, int vec, int dim_dn, bool fp64) {
+  const int nc = fp64 ? 2 : 4;
+  for (int d = 0; d < dim_dn; d += nc)
+    map.push_back({vec, d, dim_dn - d < nc ? dim_dn - d : nc, 0});
+}
 
 // Apply blocks of nr rows covering rows [0, dim_up) of vector vec.
 inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_up, int nr) {
@@ -29,14 +41,19 @@ inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_u
     map.push_back({vec, r, dim_up - r < nr ? dim_up - r : nr, 0});
 }
 
-// Pick block size / elements-per-thread for rows of length max_dim_dn.
-LaunchShape apply_shape(int max_dim_dn, bool fp64, int n_groups);
+// The configuration table: its size, and the precision, rows per CTA, pairs
+// per thread, CTAs per SM and split flag of entry i (false if out of range).
+int apply_config_count();
+bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split);
+// The default configuration (first candidate).
+LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups);
 // Raise the dynamic shared-memory limit of the apply kernel for this shape
 // (once, before launches or graph capture).
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh);
 
 // j >= 1: Lanczos step j; j == 0: plain apply x1 -> w with coefs row 0;
 // j == -1: energy (w = H x1 with coefs_obs[step], out_energy[step] = <x1,w>/Ns).
+// A split shape launches the column pass (a.col_map, a.n_col_blocks) first.
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int n_apply_blocks,
                          const LaunchShape& sh, int j, cudaStream_t s);
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int n_ew_blocks, int j,

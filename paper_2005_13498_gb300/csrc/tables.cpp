@@ -99,6 +99,56 @@ std::string make_lattice(LatticeHost& L, int Ns, int n_bonds, const int32_t* p,
   return "";
 }
 
+// Distributes the entries of 64 column lists (column l = 2 * lane + h) over
+// K slots, each list in its own column of the slots, so that the loads one
+// gather instruction makes (one slot, one h, 32 lanes) are spread over the
+// shared-memory banks.  The hardware serves a 16-byte-per-lane load a quarter
+// warp (8 lanes) at a time; sources of distinct rank mod 8 fall in distinct
+// 16-byte bank groups (16-byte columns: rank mod 8; 32-byte swizzled
+// columns: 2 (rank mod 4) + bit 2 of rank, also a bijection of rank mod 8),
+// and equal ranks are a broadcast.  Greedy, slot by slot: within each quarter
+// warp the lanes with the longest remaining lists choose first, each taking
+// the entry that adds the fewest conflicts; a lane with slack (fewer entries
+// left than slots) leaves the slot empty rather than add a conflict.  Returns
+// [K][64] entries, kEllNull where a lane has nothing in that slot.
+static std::vector<uint32_t> assign_slots(std::vector<std::vector<uint32_t>> lists, int K) {
+  std::vector<uint32_t> out((size_t)K * 64, kEllNull);
+  for (int k = 0; k < K; ++k) {
+    const int slack = K - k;
+    for (int h = 0; h < 2; ++h) {
+      for (int ph = 0; ph < 4; ++ph) {
+        int cols[8];
+        for (int i = 0; i < 8; ++i) cols[i] = 2 * (8 * ph + i) + h;
+        std::stable_sort(cols, cols + 8, [&](int a, int b) {
+          return lists[a].size() > lists[b].size();
+        });
+        std::vector<uint32_t> used;   // ranks already read in this quarter warp
+        auto cost = [&](uint32_t rank) {
+          int n = 0;
+          for (uint32_t r : used)
+            if (r != rank && (r & 7u) == (rank & 7u)) ++n;
+          return n;
+        };
+        for (int i = 0; i < 8; ++i) {
+          std::vector<uint32_t>& L = lists[cols[i]];
+          if (L.empty()) continue;
+          size_t best = 0;
+          int bc = cost(L[0] & 0xFFFFu);
+          for (size_t j = 1; j < L.size() && bc > 0; ++j) {
+            const int cj = cost(L[j] & 0xFFFFu);
+            if (cj < bc) { bc = cj; best = j; }
+          }
+          if (bc > 0 && (int)L.size() < slack) continue;   // wait for a later slot
+          out[(size_t)k * 64 + cols[i]] = L[best];
+          used.push_back(L[best] & 0xFFFFu);
+          L.erase(L.begin() + best);
+        }
+      }
+    }
+  }
+  return out;
+}
+
 SpinTable build_spin_table(const LatticeHost& L, int n) {
   SpinTable T;
   T.n = n;
@@ -146,7 +196,6 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
   // slot list per tile grouped by bond group, padded to an even slot count
   const int ntile = (T.dim + 63) / 64;
   T.tslot_off.assign(ntile + 1, 0);
-  const uint32_t pad = (uint32_t)T.dim;  // the zero column
   int nslots = 0;
   for (int c = 0; c < ntile; ++c) {
     int maxg = -1;
@@ -157,35 +206,30 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
     }
     int tile_slots = 0;
     for (int g = 0; g <= maxg; ++g) {
+      std::vector<std::vector<uint32_t>> lists(64);   // entries (rank | sign) per column
       int K = 0;
-      std::vector<int> first(64, -1), cnt(64, 0);
       for (int l = 0; l < 64; ++l) {
         const int d = c * 64 + l;
         if (d >= T.dim) continue;
         for (int e = T.off[d]; e < T.off[d + 1]; ++e)
-          if ((int)((T.ent[e] >> 16) & 0xFFu) == g) {
-            if (first[l] < 0) first[l] = e;
-            ++cnt[l];
-          }
-        K = std::max(K, cnt[l]);
+          if ((int)((T.ent[e] >> 16) & 0xFFu) == g)
+            lists[l].push_back((T.ent[e] & 0xFFFFu) | (T.ent[e] & 0x80000000u));
+        K = std::max(K, (int)lists[l].size());
       }
+      if (K == 0) continue;
+      std::vector<uint32_t> slots = assign_slots(lists, K);
       for (int k = 0; k < K; ++k) {
         T.slot_grp.push_back((uint32_t)g);
         for (int l = 0; l < 64; ++l) {   // l = 2 * lane + h
-          uint32_t rank = pad, sgn = 0;
-          if (k < cnt[l]) {
-            const uint32_t e = T.ent[first[l] + k];
-            rank = e & 0xFFFFu;
-            sgn = e & 0x80000000u;
-          }
-          T.ell.push_back(tile_offset(rank) | sgn);
+          const uint32_t e = slots[(size_t)k * 64 + l];
+          T.ell.push_back(e == kEllNull ? kEllNull : (tile_offset(e & 0xFFFFu) | (e & 0x80000000u)));
         }
         ++tile_slots;
       }
     }
-    if (tile_slots % 2) {   // padding slot: every entry points to the zero column
+    if (tile_slots % 2) {   // padding slot: no lane loads anything
       T.slot_grp.push_back(T.slot_grp.empty() ? 0u : T.slot_grp.back());
-      for (int l = 0; l < 64; ++l) T.ell.push_back(tile_offset(pad));
+      for (int l = 0; l < 64; ++l) T.ell.push_back(kEllNull);
       ++tile_slots;
     }
     nslots += tile_slots;

@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include "common.h"   // kEllNull
+
 namespace ed {
 
 // Null entry of a padded row: contributes zero (bit 30; no rank uses it).
@@ -66,9 +68,12 @@ struct SpinTable {
   // slots tslot_off[c] .. tslot_off[c+1] (a multiple of 2, grouped by bond
   // group, slot_grp[s] = group of slot s); slot s holds for lane l the two
   // entries tile_offset(rank) | sign << 31 of its columns at
-  // ell[2 * (s * 32 + l)] and [.. + 1].  Missing entries (a column with fewer
-  // hops of that group, and the padding slot) point to rank = dim, a zero
-  // column.
+  // ell[2 * (s * 32 + l)] and [.. + 1].  A group spans as many slots as its
+  // longest column list in the tile; which slot each entry of a column takes
+  // is chosen so that the eight lanes of each quarter warp read sources of
+  // distinct rank mod 8 where possible (distinct 16-byte shared-memory bank
+  // groups for 16- and 32-byte tile columns, see assign_slots).  A slot a
+  // column does not use holds kEllNull (the lane loads nothing).
   std::vector<int32_t> tslot_off;
   std::vector<uint32_t> slot_grp;
   std::vector<uint32_t> ell;

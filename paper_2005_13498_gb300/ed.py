@@ -72,12 +72,17 @@ def _load():
                                   P, P, P],
         "ed_apply_fermion_op": [P, P, I, I, I, P, P, I, P],
         "ed_device_bytes": [P, ctypes.POINTER(ctypes.c_int64)],
+        "ed_apply_config_info": [I] + [ctypes.POINTER(ctypes.c_int)] * 5,
+        "ed_set_apply_config": [I],
+        "ed_get_apply_config": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "ed_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.ed_apply_config_count.argtypes = []
+    lib.ed_apply_config_count.restype = ctypes.c_int
     lib.ed_last_error.argtypes = [P]
     lib.ed_last_error.restype = ctypes.c_char_p
     lib.ed_version.argtypes = []
@@ -248,6 +253,30 @@ def ed_apply_fermion_op(ctx, ctx_dst, site, spin, create, psi, out, dtype,
                         stream=None):
     _check(lib.ed_apply_fermion_op(ctx, ctx_dst, site, spin, 1 if create else 0,
                                    ptr(psi), ptr(out), dtype, stream_ptr(stream)), ctx)
+
+
+def ed_apply_config_count():
+    return lib.ed_apply_config_count()
+
+
+def ed_apply_config_info(config):
+    """dict(fp64, rows_per_cta, pairs_per_thread, ctas_per_sm, split)."""
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(lib.ed_apply_config_info(config, *[ctypes.byref(x) for x in v]))
+    keys = ["fp64", "rows_per_cta", "pairs_per_thread", "ctas_per_sm", "split"]
+    return {k: x.value for k, x in zip(keys, v)}
+
+
+def ed_set_apply_config(config):
+    """-1: autotune (default); otherwise pin the H v configuration."""
+    _check(lib.ed_set_apply_config(int(config)))
+
+
+def ed_get_apply_config(ctx):
+    """(propagation engine configuration, ed_apply_H plan configuration)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib.ed_get_apply_config(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
 
 
 def ed_device_bytes(ctx):

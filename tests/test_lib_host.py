@@ -28,7 +28,7 @@ def ed():
 
 def header_functions():
     src = open(os.path.join(ROOT, "include", "ed.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:ed_status|const char\*)\s+(ed_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:ed_status|const char\*|int)\s+(ed_\w+)\s*\(",
                                  src, re.M)))
 
 
@@ -171,3 +171,28 @@ def test_connection_counts_complete_graph(ed):
         off, ent, ncl = ed.ed_get_table(ctx, 0)
         assert np.all(np.diff(off) == n * (Ns - n))
         ed.ed_destroy(ctx)
+
+
+def test_apply_config_table_and_switch(ed):
+    """The H v configuration table, and the process-wide switch that pins an
+    entry (no GPU work: only the table and argument checks run here)."""
+    n = ed.ed_apply_config_count()
+    assert n >= 4
+    seen = set()
+    for c in range(n):
+        i = ed.ed_apply_config_info(c)
+        assert i["fp64"] in (0, 1) and i["split"] in (0, 1)
+        assert i["rows_per_cta"] >= 1 and i["pairs_per_thread"] >= 1 and i["ctas_per_sm"] >= 1
+        seen.add((i["fp64"], i["split"]))
+    assert seen == {(0, 0), (0, 1), (1, 0), (1, 1)}
+    for bad in (-2, n):
+        with pytest.raises(ed.EDError) as e:
+            ed.ed_set_apply_config(bad)
+        assert e.value.status == 1
+    with pytest.raises(ed.EDError):
+        ed.ed_apply_config_info(n)
+    ed.ed_set_apply_config(n - 1)
+    ed.ed_set_apply_config(-1)
+    h = ed.Hubbard(synth.ring(6), 3, 3, 2.0)
+    assert ed.ed_get_apply_config(h.ctx) == (-1, -1)   # nothing set up yet
+    h.close()
