@@ -14,6 +14,7 @@ cores, on a bounded sample of each step (see cpu_sample()).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -44,6 +45,10 @@ def parse():
     ap.add_argument("--random-start", action="store_true",
                     help="start from a seeded random state instead of the ground state")
     ap.add_argument("--no-spectral", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the ring and torus workloads")
+    ap.add_argument("--small-steps", type=int, default=20)
     ap.add_argument("--spectral-steps", type=int, default=2)
     ap.add_argument("--apply-only", choices=["c64", "c128"], default=None,
                     help="run 4 plain applies at the bench size and exit (profiler target)")
@@ -212,6 +217,112 @@ def spectral_bench(ed, torch, synth, lat, w, pulse, h, psi64, stream, barrier, s
             "speedup_batched_c64_over_sequential_c128": 56 * one64 / batched,
             "note": "sequential = 56 x one measured complex128 propagation step of "
                     "a vector of the same dimension"}
+
+
+def adaptive_bench(ed, torch, h, psi32, pulse, t_start, dt, m, stream, barrier, steps):
+    """ms per step of the ladder workload with the adaptive exit at two
+    tolerances (complex64), with the Krylov dimensions the steps used."""
+    res = {}
+    for tol in (1e-6, 1e-8):
+        ed.ed_set_krylov_tol(h.ctx, tol)
+        psi = psi32.clone()
+        ed.ed_propagate(h.ctx, psi, ed.ED_C64, pulse, t_start - 2 * dt, dt, 2, m, stream=stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = ed.ed_propagate(h.ctx, psi, ed.ED_C64, pulse, t_start, dt, steps, m,
+                              stream=stream)
+        e1.record(stream)
+        barrier()
+        me = out["m_eff"]
+        res[f"tol={tol:g}"] = {"ms_per_step_c64": e0.elapsed_time(e1) / steps,
+                               "m_eff_mean": float(np.mean(me)), "m_eff_min": int(me.min()),
+                               "m_eff_max": int(me.max()), "steps": steps}
+    ed.ed_set_krylov_tol(h.ctx, 0.0)
+    res["note"] = ("m = 30 is the maximum; one Lanczos pass past the exit is computed "
+                   "while the check runs")
+    return res
+
+
+def pulse_field(p, t):
+    """A(t) = A0 exp(-(t - t0)^2 / (2 sigma^2)) sin(Omega (t - t0)) dir."""
+    s = t - p["t0"]
+    a = p["A0"] * math.exp(-s * s / (2.0 * p["sigma"] ** 2)) * math.sin(p["omega"] * s)
+    return [a * c for c in p["dir"]]
+
+
+def smaller_workloads_bench(ed, torch, synth, stream, barrier, steps):
+    """The Ns=8 ring (complex128, m=12) and the 3x4 torus (both precisions,
+    m=20): ms per midpoint step from the ground state at t=0; 100 applies of
+    H on the seed-0 vector at A=0 and at A(dt/2); the torus spectral batch
+    (48 c/c+ vectors + psi, complex64, m=20).  These vectors (<= 14 MB) stay
+    in L2: no flush, no HBM fraction claimed."""
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    tdt = {"c128": (ed.ED_C128, torch.complex128), "c64": (ed.ED_C64, torch.complex64)}
+    for name in ("ring8", "torus3x4"):
+        w = synth.workload(name)
+        lat = synth.lattice_from_name(w["lattice"])
+        p, dt, m = w["pulse_params"], w["dt"], w["m"]
+        h = ed.Hubbard(lat, w["n_up"], w["n_dn"], w["U"])
+        g = torch.zeros(h.D, dtype=torch.complex128, device="cuda")
+        E0, _ = ed.ed_ground_state(h.ctx, g, tol=1e-10, max_iter=3000)
+        res = {"D": h.D, "m": m, "dt": dt, "E0": E0}
+        for name_dt in w["dtypes"]:
+            code, tt = tdt[name_dt]
+            psi = g.clone().to(tt)
+            ed.ed_propagate(h.ctx, psi, code, p, 0.0, dt, 3, m, stream=stream)
+            barrier()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            ed.ed_propagate(h.ctx, psi, code, p, 3 * dt, dt, steps, m, stream=stream)
+            e1.record(stream)
+            barrier()
+            res[f"ms_per_step_{name_dt}"] = e0.elapsed_time(e1) / steps
+        res["steps"] = steps
+        if name == "torus3x4":
+            v0 = synth.complex_normal(h.D, 0)
+            hv = {}
+            for label, A in (("A=0", [0.0, 0.0, 0.0]), ("A(dt/2)", pulse_field(p, dt / 2))):
+                ed.ed_set_field(h.ctx, A)
+                for name_dt in ("c128", "c64"):
+                    code, tt = tdt[name_dt]
+                    v = torch.from_numpy(v0).to(tt).cuda()
+                    wv = torch.zeros_like(v)
+                    for _ in range(3):
+                        ed.ed_apply_H(h.ctx, v, wv, code, stream=stream)
+                    barrier()
+                    e0, e1 = ev(), ev()
+                    e0.record(stream)
+                    for _ in range(100):
+                        ed.ed_apply_H(h.ctx, v, wv, code, stream=stream)
+                    e1.record(stream)
+                    barrier()
+                    ms = e0.elapsed_time(e1) / 100
+                    esz = 16 if name_dt == "c128" else 8
+                    hv[f"{label} {name_dt}"] = {"us": ms * 1e3,
+                                                "GBs": 2 * h.D * esz / (ms * 1e-3) / 1e9}
+            res["hv_100_applies_seed0"] = hv
+            # spectral batch of the torus from the same ground state
+            ws = synth.workload("torus3x4_spectral")
+            ed.ed_spectral_propagate(h.ctx, g, ed.ED_C64, p, ws["dt"], 1, ws["m"], 12,
+                                     stream=stream)
+            barrier()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            ed.ed_spectral_propagate(h.ctx, g, ed.ED_C64, p, ws["dt"], steps, ws["m"], 12,
+                                     stream=stream)
+            e1.record(stream)
+            barrier()
+            bms = e0.elapsed_time(e1) / steps
+            out["torus3x4_spectral"] = {
+                "workload": "Ns=12 3x4 torus spectral batch: 48 c/c+ vectors of dim 731,808 "
+                            "+ psi, complex64, m=20, dt=0.02",
+                "ms_per_step_batched_c64": bms, "ms_per_vector_step": bms / 49,
+                "steps": steps}
+        h.close()
+        out[name] = res
+    return out
 
 
 def reference_arm(args):
@@ -415,6 +526,16 @@ def main():
         if not args.no_spectral:
             line["spectral"] = spectral_bench(ed, torch, synth, lat, w, pulse, h, psi64,
                                               stream, barrier, args.spectral_steps)
+        # adaptive Krylov dimension (a-posteriori exit of Algorithm 6, m = 30
+        # as the maximum) on the same ladder workload and time window
+        if not args.no_adaptive:
+            line["adaptive"] = adaptive_bench(ed, torch, h, psi32, pulse, t_start, dt, m,
+                                              stream, barrier, args.steps)
+        # the ring and torus workloads (step times, H v on the seed-0 vector,
+        # the torus spectral batch)
+        if not args.no_small:
+            line.update(smaller_workloads_bench(ed, torch, synth, stream, barrier,
+                                                args.small_steps))
         # end to end through the C ABI with pinned host buffers: every step
         # copies psi in, propagates one step, copies psi and <d> out
         hostpsi = psi32.cpu().pin_memory()

@@ -233,6 +233,22 @@ ed_status ed_apply_fermion_op(ed_ctx* ctx, ed_ctx* ctx_dst, int site, int spin,
                               int create, const void* psi, void* out,
                               ed_dtype dtype, void* stream);
 
+/* Adaptive Krylov dimension (the a-posteriori exit of Algorithm 6, Sec. 3.4)
+ * for the ed_propagate and ed_spectral_propagate calls made on ctx after
+ * this one.  tol = 0 (the default): every step uses exactly m Lanczos
+ * vectors (unless the Krylov space breaks down).  tol > 0: m becomes the
+ * maximum; after Lanczos step j < m the step's approximation
+ * y^(j) = exp(-i tau T_j) e_1 is compared with y^(j-1) (zero-padded; y^(0) =
+ * 0): delta = |y^(j) - y^(j-1)| / |y^(j)|, epsilon = min(1 + |y^(j)|,
+ * delta / (1 - delta) |y^(j)|) for delta < 1 and 1 + |y^(j)| otherwise, and
+ * the step ends with dimension j once epsilon < tol or beta_j < tol * alpha,
+ * alpha = max(1, |alpha_k|, beta_k over the steps before) as the estimate of
+ * |H|.  The dimension used in each step is reported in observables->m_eff.
+ * The check of step j runs while the next Lanczos pass proceeds, so one pass
+ * past the exit is computed and discarded.  ED_ERR_ARG for a negative or
+ * non-finite tol.                                                            */
+ed_status ed_set_krylov_tol(ed_ctx* ctx, double tol);
+
 /* Kernel configurations of H v (the matrix-vector product inside Lanczos,
  * Eq. (18) applied as T_up (x) 1 + 1 (x) T_dn + diagonal, Sec. 3.2).  Each
  * entry of the library's table fixes the precision, the rows of Psi one

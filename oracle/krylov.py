@@ -6,13 +6,20 @@ Oracle (test infrastructure only).  Follows Sec. 3.4 of the paper:
       v^{n+1} = exp(-i tau H(t_n + tau/2)) v^n,   t_n = t_start + n tau.
 * Algorithm 6, Lanczos construction of the Krylov basis V and the tridiagonal
   projection h, then  exp(-i tau H) v ~= beta V exp(-i tau h) e_1.
-  Readings: the Krylov dimension m is fixed (the adaptive exit of the
-  algorithm is replaced by a fixed count); h_jj = Re(V_j^H w) because H is
+  Readings: by default the Krylov dimension m is fixed (the adaptive exit of
+  the algorithm is replaced by a fixed count); h_jj = Re(V_j^H w) because H is
   Hermitian; the breakdown exit |h_{j+1,j}| < alpha * tol of the algorithm is
   taken with alpha = max(1, max|h_kk|, max h_{k+1,k}) over the steps so far and
   tol = 1e-13 (the float64 rule the CUDA path uses too); the a-posteriori
   estimate delta / epsilon of the algorithm is computed and returned as a
-  diagnostic only.
+  diagnostic.
+  With an error tolerance ``eps_tol`` the adaptive exit is taken as printed:
+  after every step j, y^(j) = exp(-i tau h_j) e_1 is compared with y^(j-1)
+  (zero-padded; y^(0) = 0), delta = |y^(j) - y^(j-1)| / |y^(j)|, epsilon =
+  min(1 + |y^(j)|, delta / (1 - delta) |y^(j)|) for delta < 1 and 1 + |y^(j)|
+  otherwise, and the step returns beta V y^(j) once epsilon < eps_tol or
+  |h_{j+1,j}| < alpha * eps_tol (alpha as above); m is then the largest
+  dimension N_max.
 * The m x m exponential (Expokit in the paper) is computed here from the
   eigendecomposition of the real symmetric tridiagonal h (numpy.linalg.eigh):
   exp(-i tau h) e_1 = Q diag(exp(-i tau lambda)) Q^T e_1.
@@ -76,20 +83,36 @@ def small_expm_e1(alpha, beta, tau):
     return Q @ (np.exp(-1j * tau * lam) * Q[0, :])
 
 
-def lanczos_expm(H, v, tau, m, tol=BREAKDOWN_TOL):
-    """One step of Algorithm 6 with fixed Krylov dimension m.
+def epsilon_estimate(y, y_prev):
+    """(delta, epsilon) of the a-posteriori error estimate of Algorithm 6
+    for consecutive approximations y = y^(j) and y_prev = y^(j-1) (shorter by
+    one; zero-padded)."""
+    yp = np.zeros(len(y), dtype=np.complex128)
+    yp[:len(y_prev)] = y_prev
+    ny = np.linalg.norm(y)
+    delta = np.linalg.norm(y - yp) / ny
+    eps = min(1 + ny, delta / (1 - delta) * ny) if delta < 1 else 1 + ny
+    return float(delta), float(eps)
 
-    Returns (beta0 * V y, info) with info = dict(alpha, beta, m_eff, delta, eps).
+
+def lanczos_expm(H, v, tau, m, tol=BREAKDOWN_TOL, eps_tol=None):
+    """One step of Algorithm 6 with Krylov dimension m (fixed), or at most m
+    with the adaptive exit when eps_tol is given.
+
+    Returns (beta0 * V y, info) with info = dict(alpha, beta, m_eff, delta,
+    eps); with eps_tol also eps_history (epsilon after every step).
     """
     v = np.asarray(v, dtype=np.complex128)
     beta0 = np.sqrt(np.vdot(v, v).real)
     if beta0 == 0.0:
         return v.copy(), {"alpha": [], "beta": [], "m_eff": 0,
-                          "delta": 0.0, "eps": 0.0}
+                          "delta": 0.0, "eps": 0.0, "eps_history": []}
     V = [v / beta0]
     alpha, beta = [], []
     scale = 1.0
     m_eff = m
+    y_prev = np.zeros(0, dtype=np.complex128)
+    eps_hist = []
     for j in range(m):
         w = H @ V[j]
         if j > 0:
@@ -99,23 +122,27 @@ def lanczos_expm(H, v, tau, m, tol=BREAKDOWN_TOL):
         w = w - a * V[j]
         b = np.sqrt(np.vdot(w, w).real)
         scale = max(scale, abs(a))
+        beta.append(b)
         if j == m - 1:
-            beta.append(b)
             break
         if b <= tol * scale:
-            beta.append(b)
             m_eff = j + 1
             break
+        if eps_tol is not None:
+            # a-posteriori exit of Algorithm 6 after step j + 1
+            y = small_expm_e1(alpha, beta[:j], tau)
+            _, e = epsilon_estimate(y, y_prev)
+            eps_hist.append(e)
+            y_prev = y
+            if e < eps_tol or b < eps_tol * scale:
+                m_eff = j + 1
+                break
         scale = max(scale, b)
-        beta.append(b)
         V.append(w / b)
     y = small_expm_e1(alpha[:m_eff], beta[:m_eff - 1], tau)
-    # a-posteriori estimate of Algorithm 6 (diagnostic only)
     if m_eff > 1:
-        yp = np.append(small_expm_e1(alpha[:m_eff - 1], beta[:m_eff - 2], tau), 0.0)
-        ny = np.linalg.norm(y)
-        delta = np.linalg.norm(y - yp) / ny
-        eps = min(1 + ny, delta / (1 - delta) * ny) if delta < 1 else 1 + ny
+        yp = small_expm_e1(alpha[:m_eff - 1], beta[:m_eff - 2], tau)
+        delta, eps = epsilon_estimate(y, yp)
     else:
         delta = eps = 0.0
     out = np.zeros_like(v)
@@ -123,7 +150,7 @@ def lanczos_expm(H, v, tau, m, tol=BREAKDOWN_TOL):
         out += y[j] * V[j]
     out *= beta0
     return out, {"alpha": alpha, "beta": beta, "m_eff": m_eff,
-                 "delta": delta, "eps": eps}
+                 "delta": delta, "eps": eps, "eps_history": eps_hist}
 
 
 def double_occupation(psi, w_d, Ns):
@@ -139,8 +166,10 @@ def energy_per_site(H, psi, Ns):
 
 
 def propagate(lattice, n_up, n_dn, U, psi0, pulse, dt, n_steps, m,
-              t_start=0.0, with_energy=False, form="auto", record_states=False):
-    """Midpoint-rule trajectory (Eq. (32)) with fixed-m Lanczos steps.
+              t_start=0.0, with_energy=False, form="auto", record_states=False,
+              eps_tol=None):
+    """Midpoint-rule trajectory (Eq. (32)) with fixed-m Lanczos steps (or
+    at most m with the adaptive exit, eps_tol given).
 
     Observables are recorded at t_0 = t_start and after every step at
     t_{n+1}.  Returns dict(psi, docc, norm2, energy, m_eff, delta, states).
@@ -161,7 +190,7 @@ def propagate(lattice, n_up, n_dn, U, psi0, pulse, dt, n_steps, m,
     for n in range(n_steps):
         t_mid = t_start + (n + 0.5) * dt
         H = make_H(lattice, n_up, n_dn, U, pulse_A(t_mid, pulse), form)
-        psi, info = lanczos_expm(H, psi, dt, m)
+        psi, info = lanczos_expm(H, psi, dt, m, eps_tol=eps_tol)
         m_eff.append(info["m_eff"])
         deltas.append(info["delta"])
         docc.append(double_occupation(psi, w_d, Ns))

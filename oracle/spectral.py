@@ -74,13 +74,14 @@ def apply_cdag(Ns, n_up, n_dn, psi, site, spin):
 
 
 def spectral_batch(lattice, n_up, n_dn, U, psi0, pulse, dt, n_steps, m,
-                   t_start=0.0, sites=None, form="auto"):
+                   t_start=0.0, sites=None, form="auto", eps_tol=None):
     """L_{is}(n) and G_{is}(n) for n = 0..n_steps (arrays [n+1, Ns, 2]).
 
     psi is propagated in (n_up, n_dn); phi_{is} = c_{is} psi0 and
     phi'_{is} = c^+_{is} psi0 in their sectors, all with the same pulse, dt
-    and fixed Krylov dimension m.  Sectors that do not exist (n = 0 or n = Ns)
-    give zeros.
+    and Krylov dimension m (fixed, or at most m with the adaptive exit of
+    Algorithm 6 when eps_tol is given, each vector on its own).  Sectors that
+    do not exist (n = 0 or n = Ns) give zeros.
     """
     Ns = lattice["Ns"]
     sites = list(range(Ns)) if sites is None else list(sites)
@@ -108,15 +109,17 @@ def spectral_batch(lattice, n_up, n_dn, U, psi0, pulse, dt, n_steps, m,
         t_mid = t_start + (n + 0.5) * dt
         A = pulse_A(t_mid, pulse)
         psi, _ = lanczos_expm(make_H(lattice, n_up, n_dn, U, A, form),
-                              psi, dt, m)
+                              psi, dt, m, eps_tol=eps_tol)
         for (i, s) in list(phis):
             nu2, nd2 = sector_shift(n_up, n_dn, "c", s)
             phis[(i, s)], _ = lanczos_expm(
-                make_H(lattice, nu2, nd2, U, A, form), phis[(i, s)], dt, m)
+                make_H(lattice, nu2, nd2, U, A, form), phis[(i, s)], dt, m,
+                eps_tol=eps_tol)
         for (i, s) in list(phids):
             nu2, nd2 = sector_shift(n_up, n_dn, "cdag", s)
             phids[(i, s)], _ = lanczos_expm(
-                make_H(lattice, nu2, nd2, U, A, form), phids[(i, s)], dt, m)
+                make_H(lattice, nu2, nd2, U, A, form), phids[(i, s)], dt, m,
+                eps_tol=eps_tol)
         record(n + 1)
     return {"L": L, "G": G, "G_less": 1j * L, "G_greater": -1j * G,
             "psi": psi}

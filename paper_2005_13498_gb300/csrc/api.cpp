@@ -235,6 +235,14 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
   return ED_OK;
 }
 
+ed_status ed_set_krylov_tol(ed_ctx* ctx, double tol) {
+  if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
+  if (!(tol >= 0.0) || !std::isfinite(tol))
+    return fail(ctx, ED_ERR_ARG, "tol must be finite and >= 0");
+  ctx->krylov_tol = tol;
+  return ED_OK;
+}
+
 int ed_apply_config_count(void) { return apply_config_count(); }
 
 ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
@@ -388,6 +396,7 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   cfg.m = m;
   cfg.energy = energy;
   cfg.n_steps_cap = std::max(1, n_steps);
+  cfg.eps_tol = ctx->krylov_tol;
   std::vector<EngineVector> vecs = {{0, D, on_device ? psi : nullptr, !on_device}};
   CK(ctx, join_streams(us, s));
   if (!ctx->engine || !ctx->engine->compatible(cfg, vecs)) {

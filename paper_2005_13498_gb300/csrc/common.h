@@ -61,12 +61,21 @@ struct LanczosState {
   double delta;      // a-posteriori estimate of the last step
   double dot_out;    // scratch result of a plain dot product
   double red[4];     // scratch results of generic reductions
+  // adaptive exit of Algorithm 6 (eps_tol > 0): the check after step j
+  // stores y^(j) = exp(-i tau T_j) e_1 here and sets conv_m = j once the
+  // a-posteriori error epsilon drops below eps_tol
+  double eps_tol;                   // 0: fixed Krylov dimension
+  double sc_at[kMaxKrylov + 2];     // breakdown scale max(1,|alpha|,beta) seen by step j
+  double yprev_re[kMaxKrylov];
+  double yprev_im[kMaxKrylov];
+  double conv_delta;                // delta of the converged step
   int m;             // requested Krylov dimension
   int m_eff;         // dimension in use (set < m on breakdown)
   int stopped;       // 1 once breakdown was detected in this step
   int step;          // time-step counter (indexes coefficient arrays)
   int status;        // 0 ok, ED_ERR_NUMERIC on a non-finite norm
-  int pad[3];
+  int conv_m;        // 0, or the step j at which the adaptive exit was taken
+  int pad[2];
 };
 
 // One propagated vector of a batch.

@@ -48,6 +48,7 @@ struct ed_ctx {
   ed::LatticeHost lat;
   ed::SectorGPU sec;
   double A[3] = {0, 0, 0};
+  double krylov_tol = 0.0;   // > 0: adaptive Krylov dimension (Algorithm 6)
   std::string err;
   cudaStream_t stream = nullptr;
   int device = 0;

@@ -372,6 +372,7 @@ ed_status ed_spectral_propagate(ed_ctx* ctx, const void* psi0, ed_dtype dtype,
   cfg.m = m;
   cfg.overlaps = true;
   cfg.n_steps_cap = std::max(1, n_steps);
+  cfg.eps_tol = ctx->krylov_tol;
   CK(ctx, join_streams(us, s));
   if (!ctx->spec_engine || !ctx->spec_engine->compatible(cfg, vecs)) {
     ctx->spec_engine.reset(new Engine());

@@ -31,6 +31,9 @@ void DevMem::release() {
 Engine::~Engine() {
   if (exec_) cudaGraphExecDestroy(exec_);
   if (graph_) cudaGraphDestroy(graph_);
+  for (cudaEvent_t e : ev_fork_) cudaEventDestroy(e);
+  for (cudaEvent_t e : ev_check_) cudaEventDestroy(e);
+  if (side_) cudaStreamDestroy(side_);
 }
 
 size_t Engine::device_bytes() const {
@@ -49,7 +52,8 @@ bool Engine::compatible(const EngineConfig& cfg, const std::vector<EngineVector>
   const int forced = forced_apply_config();
   if (forced >= 0 && forced != shape_.cfg) return false;
   if (cfg.fp64 != cfg_.fp64 || cfg.m != cfg_.m || cfg.energy != cfg_.energy ||
-      cfg.overlaps != cfg_.overlaps || cfg.n_steps_cap > cfg_.n_steps_cap)
+      cfg.overlaps != cfg_.overlaps || cfg.n_steps_cap > cfg_.n_steps_cap ||
+      cfg.eps_tol != cfg_.eps_tol)
     return false;
   if (vecs.size() != vecs_.size()) return false;
   for (size_t i = 0; i < vecs.size(); ++i) {
@@ -176,6 +180,15 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   const size_t esz = cfg.fp64 ? 16 : 8;
   const int nv = (int)vecs.size();
   const int m = cfg.m;
+  if (cfg.eps_tol > 0.0 && !side_) {
+    ED_TRY(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
+    ev_fork_.assign(kMaxKrylov + 1, nullptr);
+    ev_check_.assign(kMaxKrylov + 1, nullptr);
+    for (int i = 0; i <= kMaxKrylov; ++i) {
+      ED_TRY(cudaEventCreateWithFlags(&ev_fork_[i], cudaEventDisableTiming));
+      ED_TRY(cudaEventCreateWithFlags(&ev_check_[i], cudaEventDisableTiming));
+    }
+  }
 
   // owned state buffers
   int64_t owned = 0;
@@ -377,6 +390,7 @@ std::string Engine::begin(const std::vector<double>& coefs, const std::vector<do
     s.m = cfg_.m;
     s.m_eff = cfg_.m;
     s.scale = 1.0;
+    s.eps_tol = cfg_.eps_tol;
   }
   ED_TRY(cudaMemcpyAsync(d_st_.p, st.data(), sizeof(LanczosState) * st.size(),
                          cudaMemcpyHostToDevice, stream));
@@ -407,10 +421,24 @@ std::string Engine::launch_step(cudaStream_t s, bool profile, cudaEvent_t* ev, i
     ED_TRY(call);                                       \
     if (!(err = mark(kind)).empty()) return err;        \
   } while (0)
+  // With the adaptive exit, the check of step j runs on the side stream
+  // while pass j + 1 proceeds on s; pass j + 2 waits for it (a converged
+  // check makes the later passes return at once, see lanczos_done).
+  const bool adaptive = cfg_.eps_tol > 0.0;
   for (int j = 1; j <= cfg_.m; ++j) {
+    if (adaptive && j >= 3) ED_TRY(cudaStreamWaitEvent(s, ev_check_[j - 2], 0));
     STEP_LAUNCH(KK_APPLY, launch_apply(f, args_, n_apply_, shape_, j, s));
-    if (j < cfg_.m) STEP_LAUNCH(KK_UPDATE, launch_update(f, args_, n_ew_, j, s));
+    if (j < cfg_.m) {
+      STEP_LAUNCH(KK_UPDATE, launch_update(f, args_, n_ew_, j, s));
+      if (adaptive) {
+        ED_TRY(cudaEventRecord(ev_fork_[j], s));
+        ED_TRY(cudaStreamWaitEvent(side_, ev_fork_[j], 0));
+        ED_TRY(launch_conv_check(args_, j, side_));
+        ED_TRY(cudaEventRecord(ev_check_[j], side_));
+      }
+    }
   }
+  if (adaptive && cfg_.m >= 2) ED_TRY(cudaStreamWaitEvent(s, ev_check_[cfg_.m - 1], 0));
   STEP_LAUNCH(KK_EXPM, launch_expm(args_, s));
   STEP_LAUNCH(KK_COMBINE, launch_combine(f, args_, n_ew_, s));
   if (cfg_.energy) STEP_LAUNCH(KK_ENERGY, launch_apply(f, args_, n_apply_, shape_, -1, s));

@@ -41,6 +41,7 @@ struct EngineConfig {
   bool energy = false;
   bool overlaps = false;
   int n_steps_cap = 0;
+  double eps_tol = 0.0;   // > 0: adaptive exit of Algorithm 6, m is the maximum
 };
 
 // Autotuner of the apply kernel: times the feasible configurations (rows per
@@ -108,6 +109,10 @@ class Engine {
   double U_ = 0.0, break_tol_ = 0.0, tau_ = 0.0;
   int n_apply_ = 0, n_ew_ = 0;
   LaunchShape shape_{};
+  // adaptive exit: side stream for the convergence checks and the events
+  // that fork check j after update j and join it before pass j + 2
+  cudaStream_t side_ = nullptr;
+  std::vector<cudaEvent_t> ev_fork_, ev_check_;
   BatchArgs args_{};
   OverlapArgs oargs_{};
   bool have_overlaps_ = false;

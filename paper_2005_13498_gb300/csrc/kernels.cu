@@ -101,6 +101,16 @@ __device__ __forceinline__ bool reduce_last_block(double (&v)[K], int blk, int b
   return true;
 }
 
+// Whether the Lanczos passes of step j are skipped: after a breakdown, or
+// once the adaptive check of a step <= j - 2 has converged.  The check of
+// step j - 1 runs concurrently with pass j (its result must not change
+// pass j's decision halfway through the grid: conv_m = j - 1 fails the test),
+// and the pass j + 1 kernels start after it has finished.
+__device__ __forceinline__ bool lanczos_done(const LanczosState* st, int j) {
+  const int c = *(volatile const int*)&st->conv_m;
+  return st->stopped || (c > 0 && c <= j - 2);
+}
+
 __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz) {
   // x_1 is the state, x_j (j >= 2) is V slot j-2
   return j == 1 ? vd.x1
@@ -280,7 +290,7 @@ k_apply(BatchArgs a, int j) {
   const ApplyBlock ab = a.apply_map[blockIdx.x];
   const VecDev vd = a.vec[ab.vec];
   LanczosState* st = a.st + ab.vec;
-  if (j >= 1 && st->stopped) return;   // uniform over the vector's blocks
+  if (j >= 1 && lanczos_done(st, j)) return;   // uniform over the vector's blocks
   const SectorDev sd = a.sec[vd.sector];
   const int dim_dn = sd.dim_dn;
   const int npairs = (dim_dn + 1) >> 1;
@@ -626,7 +636,7 @@ k_apply_up(BatchArgs a, int j) {
   const ApplyBlock cb = a.col_map[blockIdx.x];
   const VecDev vd = a.vec[cb.vec];
   const LanczosState* st = a.st + cb.vec;
-  if (j >= 1 && st->stopped) return;   // uniform over the vector's blocks
+  if (j >= 1 && lanczos_done(st, j)) return;   // uniform over the vector's blocks
   const SectorDev sd = a.sec[vd.sector];
   const int dim_up = sd.dim_up, dim_dn = sd.dim_dn;
   const int d0 = cb.row0, ncols = cb.nrows;
@@ -804,7 +814,7 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
   const EwBlock eb = a.ew_map[blockIdx.x];
   const VecDev vd = a.vec[eb.vec];
   LanczosState* st = a.st + eb.vec;
-  if (st->stopped) return;
+  if (lanczos_done(st, j)) return;
   const R as = (R)(st->alpha[j] * st->inv_scale[j]);
   double nrm_d = 0.0;
   const void* pw = vd.w;
@@ -869,6 +879,7 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
       const double beta = sqrt(v[0]);
       const double sc = fmax(st->scale, fabs(st->alpha[j]));
       st->beta[j] = beta;
+      st->sc_at[j] = sc;
       if (!isfinite(beta)) {
         st->status = 7; st->stopped = 1; st->m_eff = j;
       } else if (beta <= a.break_tol * sc) {
@@ -971,6 +982,24 @@ __global__ void __launch_bounds__(32) k_expm(BatchArgs a) {
   LanczosState* st = a.st + b;
   const VecDev vd = a.vec[b];
   const int lane = threadIdx.x;
+  const int conv = st->conv_m;
+  if (conv > 0 && conv < st->m_eff) {
+    // adaptive exit at step conv: its check left y^(conv) and delta
+    const int n = conv;
+    for (int i = lane; i < n; i += 32) {
+      const double f = st->beta0 * st->inv_scale[i + 1];
+      st->comb_re[i + 1] = f * st->yprev_re[i];
+      st->comb_im[i + 1] = f * st->yprev_im[i];
+    }
+    __syncwarp();
+    if (lane == 0) {
+      st->m_eff = n;
+      st->delta = st->conv_delta;
+      if (vd.out_delta) vd.out_delta[st->step] = st->conv_delta;
+      if (vd.out_meff) vd.out_meff[st->step] = n;
+    }
+    return;
+  }
   const int n = st->m_eff;
   for (int i = lane; i < 64; i += 32) {
     al[i] = i < n ? st->alpha[i + 1] : 0.0;
@@ -1002,6 +1031,54 @@ __global__ void __launch_bounds__(32) k_expm(BatchArgs a) {
     st->delta = delta;
     if (vd.out_delta) vd.out_delta[st->step] = delta;
     if (vd.out_meff) vd.out_meff[st->step] = n;
+  }
+}
+
+// Adaptive exit of Algorithm 6 after Lanczos step j (one warp per vector):
+// y^(j) = exp(-i tau T_j) e_1, delta = |y^(j) - y^(j-1)| / |y^(j)| against the
+// previous check's y (zero-padded; none at j = 1), epsilon = min(1 + |y|,
+// delta / (1 - delta) |y|) for delta < 1, else 1 + |y|; the step converges
+// when epsilon < eps_tol or beta_j < eps_tol * (the breakdown scale seen by
+// step j).  Runs on a side stream while pass j + 1 proceeds; it reads only
+// scalars of steps <= j, and writes yprev, conv_delta and conv_m.
+__global__ void __launch_bounds__(32) k_conv_check(BatchArgs a, int j) {
+  __shared__ double al[64], be[64], yre[64], yim[64], tre[64], tim[64];
+  LanczosState* st = a.st + blockIdx.x;
+  const int lane = threadIdx.x;
+  if (!(st->eps_tol > 0.0) || st->conv_m > 0 || st->m_eff <= j || j >= st->m) return;
+  const int n = j;
+  for (int i = lane; i < 64; i += 32) {
+    al[i] = i < n ? st->alpha[i + 1] : 0.0;
+    be[i] = i < n - 1 ? st->beta[i + 1] : 0.0;
+  }
+  __syncwarp();
+  tridiag_expm_e1(al, be, n, a.tau, yre, yim, tre, tim);
+  double dn = 0.0, yn = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double pr = i < n - 1 ? st->yprev_re[i] : 0.0;
+    const double pi = i < n - 1 ? st->yprev_im[i] : 0.0;
+    dn += (yre[i] - pr) * (yre[i] - pr) + (yim[i] - pi) * (yim[i] - pi);
+    yn += yre[i] * yre[i] + yim[i] * yim[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    yn += __shfl_xor_sync(0xffffffffu, yn, o);
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    st->yprev_re[i] = yre[i];
+    st->yprev_im[i] = yim[i];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const double ny = sqrt(yn);
+    const double delta = sqrt(dn) / ny;
+    const double eps = delta < 1.0 ? fmin(1.0 + ny, delta / (1.0 - delta) * ny) : 1.0 + ny;
+    if (eps < st->eps_tol || st->beta[j] < st->eps_tol * st->sc_at[j]) {
+      st->conv_delta = delta;
+      __threadfence();
+      *(volatile int*)&st->conv_m = j;
+    }
   }
 }
 
@@ -1133,6 +1210,7 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
       st->inv_scale[1] = b0 > 0.0 ? 1.0 / b0 : 0.0;
       st->scale = 1.0;
       st->m_eff = st->m;
+      st->conv_m = 0;
       st->stopped = b0 > 0.0 && isfinite(b0) ? 0 : 1;
       if (COMBINE) st->step = st->step + 1;
     }
@@ -1547,6 +1625,11 @@ cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchSh
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int nblk, int j, cudaStream_t s) {
   if (fp64) k_update<double, false><<<nblk, 256, 0, s>>>(a, j);
   else k_update<float, true><<<nblk, 256, 0, s>>>(a, j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_check(const BatchArgs& a, int j, cudaStream_t s) {
+  k_conv_check<<<a.nvec, 32, 0, s>>>(a, j);
   return cudaGetLastError();
 }
 

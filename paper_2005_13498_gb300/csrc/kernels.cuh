@@ -59,6 +59,8 @@ cudaError_t launch_apply(bool fp64, const BatchArgs& a, int n_apply_blocks,
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int n_ew_blocks, int j,
                           cudaStream_t s);
 cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s);
+// Adaptive exit check after Lanczos step j (vectors with eps_tol > 0).
+cudaError_t launch_conv_check(const BatchArgs& a, int j, cudaStream_t s);
 cudaError_t launch_combine(bool fp64, const BatchArgs& a, int n_ew_blocks,
                            cudaStream_t s);
 // Observables of x1 without combining (t_0): sets beta0, inv_scale[1], outputs.

@@ -74,6 +74,7 @@ def _load():
         "ed_device_bytes": [P, ctypes.POINTER(ctypes.c_int64)],
         "ed_apply_config_info": [I] + [ctypes.POINTER(ctypes.c_int)] * 5,
         "ed_set_apply_config": [I],
+        "ed_set_krylov_tol": [P, D],
         "ed_get_apply_config": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "ed_destroy": [P],
     }
@@ -253,6 +254,12 @@ def ed_apply_fermion_op(ctx, ctx_dst, site, spin, create, psi, out, dtype,
                         stream=None):
     _check(lib.ed_apply_fermion_op(ctx, ctx_dst, site, spin, 1 if create else 0,
                                    ptr(psi), ptr(out), dtype, stream_ptr(stream)), ctx)
+
+
+def ed_set_krylov_tol(ctx, tol):
+    """0: fixed Krylov dimension m (default); > 0: adaptive exit of
+    Algorithm 6 with m as the maximum."""
+    _check(lib.ed_set_krylov_tol(ctx, float(tol)), ctx)
 
 
 def ed_apply_config_count():

@@ -196,3 +196,14 @@ def test_apply_config_table_and_switch(ed):
     h = ed.Hubbard(synth.ring(6), 3, 3, 2.0)
     assert ed.ed_get_apply_config(h.ctx) == (-1, -1)   # nothing set up yet
     h.close()
+
+
+def test_krylov_tolerance_argument_checks(ed):
+    h = ed.Hubbard(synth.ring(6), 3, 3, 2.0)
+    ed.ed_set_krylov_tol(h.ctx, 1e-8)
+    ed.ed_set_krylov_tol(h.ctx, 0.0)
+    for bad in (-1e-3, float("nan"), float("inf")):
+        with pytest.raises(ed.EDError) as e:
+            ed.ed_set_krylov_tol(h.ctx, bad)
+        assert e.value.status == 1
+    h.close()

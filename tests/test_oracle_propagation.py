@@ -161,3 +161,86 @@ def test_observables_definitions():
         assert oracle.double_occupation(e, w, 4) == w[k] / 4
     lam, vec = np.linalg.eigh(H.toarray())
     assert abs(oracle.energy_per_site(H, vec[:, 3], 4) - lam[3] / 4) < 1e-14
+
+
+# ---------------------------------------------------------------- adaptive m
+# The a-posteriori exit of Algorithm 6: delta = |y^(j) - y^(j-1)| / |y^(j)|,
+# epsilon = min(1 + |y|, delta / (1 - delta) |y|) (delta < 1).
+
+def test_adaptive_estimate_two_level_closed_form():
+    """H = [[a, b], [b, a]], v = e_1: the Krylov space has dimension 2 and
+    exp(-i tau T_2) e_1 = exp(-i tau a) (cos tau|b|, -i sin tau|b|), so
+    delta = 2 |sin(tau |b| / 2)| exactly; y^(1) against y^(0) = 0 gives
+    delta = 1, epsilon = 1 + |y^(1)| = 2."""
+    a, b, tau = 0.7, -1.3, 0.4
+    H = np.array([[a, b], [b, a]], dtype=np.complex128)
+    v = np.array([1.0, 0.0], dtype=np.complex128)
+    out, info = oracle.lanczos_expm(H, v, tau, 3, eps_tol=1e-9)
+    assert info["m_eff"] == 2
+    assert info["eps_history"] == [2.0]
+    d = 2 * abs(np.sin(tau * abs(b) / 2))
+    assert abs(info["delta"] - d) < 1e-14
+    assert abs(info["eps"] - min(2.0, d / (1 - d))) < 1e-13
+    ref = sla.expm(-1j * tau * H) @ v
+    assert np.abs(out - ref).max() < 1e-14
+
+
+def test_adaptive_exit_is_first_converged_step_and_equals_truncation():
+    """The exit happens at the first j with epsilon_j < tol, and the result is
+    then exactly the fixed-m step with m = j (same arithmetic, truncated)."""
+    lat = synth.ring(6)
+    H = oracle.build_H(lat, 3, 2, 4.0, (0.4, 0.0, 0.0))
+    v = rand_vec(H.shape[0], 9)
+    for tau, tol in ((0.05, 1e-6), (0.05, 1e-10), (0.3, 1e-8)):
+        out, info = oracle.lanczos_expm(H, v, tau, 30, eps_tol=tol)
+        eh = info["eps_history"]
+        k = info["m_eff"]
+        assert k < 30 and len(eh) == k
+        assert eh[-1] < tol and all(e >= tol for e in eh[:-1])
+        ref, rinfo = oracle.lanczos_expm(H, v, tau, k)
+        assert rinfo["m_eff"] == k
+        assert np.abs(out - ref).max() == 0.0
+
+
+def test_adaptive_accuracy_against_dense_expm():
+    """The error of the adaptive step stays within a small multiple of the
+    tolerance (the estimate is within about an order of magnitude of the
+    error, Fig. of Sec. 3.4), and a tighter tolerance never uses fewer
+    vectors."""
+    lat = synth.ring(6)
+    H = oracle.build_H(lat, 3, 3, 6.0, (0.25, 0.0, 0.0))
+    Hd = H.toarray()
+    v = rand_vec(H.shape[0], 4)
+    for tau in (0.02, 0.1, 0.4):
+        ref = sla.expm(-1j * tau * Hd) @ v
+        prev_m = 0
+        for tol in (1e-4, 1e-7, 1e-10, 1e-13):
+            out, info = oracle.lanczos_expm(H, v, tau, 40, eps_tol=tol)
+            err = np.linalg.norm(out - ref)
+            assert err <= 100 * tol + 1e-14, (tau, tol, err, info["m_eff"])
+            assert info["m_eff"] >= prev_m
+            prev_m = info["m_eff"]
+
+
+def test_adaptive_with_tiny_tolerance_is_fixed_m():
+    lat = synth.ring(6)
+    H = oracle.build_H(lat, 3, 3, 6.0, (0.25, 0.0, 0.0))
+    v = rand_vec(H.shape[0], 2)
+    a, ia = oracle.lanczos_expm(H, v, 0.05, 14, eps_tol=1e-300)
+    b, ib = oracle.lanczos_expm(H, v, 0.05, 14)
+    assert ia["m_eff"] == ib["m_eff"] == 14
+    assert np.array_equal(a, b)
+
+
+def test_adaptive_trajectory_close_to_fixed_m():
+    """A pulsed ring trajectory with the adaptive exit stays within the
+    tolerance scale of the fixed-m trajectory and uses fewer vectors."""
+    lat = synth.ring(8)
+    psi0 = rand_vec(56 * 56, 3)
+    p = synth.PULSES["ring8"]
+    fixed = oracle.propagate(lat, 3, 3, 8.0, psi0, p, 0.02, 40, 20, t_start=4.0)
+    adap = oracle.propagate(lat, 3, 3, 8.0, psi0, p, 0.02, 40, 20, t_start=4.0,
+                            eps_tol=1e-10)
+    assert max(adap["m_eff"]) < 20
+    assert np.abs(adap["docc"] - fixed["docc"]).max() < 1e-8
+    assert np.linalg.norm(adap["psi"] - fixed["psi"]) < 1e-8
