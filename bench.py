@@ -46,6 +46,10 @@ def parse():
                     help="start from a seeded random state instead of the ground state")
     ap.add_argument("--no-spectral", action="store_true")
     ap.add_argument("--no-adaptive", action="store_true")
+    ap.add_argument("--m", type=int, default=0,
+                    help="Krylov dimension override for profiling runs (0: the workload's)")
+    ap.add_argument("--apply-config", type=int, default=None,
+                    help="pin the H v kernel configuration (default: autotuned)")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the ring and torus workloads")
     ap.add_argument("--small-steps", type=int, default=20)
@@ -219,6 +223,27 @@ def spectral_bench(ed, torch, synth, lat, w, pulse, h, psi64, stream, barrier, s
                     "a vector of the same dimension"}
 
 
+def profiled_traffic(apply_config):
+    """DRAM bytes per Lanczos-pass apply from the committed ncu summary, or
+    None when the kernel sources or the configuration differ from the
+    profiled ones (the counters no longer describe this kernel)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "apply_ladder2x7_c64_lanczos_dram.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    want = re.search(r"kernel_sources_sha256: ([0-9a-f]+)", txt)
+    val = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
+    cfg = re.search(r"apply configuration (\d+)", txt)
+    if not (want and val and cfg) or int(cfg.group(1)) != apply_config:
+        return None
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "tables.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_2005_13498_gb300", "csrc", f), "rb").read())
+    return int(val.group(1)) if h.hexdigest() == want.group(1) else None
+
+
 def adaptive_bench(ed, torch, h, psi32, pulse, t_start, dt, m, stream, barrier, steps):
     """ms per step of the ladder workload with the adaptive exit at two
     tolerances (complex64), with the Krylov dimensions the steps used."""
@@ -376,6 +401,10 @@ def main():
     lat = synth.lattice_from_name(w["lattice"])
     pulse = w["pulse_params"]
     dt, m = w["dt"], w["m"]
+    if args.m:            # profiling a smaller Krylov space (not the headline)
+        m = args.m
+    if args.apply_config is not None:
+        ed.ed_set_apply_config(args.apply_config)
     if args.apply_only:
         h = ed.Hubbard(lat, w["n_up"], w["n_dn"], w["U"])
         ed.ed_set_field(h.ctx, [0.3, 0.0, 0.0])
@@ -438,7 +467,7 @@ def main():
             "config": {"workload": "Ns=14 2x7 ladder (periodic legs, open rungs), n_up=n_dn=7, "
                                    "D=11,778,624, U=8, m=30, dt=0.02, pulse A0=0.5 Omega=8 "
                                    "sigma=2 t0=10 along the legs",
-                       "t_start": t_start, "m_eff_min": int(m_eff.min()),
+                       "t_start": t_start, "m": m, "m_eff_min": int(m_eff.min()),
                        "parallelism": f"replicas x{ws}",
                        "l2": "no flush: per-step working set 2.9 GB (31 Krylov vectors of "
                              "94 MB) > 129 MB L2"},
@@ -468,12 +497,12 @@ def main():
         bytes_apply = (2 + 3 * (m - 1)) / m * D * s
         a_ms = kern["apply"]["ms_per_launch"]
         achieved = bytes_apply / (a_ms * 1e-3) / 1e9
-        traffic = None
-        tp = os.path.join(ROOT, "profiles", "apply_traffic.json")
-        if os.path.exists(tp):
-            traffic = json.load(open(tp)).get("bytes_per_launch_c64_ladder")
+        traffic = profiled_traffic(acfg)
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                            "traffic_note": "ncu dram read + write of one j >= 2 pass "
+                                            "(profiles/apply_ladder2x7_c64_lanczos_dram.md); "
+                                            "null if the kernel changed since",
                             "kernel": ("k_apply_up + k_apply (split" if ainfo["split"]
                                        else "k_apply (one kernel") +
                                       ": w = s_j H x_j - beta s x_{j-1}, <v_j,w>)",
