@@ -46,6 +46,7 @@ def parse():
                     help="start from a seeded random state instead of the ground state")
     ap.add_argument("--no-spectral", action="store_true")
     ap.add_argument("--no-adaptive", action="store_true")
+    ap.add_argument("--no-ns16", action="store_true", help="skip the Ns=16 torus")
     ap.add_argument("--m", type=int, default=0,
                     help="Krylov dimension override for profiling runs (0: the workload's)")
     ap.add_argument("--apply-config", type=int, default=None,
@@ -266,6 +267,58 @@ def adaptive_bench(ed, torch, h, psi32, pulse, t_start, dt, m, stream, barrier, 
     ed.ed_set_krylov_tol(h.ctx, 0.0)
     res["note"] = ("m = 30 is the maximum; one Lanczos pass past the exit is computed "
                    "while the check runs")
+    return res
+
+
+def ns16_bench(ed, torch, synth, stream, barrier, steps, peak):
+    """Ns=16 4x4 torus at half filling, (8,8), D = 165,636,900 (1.3 GB per
+    complex64 vector): ms per midpoint step (complex64, m = 30, fixed and
+    with the adaptive exit at 1e-8) from a seeded random state inside the
+    pulse, and plain H v in both precisions."""
+    w = synth.workload("torus4x4")
+    lat = synth.lattice_from_name(w["lattice"])
+    p, dt, m = w["pulse_params"], w["dt"], w["m"]
+    h = ed.Hubbard(lat, w["n_up"], w["n_dn"], w["U"])
+    D = h.D
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    psi = torch.randn(D, dtype=torch.complex64, device="cuda", generator=gen)
+    psi /= torch.linalg.vector_norm(psi)
+    t_start = p["t0"] - 1.0
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    res = {"workload": "Ns=16 4x4 torus, (8,8), D=165,636,900, U=8, m=30, dt=0.02, "
+                       "pulse A0=0.5 Omega=8 sigma=2 t0=5 along (1,1)", "steps": steps}
+    for tol in (0.0, 1e-8):
+        ed.ed_set_krylov_tol(h.ctx, tol)
+        ed.ed_propagate(h.ctx, psi, ed.ED_C64, p, t_start - dt, dt, 1, m, stream=stream)
+        barrier()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        out = ed.ed_propagate(h.ctx, psi, ed.ED_C64, p, t_start, dt, steps, m, stream=stream)
+        e1.record(stream)
+        barrier()
+        key = "fixed_m30" if tol == 0.0 else "adaptive_1e-8"
+        res[key] = {"ms_per_step_c64": e0.elapsed_time(e1) / steps,
+                    "m_eff_mean": float(np.mean(out["m_eff"]))}
+    ed.ed_set_krylov_tol(h.ctx, 0.0)
+    ed.ed_set_field(h.ctx, pulse_field(p, t_start))
+    for name, tt, code, esz, n in (("c64", torch.complex64, ed.ED_C64, 8, 10),
+                                   ("c128", torch.complex128, ed.ED_C128, 16, 3)):
+        v = psi.to(tt)
+        wv = torch.empty_like(v)
+        ed.ed_apply_H(h.ctx, v, wv, code, stream=stream)
+        barrier()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(n):
+            ed.ed_apply_H(h.ctx, v, wv, code, stream=stream)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / n
+        gbs = 2 * D * esz / (ms * 1e-3) / 1e9
+        res[f"hv_{name}"] = {"ms": ms, "GBs": gbs, "frac_of_peak": gbs / peak}
+        del v, wv
+    res["apply_config_c64_step"] = ed.ed_get_apply_config(h.ctx)[0]
+    h.close()
     return res
 
 
@@ -560,6 +613,9 @@ def main():
         if not args.no_adaptive:
             line["adaptive"] = adaptive_bench(ed, torch, h, psi32, pulse, t_start, dt, m,
                                               stream, barrier, args.steps)
+        # Ns = 16 at half filling (beyond the paper's CSR memory limit)
+        if not args.no_ns16:
+            line["ns16"] = ns16_bench(ed, torch, synth, stream, barrier, 2, peak)
         # the ring and torus workloads (step times, H v on the seed-0 vector,
         # the torus spectral batch)
         if not args.no_small:

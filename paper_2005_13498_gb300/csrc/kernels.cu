@@ -1524,13 +1524,18 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     if (c.split && (sh.smem_c * (size_t)c.minbc > 228 * 1024 || sh.smem_c > 227 * 1024)) continue;
     out.push_back(sh);
   }
-  if (out.empty()) {   // very long rows: one row per CTA, one CTA per SM
+  if (out.empty()) {   // very long rows: one row per CTA, one CTA per SM;
+    // of those entries the one with the fewest target CTAs per SM (the
+    // largest register budget)
+    int best = -1;
     for (int i = 0; i < kNumApplyCfgs; ++i) {
       const ApplyCfg& c = kApplyCfgs[i];
       if (c.fp64 != fp64 || c.nr != 1 || c.split) continue;
-      LaunchShape sh = make(i);
+      if (best < 0 || c.minb < kApplyCfgs[best].minb) best = i;
+    }
+    if (best >= 0) {
+      LaunchShape sh = make(best);
       if (sh.smem <= 227 * 1024) out.push_back(sh);
-      break;
     }
   }
   return out;

@@ -99,6 +99,7 @@ def lattice_from_name(name):
         "ring8": lambda: ring(8),
         "torus3x4": lambda: torus(4, 3),
         "ladder2x7": lambda: ladder(7),
+        "torus4x4": lambda: torus(4, 4),
         "dimer": dimer,
         "triangle": triangle,
     }
