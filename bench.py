@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-spectral", action="store_true")
     ap.add_argument("--no-adaptive", action="store_true")
     ap.add_argument("--no-ns16", action="store_true", help="skip the Ns=16 torus")
+    ap.add_argument("--no-cfet4", action="store_true")
     ap.add_argument("--m", type=int, default=0,
                     help="Krylov dimension override for profiling runs (0: the workload's)")
     ap.add_argument("--apply-config", type=int, default=None,
@@ -319,6 +320,38 @@ def ns16_bench(ed, torch, synth, stream, barrier, steps, peak):
         del v, wv
     res["apply_config_c64_step"] = ed.ed_get_apply_config(h.ctx)[0]
     h.close()
+    return res
+
+
+def cfet4_bench(ed, torch, h, psi32, pulse, t_start, m, stream, barrier):
+    """Accuracy per cost on the ladder workload inside the pulse (complex64,
+    m = 30): the midpoint rule at dt = 0.02 against CFET4 at dt = 0.08 over
+    the same time window T = 0.32, both compared with CFET4 at dt = 0.01
+    (the reference); time per unit of physical time."""
+    T = 0.32
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def run(scheme, dt):
+        ed.ed_set_integrator(h.ctx, scheme)
+        psi = psi32.clone()
+        n = int(round(T / dt))
+        barrier()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        ed.ed_propagate(h.ctx, psi, ed.ED_C64, pulse, t_start, dt, n, m, stream=stream)
+        e1.record(stream)
+        barrier()
+        return psi, e0.elapsed_time(e1)
+
+    run("cfet4", 0.08)          # warm-up (engine setup, graph capture)
+    ref, _ = run("cfet4", 0.01)
+    res = {"window": f"T = {T} from t = {t_start}", "reference": "CFET4, dt = 0.01"}
+    for scheme, dt in (("midpoint", 0.02), ("cfet4", 0.08), ("cfet4", 0.04)):
+        run(scheme, dt)         # engine for this step count
+        psi, ms = run(scheme, dt)
+        err = float(torch.linalg.vector_norm(psi.to(torch.complex128) - ref.to(torch.complex128)))
+        res[f"{scheme} dt={dt}"] = {"ms_per_unit_time": ms / T, "state_error": err}
+    ed.ed_set_integrator(h.ctx, "midpoint")
     return res
 
 
@@ -613,6 +646,10 @@ def main():
         if not args.no_adaptive:
             line["adaptive"] = adaptive_bench(ed, torch, h, psi32, pulse, t_start, dt, m,
                                               stream, barrier, args.steps)
+        # fourth-order commutator-free integrator: accuracy per cost
+        if not args.no_cfet4:
+            line["cfet4"] = cfet4_bench(ed, torch, h, psi32, pulse, t_start, m, stream,
+                                        barrier)
         # Ns = 16 at half filling (beyond the paper's CSR memory limit)
         if not args.no_ns16:
             line["ns16"] = ns16_bench(ed, torch, synth, stream, barrier, 2, peak)

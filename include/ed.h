@@ -67,6 +67,17 @@ typedef enum {
 
 typedef enum { ED_C128 = 0, ED_C64 = 1 } ed_dtype;
 
+/* Time-stepping scheme of ed_propagate / ed_spectral_propagate.
+ * ED_MIDPOINT: the exponential midpoint rule of Eq. (32), one Krylov step of
+ *   Algorithm 6 per time step with H at the midpoint (second order).
+ * ED_CFET4: the fourth-order commutator-free exponential propagator (the
+ *   family named in Sec. 3.4; the two-exponential form of Alvermann and
+ *   Fehske, J. Comput. Phys. 230, 5930 (2011)):
+ *     psi(t+dt) = exp(-i dt (a1 H1 + a2 H2)) exp(-i dt (a2 H1 + a1 H2)) psi(t),
+ *   H_k = H(t + c_k dt), c_{1,2} = 1/2 -+ sqrt(3)/6, a_{1,2} = (3 -+ 2 sqrt(3))/12;
+ *   two Krylov steps of length dt/2 per time step.                            */
+typedef enum { ED_MIDPOINT = 0, ED_CFET4 = 1 } ed_integrator;
+
 /* Vector potential of the pump pulse, A(t) = A0 exp(-(t-t0)^2/(2 sigma^2))
  * sin(omega (t - t0)) * dir, entering every bond through A(t).d_b (Eq. (3)).
  * dir is used as given (not normalised).                                     */
@@ -248,6 +259,14 @@ ed_status ed_apply_fermion_op(ed_ctx* ctx, ed_ctx* ctx_dst, int site, int spin,
  * past the exit is computed and discarded.  ED_ERR_ARG for a negative or
  * non-finite tol.                                                            */
 ed_status ed_set_krylov_tol(ed_ctx* ctx, double tol);
+
+/* Select the time-stepping scheme (ed_integrator) for the ed_propagate and
+ * ed_spectral_propagate calls made on ctx after this one (default
+ * ED_MIDPOINT).  With ED_CFET4, n_steps, dt, m, the observables and the
+ * Green's functions keep their meaning per time step: docc, norm2 and energy
+ * are recorded at t_start + n dt, and m_eff / delta report the larger value of
+ * the step's two Krylov steps.  ED_ERR_ARG for an unknown scheme.            */
+ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme);
 
 /* Kernel configurations of H v (the matrix-vector product inside Lanczos,
  * Eq. (18) applied as T_up (x) 1 + 1 (x) T_dn + diagonal, Sec. 3.2).  Each

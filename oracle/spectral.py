@@ -24,7 +24,7 @@ Oracle (test infrastructure only).
 import numpy as np
 
 from .basis import spin_basis, rank_of, popcount
-from .krylov import make_H, lanczos_expm
+from .krylov import make_H, lanczos_expm, cfet4_factors
 from .hamiltonian import pulse_A
 
 
@@ -74,13 +74,15 @@ def apply_cdag(Ns, n_up, n_dn, psi, site, spin):
 
 
 def spectral_batch(lattice, n_up, n_dn, U, psi0, pulse, dt, n_steps, m,
-                   t_start=0.0, sites=None, form="auto", eps_tol=None):
+                   t_start=0.0, sites=None, form="auto", eps_tol=None,
+                   scheme="midpoint"):
     """L_{is}(n) and G_{is}(n) for n = 0..n_steps (arrays [n+1, Ns, 2]).
 
     psi is propagated in (n_up, n_dn); phi_{is} = c_{is} psi0 and
     phi'_{is} = c^+_{is} psi0 in their sectors, all with the same pulse, dt
     and Krylov dimension m (fixed, or at most m with the adaptive exit of
-    Algorithm 6 when eps_tol is given, each vector on its own).  Sectors that
+    Algorithm 6 when eps_tol is given, each vector on its own), by the
+    midpoint rule or by CFET4 (scheme).  Sectors that
     do not exist (n = 0 or n = Ns) give zeros.
     """
     Ns = lattice["Ns"]
@@ -105,21 +107,24 @@ def spectral_batch(lattice, n_up, n_dn, U, psi0, pulse, dt, n_steps, m,
             G[n, i, s] = np.vdot(apply_cdag(Ns, n_up, n_dn, psi, i, s), ph)
 
     record(0)
+
+    def step(vec, nu2, nd2, n):
+        if scheme == "cfet4":
+            Ha, Hb = cfet4_factors(lattice, nu2, nd2, U, pulse, t_start + n * dt, dt, form)
+            vec, _ = lanczos_expm(Ha, vec, dt, m, eps_tol=eps_tol)
+            vec, _ = lanczos_expm(Hb, vec, dt, m, eps_tol=eps_tol)
+            return vec
+        A = pulse_A(t_start + (n + 0.5) * dt, pulse)
+        vec, _ = lanczos_expm(make_H(lattice, nu2, nd2, U, A, form), vec, dt, m,
+                              eps_tol=eps_tol)
+        return vec
+
     for n in range(n_steps):
-        t_mid = t_start + (n + 0.5) * dt
-        A = pulse_A(t_mid, pulse)
-        psi, _ = lanczos_expm(make_H(lattice, n_up, n_dn, U, A, form),
-                              psi, dt, m, eps_tol=eps_tol)
+        psi = step(psi, n_up, n_dn, n)
         for (i, s) in list(phis):
-            nu2, nd2 = sector_shift(n_up, n_dn, "c", s)
-            phis[(i, s)], _ = lanczos_expm(
-                make_H(lattice, nu2, nd2, U, A, form), phis[(i, s)], dt, m,
-                eps_tol=eps_tol)
+            phis[(i, s)] = step(phis[(i, s)], *sector_shift(n_up, n_dn, "c", s), n)
         for (i, s) in list(phids):
-            nu2, nd2 = sector_shift(n_up, n_dn, "cdag", s)
-            phids[(i, s)], _ = lanczos_expm(
-                make_H(lattice, nu2, nd2, U, A, form), phids[(i, s)], dt, m,
-                eps_tol=eps_tol)
+            phids[(i, s)] = step(phids[(i, s)], *sector_shift(n_up, n_dn, "cdag", s), n)
         record(n + 1)
     return {"L": L, "G": G, "G_less": 1j * L, "G_greater": -1j * G,
             "psi": psi}

@@ -139,6 +139,50 @@ std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* puls
   return out;
 }
 
+// CFET4 (fourth-order commutator-free exponential propagator, the family
+// named in Sec. 3.4; two-exponential form of Alvermann and Fehske, J. Comput.
+// Phys. 230, 5930 (2011)): one step t -> t + dt is
+//   exp(-i dt (a1 H1 + a2 H2)) exp(-i dt (a2 H1 + a1 H2)),
+// H_k = H(t + c_k dt), c_{1,2} = 1/2 -+ sqrt(3)/6, a_{1,2} = (3 -+ 2 sqrt(3))/12.
+// Since a1 + a2 = 1/2, each factor equals exp(-i (dt/2) H~) with H~ the full
+// diagonal plus hopping coefficients 2 (a c_g(A1) + b c_g(A2)): a Krylov
+// sub-step of length dt/2 with combined group coefficients.
+SubSteps integrator_substeps(const ed_ctx* ctx, const ed_pulse* pulse, double t_start,
+                             double dt, int n_steps) {
+  SubSteps r;
+  if (ctx->integrator != ED_CFET4) {
+    r.coefs = step_coefficients(ctx->lat, pulse, t_start, dt, n_steps, true);
+    r.tau = dt;
+    r.per_step = 1;
+    return r;
+  }
+  const double s3 = std::sqrt(3.0);
+  const double c1 = 0.5 - s3 / 6.0, c2 = 0.5 + s3 / 6.0;
+  const double a1 = (3.0 - 2.0 * s3) / 12.0, a2 = (3.0 + 2.0 * s3) / 12.0;
+  const int ng = 2 * ctx->lat.n_classes;
+  r.coefs.assign((size_t)2 * n_steps * ng * 2, 0.0);
+  std::vector<double> g1(ng * 2), g2(ng * 2);
+  for (int n = 0; n < n_steps; ++n) {
+    const double t = t_start + n * dt;
+    double A1[3] = {0, 0, 0}, A2[3] = {0, 0, 0};
+    if (pulse) {
+      pulse_A(pulse->A0, pulse->omega, pulse->sigma, pulse->t0, pulse->dir, t + c1 * dt, A1);
+      pulse_A(pulse->A0, pulse->omega, pulse->sigma, pulse->t0, pulse->dir, t + c2 * dt, A2);
+    }
+    group_coefficients(ctx->lat, A1, g1.data());
+    group_coefficients(ctx->lat, A2, g2.data());
+    double* first = r.coefs.data() + (size_t)(2 * n) * ng * 2;     // a2 H1 + a1 H2
+    double* second = r.coefs.data() + (size_t)(2 * n + 1) * ng * 2; // a1 H1 + a2 H2
+    for (int k = 0; k < ng * 2; ++k) {
+      first[k] = 2.0 * (a2 * g1[k] + a1 * g2[k]);
+      second[k] = 2.0 * (a1 * g1[k] + a2 * g2[k]);
+    }
+  }
+  r.tau = 0.5 * dt;
+  r.per_step = 2;
+  return r;
+}
+
 }  // namespace ed
 
 extern "C" {
@@ -240,6 +284,14 @@ ed_status ed_set_krylov_tol(ed_ctx* ctx, double tol) {
   if (!(tol >= 0.0) || !std::isfinite(tol))
     return fail(ctx, ED_ERR_ARG, "tol must be finite and >= 0");
   ctx->krylov_tol = tol;
+  return ED_OK;
+}
+
+ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme) {
+  if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
+  if (scheme != ED_MIDPOINT && scheme != ED_CFET4)
+    return fail(ctx, ED_ERR_ARG, "unknown integrator");
+  ctx->integrator = scheme;
   return ED_OK;
 }
 
@@ -391,11 +443,15 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   const bool energy = obs && obs->energy;
   const bool profile = obs && obs->profile;
 
+  const SubSteps sub = integrator_substeps(ctx, pulse, t_start, dt, n_steps);
+  const int per = sub.per_step;
+  const int n_sub = n_steps * per;
+
   EngineConfig cfg;
   cfg.fp64 = fp64;
   cfg.m = m;
   cfg.energy = energy;
-  cfg.n_steps_cap = std::max(1, n_steps);
+  cfg.n_steps_cap = std::max(1, n_sub);
   cfg.eps_tol = ctx->krylov_tol;
   std::vector<EngineVector> vecs = {{0, D, on_device ? psi : nullptr, !on_device}};
   CK(ctx, join_streams(us, s));
@@ -411,16 +467,42 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   }
   Engine& E = *ctx->engine;
   if (!on_device) CK(ctx, cudaMemcpyAsync(E.vec_x1(0), psi, D * esz, cudaMemcpyHostToDevice, s));
-  std::vector<double> coefs = step_coefficients(ctx->lat, pulse, t_start, dt, n_steps, true);
+  // energy at the time-step boundaries t_start + k dt / per of the sub-steps
+  // (only every per-th entry, a whole time step, is reported)
   std::vector<double> coefs_obs;
-  if (energy) coefs_obs = step_coefficients(ctx->lat, pulse, t_start, dt, n_steps + 1, false);
-  CKS(ctx, E.begin(coefs, coefs_obs, n_steps, dt, s));
-  CKS(ctx, E.run(n_steps, profile, obs ? obs->kernel_ms : nullptr,
+  if (energy)
+    coefs_obs = step_coefficients(ctx->lat, pulse, t_start, dt / per, n_sub + 1, false);
+  CKS(ctx, E.begin(sub.coefs, coefs_obs, n_sub, sub.tau, s));
+  CKS(ctx, E.run(n_sub, profile, obs ? obs->kernel_ms : nullptr,
                  obs ? obs->kernel_launches : nullptr, s));
   int status = 0;
-  CKS(ctx, E.fetch(0, n_steps, obs ? obs->docc : nullptr, obs ? obs->norm2 : nullptr,
-                   energy ? obs->energy : nullptr, obs ? obs->delta : nullptr,
-                   obs ? obs->m_eff : nullptr, &status, s));
+  if (per == 1) {
+    CKS(ctx, E.fetch(0, n_steps, obs ? obs->docc : nullptr, obs ? obs->norm2 : nullptr,
+                     energy ? obs->energy : nullptr, obs ? obs->delta : nullptr,
+                     obs ? obs->m_eff : nullptr, &status, s));
+  } else {
+    std::vector<double> d(n_sub + 1), n2(n_sub + 1), en(n_sub + 1), dl(std::max(1, n_sub));
+    std::vector<int32_t> me(std::max(1, n_sub));
+    CKS(ctx, E.fetch(0, n_sub, d.data(), n2.data(), energy ? en.data() : nullptr, dl.data(),
+                     me.data(), &status, s));
+    if (obs) {
+      for (int n = 0; n <= n_steps; ++n) {
+        if (obs->docc) obs->docc[n] = d[(size_t)n * per];
+        if (obs->norm2) obs->norm2[n] = n2[(size_t)n * per];
+        if (energy) obs->energy[n] = en[(size_t)n * per];
+      }
+      for (int n = 0; n < n_steps; ++n) {
+        double dmax = 0.0;
+        int mmax = 0;
+        for (int k = 0; k < per; ++k) {
+          dmax = std::max(dmax, dl[(size_t)n * per + k]);
+          mmax = std::max(mmax, me[(size_t)n * per + k]);
+        }
+        if (obs->delta) obs->delta[n] = dmax;
+        if (obs->m_eff) obs->m_eff[n] = mmax;
+      }
+    }
+  }
   if (!on_device) {
     CK(ctx, cudaMemcpyAsync(psi, E.vec_x1(0), D * esz, cudaMemcpyDeviceToHost, s));
     CK(ctx, cudaStreamSynchronize(s));

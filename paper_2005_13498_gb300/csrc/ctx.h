@@ -49,6 +49,7 @@ struct ed_ctx {
   ed::SectorGPU sec;
   double A[3] = {0, 0, 0};
   double krylov_tol = 0.0;   // > 0: adaptive Krylov dimension (Algorithm 6)
+  int integrator = 0;        // ED_MIDPOINT or ED_CFET4
   std::string err;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -71,6 +72,16 @@ bool is_device_ptr(const void* p);
 cudaError_t join_streams(cudaStream_t from, cudaStream_t to);
 std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* pulse,
                                       double t_start, double dt, int n_steps, bool mid);
+// The Krylov sub-steps of n_steps time steps of the context's integrator:
+// per-sub-step group coefficients, the sub-step length, and the number of
+// sub-steps per time step (1 for the midpoint rule, 2 for CFET4).
+struct SubSteps {
+  std::vector<double> coefs;
+  double tau = 0.0;
+  int per_step = 1;
+};
+SubSteps integrator_substeps(const ed_ctx* ctx, const ed_pulse* pulse, double t_start,
+                             double dt, int n_steps);
 
 template <typename T>
 cudaError_t upload(DevMem& m, const std::vector<T>& v) {

@@ -371,7 +371,10 @@ ed_status ed_spectral_propagate(ed_ctx* ctx, const void* psi0, ed_dtype dtype,
   cfg.fp64 = fp64;
   cfg.m = m;
   cfg.overlaps = true;
-  cfg.n_steps_cap = std::max(1, n_steps);
+  const SubSteps sub = integrator_substeps(ctx, pulse, 0.0, dt, n_steps);
+  const int per = sub.per_step;
+  const int n_sub = n_steps * per;
+  cfg.n_steps_cap = std::max(1, n_sub);
   cfg.eps_tol = ctx->krylov_tol;
   CK(ctx, join_streams(us, s));
   if (!ctx->spec_engine || !ctx->spec_engine->compatible(cfg, vecs)) {
@@ -404,11 +407,10 @@ ed_status ed_spectral_propagate(ed_ctx* ctx, const void* psi0, ed_dtype dtype,
                               (int)ctx->dim_dn, sd.dim_up, sd.dim_dn, f.spin,
                               static_cast<const int32_t*>(dmaps.p) + moff[f.vec], s));
   }
-  std::vector<double> coefs = step_coefficients(ctx->lat, pulse, 0.0, dt, n_steps, true);
-  CKS(ctx, E.begin(coefs, {}, n_steps, dt, s));
-  CKS(ctx, E.run(n_steps, false, nullptr, nullptr, s));
+  CKS(ctx, E.begin(sub.coefs, {}, n_sub, sub.tau, s));
+  CKS(ctx, E.run(n_sub, false, nullptr, nullptr, s));
   std::vector<double> ov;
-  CKS(ctx, E.fetch_overlaps(n_steps, ov, s));
+  CKS(ctx, E.fetch_overlaps(n_sub, ov, s));
   int status = 0;
   for (int v = 0; v < E.nvec(); ++v) {
     int st = 0;
@@ -422,7 +424,8 @@ ed_status ed_spectral_propagate(ed_ctx* ctx, const void* psi0, ed_dtype dtype,
   const int nv = E.nvec();
   for (int n = 0; n <= n_steps; ++n)
     for (const Phi& f : phis) {
-      const double re = ov[((size_t)n * nv + f.vec) * 2], im = ov[((size_t)n * nv + f.vec) * 2 + 1];
+      const size_t k = (size_t)n * per;   // overlaps after whole time steps
+      const double re = ov[(k * nv + f.vec) * 2], im = ov[(k * nv + f.vec) * 2 + 1];
       const size_t o = (((size_t)n * Ns + f.site) * 2 + f.spin) * 2;
       if (f.op == 0) {  // G^< = i L
         G_less[o] = -im;

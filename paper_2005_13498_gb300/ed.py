@@ -17,6 +17,8 @@ from . import build as _build
 
 ED_C128 = 0
 ED_C64 = 1
+ED_MIDPOINT = 0
+ED_CFET4 = 1
 ED_KERNEL_KINDS = 6
 KERNEL_KIND_NAMES = ["apply", "update", "expm", "combine", "energy", "overlap"]
 
@@ -75,6 +77,7 @@ def _load():
         "ed_apply_config_info": [I] + [ctypes.POINTER(ctypes.c_int)] * 5,
         "ed_set_apply_config": [I],
         "ed_set_krylov_tol": [P, D],
+        "ed_set_integrator": [P, I],
         "ed_get_apply_config": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "ed_destroy": [P],
     }
@@ -260,6 +263,14 @@ def ed_set_krylov_tol(ctx, tol):
     """0: fixed Krylov dimension m (default); > 0: adaptive exit of
     Algorithm 6 with m as the maximum."""
     _check(lib.ed_set_krylov_tol(ctx, float(tol)), ctx)
+
+
+def ed_set_integrator(ctx, scheme):
+    """ED_MIDPOINT (Eq. (32), default) or ED_CFET4 (fourth order, two Krylov
+    steps of dt/2 per time step); also accepts "midpoint" / "cfet4"."""
+    if isinstance(scheme, str):
+        scheme = {"midpoint": ED_MIDPOINT, "cfet4": ED_CFET4}[scheme]
+    _check(lib.ed_set_integrator(ctx, int(scheme)), ctx)
 
 
 def ed_apply_config_count():

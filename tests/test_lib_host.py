@@ -207,3 +207,13 @@ def test_krylov_tolerance_argument_checks(ed):
             ed.ed_set_krylov_tol(h.ctx, bad)
         assert e.value.status == 1
     h.close()
+
+
+def test_integrator_argument_checks(ed):
+    h = ed.Hubbard(synth.ring(6), 3, 3, 2.0)
+    ed.ed_set_integrator(h.ctx, ed.ED_CFET4)
+    ed.ed_set_integrator(h.ctx, "midpoint")
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_set_integrator(h.ctx, 7)
+    assert e.value.status == 1
+    h.close()

@@ -244,3 +244,70 @@ def test_adaptive_trajectory_close_to_fixed_m():
     assert max(adap["m_eff"]) < 20
     assert np.abs(adap["docc"] - fixed["docc"]).max() < 1e-8
     assert np.linalg.norm(adap["psi"] - fixed["psi"]) < 1e-8
+
+
+# -------------------------------------------------------------------- CFET4
+# exp(-i tau (a1 H1 + a2 H2)) exp(-i tau (a2 H1 + a1 H2)), H_k = H(t + c_k tau)
+
+def test_cfet4_coefficients():
+    """Gauss-Legendre nodes of [0, 1] and weights summing to 1/2 per factor
+    with a1 - a2 = -sqrt(3)/3 (the conditions of fourth order)."""
+    c1, c2 = oracle.CFET4_C
+    a1, a2 = oracle.CFET4_A
+    x, w = np.polynomial.legendre.leggauss(2)
+    assert np.allclose(sorted([c1, c2]), (x + 1) / 2, atol=1e-15)
+    assert abs(a1 + a2 - 0.5) < 1e-15
+    assert abs((a1 - a2) + np.sqrt(3) / 3) < 1e-15
+
+
+def test_cfet4_time_independent_is_exact_exponential():
+    lat = synth.ring(6)
+    psi0 = rand_vec(400, 8)
+    H = oracle.build_H(lat, 3, 3, 5.0, (0.0, 0.0, 0.0)).toarray()
+    res = oracle.propagate(lat, 3, 3, 5.0, psi0, None, 0.1, 6, 24, form="csr",
+                           scheme="cfet4")
+    ref = sla.expm(-0.6j * H) @ psi0
+    assert np.linalg.norm(res["psi"] - ref) < 1e-11
+
+
+@pytest.mark.parametrize("lat,sec", [(synth.ring(6), (3, 2)), (synth.triangle(), (2, 1))])
+def test_cfet4_free_fermions_are_slater_of_one_electron_cfet4(lat, sec):
+    """U = 0: the many-body CFET4 step is the determinant-minor lift of the
+    one-electron CFET4 step (each factor is a quadratic Hamiltonian)."""
+    pulse = {"A0": 0.9, "omega": 5.0, "sigma": 0.6, "t0": 0.5, "dir": (1.0, 0.7, 0.0)}
+    dt, n_steps = 0.1, 12
+    Ns = lat["Ns"]
+    D = oracle.sector_dims(Ns, *sec)[2]
+    psi0 = rand_vec(D, 4)
+    res = oracle.propagate(lat, *sec, 0.0, psi0, pulse, dt, n_steps, 24, form="csr",
+                           scheme="cfet4")
+    (c1, c2), (a1, a2) = oracle.CFET4_C, oracle.CFET4_A
+    u = np.eye(Ns, dtype=complex)
+    for n in range(n_steps):
+        h1 = oracle.single_particle_matrix(lat, oracle.pulse_A((n + c1) * dt, pulse))
+        h2 = oracle.single_particle_matrix(lat, oracle.pulse_A((n + c2) * dt, pulse))
+        u = sla.expm(-1j * dt * (a1 * h1 + a2 * h2)) @ sla.expm(-1j * dt * (a2 * h1 + a1 * h2)) @ u
+    Mu = minors_matrix(u, Ns, sec[0])
+    Md = minors_matrix(u, Ns, sec[1])
+    ref = (Mu @ psi0.reshape(Mu.shape[0], -1) @ Md.T).reshape(-1)
+    assert np.linalg.norm(res["psi"] - ref) < 1e-11
+
+
+def test_cfet4_is_fourth_order():
+    """Error at T = 1.2 against a dt/16 reference, for dt and dt/2: the
+    observed order is >= 3.8 (midpoint: about 2)."""
+    lat = synth.ring(6)
+    psi0 = rand_vec(400, 6)
+    p = {"A0": 0.8, "omega": 4.0, "sigma": 0.5, "t0": 0.6, "dir": (1.0, 0.0, 0.0)}
+
+    def run(dt, scheme):
+        n = int(round(1.2 / dt))
+        return oracle.propagate(lat, 3, 3, 4.0, psi0, p, dt, n, 30, form="csr",
+                                scheme=scheme)["psi"]
+    ref = run(0.1 / 16, "cfet4")
+    e1 = np.linalg.norm(run(0.1, "cfet4") - ref)
+    e2 = np.linalg.norm(run(0.05, "cfet4") - ref)
+    order = np.log2(e1 / e2)
+    assert order >= 3.8, order
+    em = np.linalg.norm(run(0.05, "midpoint") - ref)
+    assert e2 < em / 10
