@@ -426,6 +426,27 @@ def smaller_workloads_bench(ed, torch, synth, stream, barrier, steps):
             e1.record(stream)
             barrier()
             bms = e0.elapsed_time(e1) / steps
+            # A(nu, t_ref) at t_ref = 1.0 (Eq. (15) and Eq. (A_noneq_broad)):
+            # psi to t_ref, the batch from t_ref, the broadened transform
+            t_ref, n_tr = 1.0, 2 * steps
+            x = g.clone()
+            barrier()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            ed.ed_propagate(h.ctx, x, ed.ED_C128, p, 0.0, ws["dt"], int(round(t_ref / ws["dt"])),
+                            ws["m"], stream=stream)
+            Gl, Gg = ed.ed_spectral_propagate_at(h.ctx, x, t_ref, ed.ED_C64, p, ws["dt"], n_tr,
+                                                 ws["m"], 12, stream=stream)
+            nu = np.linspace(-12.0, 12.0, 241)
+            Anu = (ed.ed_spectral_function(Gl, ws["dt"], 0.2, nu) +
+                   ed.ed_spectral_function(Gg, ws["dt"], 0.2, nu))
+            e1.record(stream)
+            barrier()
+            out["torus3x4_A_nu_tref"] = {
+                "workload": f"A(nu, t_ref = {t_ref}) of the 3x4 torus: psi propagated to t_ref "
+                            f"(complex128, m=20), {n_tr} batch steps (complex64), transform on "
+                            f"{len(nu)} frequencies, eps = 0.2",
+                "ms_total": e0.elapsed_time(e1), "A_site_avg_max": float(Anu.mean(axis=(1, 2)).max())}
             out["torus3x4_spectral"] = {
                 "workload": "Ns=12 3x4 torus spectral batch: 48 c/c+ vectors of dim 731,808 "
                             "+ psi, complex64, m=20, dt=0.02",

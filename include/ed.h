@@ -78,12 +78,24 @@ typedef enum { ED_C128 = 0, ED_C64 = 1 } ed_dtype;
  *   two Krylov steps of length dt/2 per time step.                            */
 typedef enum { ED_MIDPOINT = 0, ED_CFET4 = 1 } ed_integrator;
 
-/* Vector potential of the pump pulse, A(t) = A0 exp(-(t-t0)^2/(2 sigma^2))
- * sin(omega (t - t0)) * dir, entering every bond through A(t).d_b (Eq. (3)).
- * dir is used as given (not normalised).                                     */
+/* Vector potential of the pump pulse, entering every bond through its phase
+ * A(t).d_b (Eq. (3)); dir is used as given (not normalised).
+ * shape ED_PULSE_SIN_GAUSS (0):
+ *   A(t) = A0 exp(-(t-t0)^2/(2 sigma^2)) sin(omega (t - t0)) dir,
+ *   the vector potential of the field pulse of Eq. (2) up to the integration.
+ * shape ED_PULSE_COS_PHASE (1): the paper's simplified phase of Eq. (5),
+ *   A(t) = -A0 [cos(omega (t - t0)) - b] exp(-(t-t0)^2/(2 sigma^2)) dir,
+ *   so that a hop p -> q with dir.d_b = 1 carries exactly the factor
+ *   f(t) = exp(i a [cos(omega (t - t_p)) - b] exp(-(t-t_p)^2/(2 sigma^2)))
+ *   with a = A0, t_p = t0 (b = cos(omega t0) makes f(0) = 1).
+ * A zero-initialised shape/b gives the first form.                            */
+typedef enum { ED_PULSE_SIN_GAUSS = 0, ED_PULSE_COS_PHASE = 1 } ed_pulse_shape;
 typedef struct {
   double A0, omega, sigma, t0;
   double dir[3];
+  double b;        /* ED_PULSE_COS_PHASE only                                 */
+  int shape;       /* ed_pulse_shape                                          */
+  int reserved;    /* must be 0                                               */
 } ed_pulse;
 
 /* Optional per-step outputs of ed_propagate (all host arrays, each nullable). */
@@ -234,6 +246,27 @@ ed_status ed_spectral_propagate(ed_ctx* ctxN, const void* psi0,
                                 ed_dtype dtype, const ed_pulse* pulse,
                                 double dt, int n_steps, int m,
                                 double* G_less, double* G_great, void* stream);
+
+/* ed_spectral_propagate with the reference time t_ref of Eq. (15) instead of
+ * 0: psi0 is the state psi(t_ref) (e.g. the ground state propagated to t_ref
+ * with ed_propagate and the same pulse), and G_less[n] / G_great[n] are the
+ * Green's functions at times (t_ref, t_ref + n dt), the pulse evaluated at
+ * the absolute times.  Same arguments, outputs and errors otherwise.        */
+ed_status ed_spectral_propagate_at(ed_ctx* ctxN, const void* psi0, double t_ref,
+                                   ed_dtype dtype, const ed_pulse* pulse,
+                                   double dt, int n_steps, int m,
+                                   double* G_less, double* G_great, void* stream);
+
+/* Broadened Fourier transform of Eq. (A_noneq_broad) (Sec. 3.7), on the host:
+ *   A[f][j] = (1/pi) Im int_0^{T} e^{-eps t} e^{i nu_f t} G_j(t) dt,
+ * T = n_steps dt, by the trapezoid rule over the samples G_j(k dt),
+ * k = 0..n_steps.  G: host array [n_steps+1][n_series] complex128
+ * (interleaved re, im), e.g. G_less or G_great of ed_spectral_propagate with
+ * n_series = 2 Ns; nu: host [n_nu]; A: host [n_nu][n_series].  A(nu, t) of
+ * the paper is the sum of the A of G_less and of G_great.  ED_ERR_ARG for
+ * NULL pointers, sizes < 1, dt <= 0 or eps < 0.                              */
+ed_status ed_spectral_function(const double* G, int n_steps, int n_series, double dt,
+                               double eps, const double* nu, int n_nu, double* A);
 
 /* Apply c_is (create = 0) or c^+_is (create = 1) to psi of ctx's sector and
  * write the result into out (a vector of ctx_dst's sector, which must be

@@ -32,13 +32,13 @@ from .hamiltonian import (pulse_A, bond_phases, spin_hopping_matrix,
 from .krylov import (lanczos_expm, propagate, ground_state, small_expm_e1,
                      double_occupation, energy_per_site, cfet4_factors,
                      epsilon_estimate, CFET4_A, CFET4_C)
-from .spectral import (apply_c, apply_cdag, sector_shift, spectral_batch,
+from .spectral import (broadened_transform, apply_c, apply_cdag, sector_shift, spectral_batch,
                        lehmann_overlaps)
 
 __all__ = [
     "spin_basis", "rank_of", "sector_dims", "binom", "pulse_A", "bond_phases",
     "spin_hopping_matrix", "build_H", "diag_U", "double_occupancy_weights",
-    "single_particle_matrix", "lanczos_expm", "propagate", "ground_state",
+    "single_particle_matrix", "lanczos_expm", "broadened_transform", "propagate", "ground_state",
     "cfet4_factors", "epsilon_estimate", "CFET4_A", "CFET4_C",
     "small_expm_e1", "double_occupation", "energy_per_site", "apply_c",
     "apply_cdag", "sector_shift", "spectral_batch", "lehmann_overlaps",

@@ -33,12 +33,22 @@ from .basis import spin_basis, rank_of, popcount
 
 
 def pulse_A(t, pulse):
-    """Vector potential A(t) (3-vector) of the workload pulse."""
+    """Vector potential A(t) (3-vector) of a pulse.
+
+    shape "sin" (default): A0 exp(-s^2/(2 sigma^2)) sin(omega s) dir, s = t - t0.
+    shape "cos_phase": the paper's phase function of Eq. (5) written as a
+    vector potential, A(t) = -A0 [cos(omega s) - b] exp(-s^2/(2 sigma^2)) dir,
+    so a hop along dir (d_b . dir = 1) carries f(t) = exp(i a [cos(omega
+    (t - t_p)) - b] e^{-(t-t_p)^2/(2 sigma^2)}) with a = A0, t_p = t0.
+    """
     if pulse is None:
         return np.zeros(3)
     s = t - pulse["t0"]
-    amp = pulse["A0"] * np.exp(-s * s / (2.0 * pulse["sigma"] ** 2)) * \
-        np.sin(pulse["omega"] * s)
+    env = np.exp(-s * s / (2.0 * pulse["sigma"] ** 2))
+    if pulse.get("shape", "sin") == "cos_phase":
+        amp = -pulse["A0"] * (np.cos(pulse["omega"] * s) - pulse.get("b", 0.0)) * env
+    else:
+        amp = pulse["A0"] * env * np.sin(pulse["omega"] * s)
     return amp * np.asarray(pulse["dir"], dtype=np.float64)
 
 

@@ -147,3 +147,17 @@ def lehmann_overlaps(lattice, n_up, n_dn, U, psi0, E0, times, site, spin):
         out[op] = np.array([np.sum(wts * np.exp(-1j * (lam - E0) * t))
                             for t in times])
     return out["c"], out["cdag"]
+
+
+def broadened_transform(G, dt, eps, nu):
+    """Eq. (A_noneq_broad), Sec. 3.7: A(nu) = (1/pi) Im int_0^T e^{-eps t}
+    e^{i nu t} G(t) dt with T = (len(G) - 1) dt, the integral by the
+    trapezoid rule over the samples G[k] = G(k dt).  G: [n+1, ...]."""
+    G = np.asarray(G, dtype=np.complex128)
+    t = np.arange(G.shape[0]) * dt
+    out = []
+    for v in np.atleast_1d(nu):
+        f = (np.exp((-eps + 1j * v) * t)).reshape((-1,) + (1,) * (G.ndim - 1)) * G
+        integral = dt * (f.sum(axis=0) - 0.5 * (f[0] + f[-1]))
+        out.append(integral.imag / np.pi)
+    return np.array(out)

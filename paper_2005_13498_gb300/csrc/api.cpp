@@ -126,6 +126,21 @@ cudaError_t join_streams(cudaStream_t from, cudaStream_t to) {
   return e;
 }
 
+ed_status check_pulse(ed_ctx* ctx, const ed_pulse* pulse) {
+  if (!pulse) return ED_OK;
+  if (!(std::isfinite(pulse->A0) && std::isfinite(pulse->omega) &&
+        std::isfinite(pulse->sigma) && pulse->sigma != 0.0 && std::isfinite(pulse->t0) &&
+        std::isfinite(pulse->b)))
+    return fail(ctx, ED_ERR_ARG, "pulse parameters not finite or sigma == 0");
+  if (pulse->shape != ED_PULSE_SIN_GAUSS && pulse->shape != ED_PULSE_COS_PHASE)
+    return fail(ctx, ED_ERR_ARG, "unknown pulse shape");
+  return ED_OK;
+}
+
+static void pulse_at(const ed_pulse& p, double t, double A[3]) {
+  pulse_A(p.shape, p.A0, p.omega, p.sigma, p.t0, p.b, p.dir, t, A);
+}
+
 std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* pulse,
                                       double t_start, double dt, int n_steps, bool mid) {
   const int ng = 2 * L.n_classes;
@@ -133,7 +148,7 @@ std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* puls
   for (int n = 0; n < n_steps; ++n) {
     const double t = t_start + (n + (mid ? 0.5 : 0.0)) * dt;
     double A[3] = {0, 0, 0};
-    if (pulse) pulse_A(pulse->A0, pulse->omega, pulse->sigma, pulse->t0, pulse->dir, t, A);
+    if (pulse) pulse_at(*pulse, t, A);
     group_coefficients(L, A, out.data() + (size_t)n * ng * 2);
   }
   return out;
@@ -166,8 +181,8 @@ SubSteps integrator_substeps(const ed_ctx* ctx, const ed_pulse* pulse, double t_
     const double t = t_start + n * dt;
     double A1[3] = {0, 0, 0}, A2[3] = {0, 0, 0};
     if (pulse) {
-      pulse_A(pulse->A0, pulse->omega, pulse->sigma, pulse->t0, pulse->dir, t + c1 * dt, A1);
-      pulse_A(pulse->A0, pulse->omega, pulse->sigma, pulse->t0, pulse->dir, t + c2 * dt, A2);
+      pulse_at(*pulse, t + c1 * dt, A1);
+      pulse_at(*pulse, t + c2 * dt, A2);
     }
     group_coefficients(ctx->lat, A1, g1.data());
     group_coefficients(ctx->lat, A2, g2.data());
@@ -430,9 +445,7 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   if (m < 1) return fail(ctx, ED_ERR_ARG, "m < 1");
   if (m > kMaxKrylov) return fail(ctx, ED_ERR_UNSUPPORTED, "m > 64");
   if (!std::isfinite(dt) || !std::isfinite(t_start)) return fail(ctx, ED_ERR_ARG, "dt/t_start not finite");
-  if (pulse && !(std::isfinite(pulse->A0) && std::isfinite(pulse->omega) &&
-                 std::isfinite(pulse->sigma) && pulse->sigma != 0.0 && std::isfinite(pulse->t0)))
-    return fail(ctx, ED_ERR_ARG, "pulse parameters not finite or sigma == 0");
+  if (ed_status e = check_pulse(ctx, pulse)) return e;
   if (ed_status e = ensure_device(ctx)) return e;
   cudaStream_t us = static_cast<cudaStream_t>(stream);
   cudaStream_t s = ctx->stream;

@@ -72,6 +72,8 @@ bool is_device_ptr(const void* p);
 cudaError_t join_streams(cudaStream_t from, cudaStream_t to);
 std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* pulse,
                                       double t_start, double dt, int n_steps, bool mid);
+// ED_ERR_ARG (recorded on ctx) for non-finite parameters or an unknown shape.
+ed_status check_pulse(ed_ctx* ctx, const ed_pulse* pulse);
 // The Krylov sub-steps of n_steps time steps of the context's integrator:
 // per-sub-step group coefficients, the sub-step length, and the number of
 // sub-steps per time step (1 for the midpoint rule, 2 for CFET4).

@@ -311,12 +311,21 @@ ed_status ed_ground_state(ed_ctx* ctx, void* psi, double* E0, double tol, int ma
 ed_status ed_spectral_propagate(ed_ctx* ctx, const void* psi0, ed_dtype dtype,
                                 const ed_pulse* pulse, double dt, int n_steps, int m,
                                 double* G_less, double* G_great, void* stream) {
+  return ed_spectral_propagate_at(ctx, psi0, 0.0, dtype, pulse, dt, n_steps, m, G_less,
+                                  G_great, stream);
+}
+
+ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
+                                   ed_dtype dtype, const ed_pulse* pulse, double dt,
+                                   int n_steps, int m, double* G_less, double* G_great,
+                                   void* stream) {
   if (!ctx || !psi0 || !G_less || !G_great) return fail(ctx, ED_ERR_ARG, "NULL argument");
   if (!ctx->lattice_set) return fail(ctx, ED_ERR_STATE, "ed_set_lattice has not been called");
   if (dtype != ED_C128 && dtype != ED_C64) return fail(ctx, ED_ERR_ARG, "bad dtype");
   if (n_steps < 0 || m < 1) return fail(ctx, ED_ERR_ARG, "n_steps >= 0 and m >= 1 required");
   if (m > kMaxKrylov) return fail(ctx, ED_ERR_UNSUPPORTED, "m > 64");
-  if (!std::isfinite(dt)) return fail(ctx, ED_ERR_ARG, "dt not finite");
+  if (!std::isfinite(dt) || !std::isfinite(t_ref)) return fail(ctx, ED_ERR_ARG, "dt/t_ref not finite");
+  if (ed_status e = check_pulse(ctx, pulse)) return e;
   if (ed_status e = ensure_device(ctx)) return e;
   cudaStream_t us = static_cast<cudaStream_t>(stream);
   cudaStream_t s = ctx->stream;
@@ -371,7 +380,7 @@ ed_status ed_spectral_propagate(ed_ctx* ctx, const void* psi0, ed_dtype dtype,
   cfg.fp64 = fp64;
   cfg.m = m;
   cfg.overlaps = true;
-  const SubSteps sub = integrator_substeps(ctx, pulse, 0.0, dt, n_steps);
+  const SubSteps sub = integrator_substeps(ctx, pulse, t_ref, dt, n_steps);
   const int per = sub.per_step;
   const int n_sub = n_steps * per;
   cfg.n_steps_cap = std::max(1, n_sub);
@@ -436,6 +445,33 @@ ed_status ed_spectral_propagate(ed_ctx* ctx, const void* psi0, ed_dtype dtype,
       }
     }
   if (status != 0) return fail(ctx, ED_ERR_NUMERIC, "non-finite norm during spectral propagation");
+  return ED_OK;
+}
+
+// Eq. (A_noneq_broad), Sec. 3.7: A(nu) = (1/pi) Im int_0^T e^{-eps t} e^{i nu t}
+// G(t) dt over the samples G(k dt), k = 0..n_steps, by the trapezoid rule.
+ed_status ed_spectral_function(const double* G, int n_steps, int n_series, double dt,
+                               double eps, const double* nu, int n_nu, double* A) {
+  if (!G || !nu || !A) return fail(nullptr, ED_ERR_ARG, "NULL argument");
+  if (n_steps < 1 || n_series < 1 || n_nu < 1)
+    return fail(nullptr, ED_ERR_ARG, "n_steps, n_series, n_nu must be >= 1");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !(eps >= 0.0) || !std::isfinite(eps))
+    return fail(nullptr, ED_ERR_ARG, "dt > 0 and eps >= 0 required");
+  for (int f = 0; f < n_nu; ++f) {
+    for (int j = 0; j < n_series; ++j) {
+      double sr = 0.0, si = 0.0;   // sum of weights * e^{(i nu - eps) t} G(t)
+      for (int k = 0; k <= n_steps; ++k) {
+        const double t = k * dt;
+        const double wgt = (k == 0 || k == n_steps) ? 0.5 : 1.0;
+        const double damp = wgt * std::exp(-eps * t);
+        const double c = std::cos(nu[f] * t) * damp, sn = std::sin(nu[f] * t) * damp;
+        const double gr = G[((size_t)k * n_series + j) * 2], gi = G[((size_t)k * n_series + j) * 2 + 1];
+        sr += c * gr - sn * gi;
+        si += c * gi + sn * gr;
+      }
+      A[(size_t)f * n_series + j] = si * dt / 3.14159265358979323846;
+    }
+  }
   return ED_OK;
 }
 

@@ -261,10 +261,12 @@ void group_coefficients(const LatticeHost& L, const double A[3], double* out) {
   }
 }
 
-void pulse_A(const double A0, double omega, double sigma, double t0, const double dir[3],
-             double t, double out[3]) {
+void pulse_A(int shape, double A0, double omega, double sigma, double t0, double b,
+             const double dir[3], double t, double out[3]) {
   const double s = t - t0;
-  const double amp = A0 * std::exp(-s * s / (2.0 * sigma * sigma)) * std::sin(omega * s);
+  const double env = std::exp(-s * s / (2.0 * sigma * sigma));
+  const double amp = shape == 1 ? -A0 * (std::cos(omega * s) - b) * env
+                                : A0 * env * std::sin(omega * s);
   for (int k = 0; k < 3; ++k) out[k] = amp * dir[k];
 }
 

@@ -86,8 +86,10 @@ SpinTable build_spin_table(const LatticeHost& L, int n);
 // written as interleaved (re, im) doubles, 2 * n_classes complex numbers.
 void group_coefficients(const LatticeHost& L, const double A[3], double* out);
 
-// Vector potential of the pump pulse at time t.
-void pulse_A(const double A0, double omega, double sigma, double t0,
+// Vector potential of the pump pulse at time t (shape 0: A0 e^{-s^2/2sigma^2}
+// sin(omega s) dir; shape 1: -A0 [cos(omega s) - b] e^{-s^2/2sigma^2} dir,
+// s = t - t0).
+void pulse_A(int shape, double A0, double omega, double sigma, double t0, double b,
              const double dir[3], double t, double out[3]);
 
 // Map for c_{i,s} (create = false) or c^+_{i,s} (create = true) from the

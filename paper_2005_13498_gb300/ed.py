@@ -33,10 +33,15 @@ class EDError(RuntimeError):
         self.status = status
 
 
+ED_PULSE_SIN_GAUSS = 0
+ED_PULSE_COS_PHASE = 1
+
+
 class ed_pulse(ctypes.Structure):
     _fields_ = [("A0", ctypes.c_double), ("omega", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("t0", ctypes.c_double),
-                ("dir", ctypes.c_double * 3)]
+                ("dir", ctypes.c_double * 3), ("b", ctypes.c_double),
+                ("shape", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class ed_observables(ctypes.Structure):
@@ -73,6 +78,9 @@ def _load():
         "ed_spectral_propagate": [P, P, I, ctypes.POINTER(ed_pulse), D, I, I,
                                   P, P, P],
         "ed_apply_fermion_op": [P, P, I, I, I, P, P, I, P],
+        "ed_spectral_propagate_at": [P, P, D, I, ctypes.POINTER(ed_pulse), D, I, I,
+                                     P, P, P],
+        "ed_spectral_function": [P, I, I, D, D, P, I, P],
         "ed_device_bytes": [P, ctypes.POINTER(ctypes.c_int64)],
         "ed_apply_config_info": [I] + [ctypes.POINTER(ctypes.c_int)] * 5,
         "ed_set_apply_config": [I],
@@ -191,10 +199,12 @@ def ed_ground_state(ctx, psi, tol=1e-12, max_iter=2000, seed=1):
 
 
 def make_pulse(p):
+    """dict(A0, omega, sigma, t0, dir[, shape "sin" | "cos_phase", b])."""
     if p is None:
         return None
+    shape = {"sin": ED_PULSE_SIN_GAUSS, "cos_phase": ED_PULSE_COS_PHASE}[p.get("shape", "sin")]
     return ed_pulse(p["A0"], p["omega"], p["sigma"], p["t0"],
-                    (ctypes.c_double * 3)(*p["dir"]))
+                    (ctypes.c_double * 3)(*p["dir"]), float(p.get("b", 0.0)), shape, 0)
 
 
 def ed_propagate(ctx, psi, dtype, pulse, t_start, dt, n_steps, m,
@@ -251,6 +261,33 @@ def ed_spectral_propagate(ctx, psi0, dtype, pulse, dt, n_steps, m, Ns,
                                      float(dt), int(n_steps), int(m), ptr(gl),
                                      ptr(gg), stream_ptr(stream)), ctx)
     return gl[..., 0] + 1j * gl[..., 1], gg[..., 0] + 1j * gg[..., 1]
+
+
+def ed_spectral_propagate_at(ctx, psi_ref, t_ref, dtype, pulse, dt, n_steps, m, Ns,
+                             stream=None):
+    """Green's functions at (t_ref, t_ref + n dt); psi_ref = psi(t_ref)."""
+    gl = np.zeros((n_steps + 1, Ns, 2, 2))
+    gg = np.zeros((n_steps + 1, Ns, 2, 2))
+    pl = make_pulse(pulse)
+    _check(lib.ed_spectral_propagate_at(ctx, ptr(psi_ref), float(t_ref), dtype,
+                                        ctypes.byref(pl) if pl is not None else None,
+                                        float(dt), int(n_steps), int(m), ptr(gl),
+                                        ptr(gg), stream_ptr(stream)), ctx)
+    return gl[..., 0] + 1j * gl[..., 1], gg[..., 0] + 1j * gg[..., 1]
+
+
+def ed_spectral_function(G, dt, eps, nu):
+    """(1/pi) Im int_0^T e^{-eps t} e^{i nu t} G(t) dt (trapezoid) for G of
+    shape [n_steps+1, ...] (complex); returns [len(nu), ...]."""
+    G = np.asarray(G, dtype=np.complex128)
+    shp = G.shape[1:]
+    nser = int(np.prod(shp)) if shp else 1
+    g = np.ascontiguousarray(np.stack([G.real, G.imag], axis=-1).reshape(G.shape[0], nser, 2))
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    A = np.zeros((len(nu), nser))
+    _check(lib.ed_spectral_function(ptr(g), G.shape[0] - 1, nser, float(dt), float(eps),
+                                    ptr(nu), len(nu), ptr(A)))
+    return A.reshape((len(nu),) + shp)
 
 
 def ed_apply_fermion_op(ctx, ctx_dst, site, spin, create, psi, out, dtype,

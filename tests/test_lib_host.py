@@ -217,3 +217,18 @@ def test_integrator_argument_checks(ed):
         ed.ed_set_integrator(h.ctx, 7)
     assert e.value.status == 1
     h.close()
+
+
+def test_spectral_function_host_transform_matches_oracle(ed):
+    """ed_spectral_function (host code of the library) against the oracle's
+    broadened transform of Eq. (A_noneq_broad)."""
+    rng = np.random.default_rng(1)
+    G = rng.standard_normal((101, 3, 2)) + 1j * rng.standard_normal((101, 3, 2))
+    nu = np.linspace(-5, 5, 17)
+    A = ed.ed_spectral_function(G, 0.05, 0.1, nu)
+    ref = oracle.broadened_transform(G, 0.05, 0.1, nu)
+    assert A.shape == ref.shape == (17, 3, 2)
+    assert np.abs(A - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+    for bad in ((0.0, 0.1), (0.05, -1.0)):
+        with pytest.raises(ed.EDError):
+            ed.ed_spectral_function(G, bad[0], bad[1], nu)
