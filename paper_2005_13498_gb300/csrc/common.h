@@ -19,7 +19,8 @@ constexpr uint32_t kEntRankMask = 0xFFFFu;
 constexpr int kEntGroupShift = 16;
 constexpr uint32_t kEntSignBit = 0x80000000u;
 constexpr uint32_t kNullEntryBit = 0x40000000u;  // padding entry of a row list
-constexpr uint32_t kEllNull = 0x7FFFFFFFu;       // empty ELL slot of a lane (no load)
+constexpr uint32_t kEllNull = 0x7FFFFFFFu;       // host marker of an unassigned ELL slot
+constexpr int kZeroCols = 8;                     // zero columns past the end of a staged tile
 
 // Device view of one sector's tables (pointers into device memory).
 struct SectorDev {

@@ -37,6 +37,41 @@ template <typename C> __device__ __forceinline__ C czero();
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
 
+// Two independent round-to-nearest FP32 FMAs in one packed instruction
+// (fma.rn.f32x2, sm_100 and later): (a.x b.x + c.x, a.y b.y + c.y), the same
+// values as two scalar FMAs.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ra, rb, rc, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+// s += g v (complex s, v; real g)
+template <typename C, typename R>
+__device__ __forceinline__ void cax(C& s, R g, const C& v) {
+  if constexpr (sizeof(R) == 4) {
+    s = ffma2(make_float2(g, g), v, s);
+  } else {
+    s.x += g * v.x;
+    s.y += g * v.y;
+  }
+}
+// acc += c s (complex)
+template <typename C>
+__device__ __forceinline__ void cmac(C& acc, const C& c, const C& s) {
+  if constexpr (sizeof(C) == 8) {
+    acc = ffma2(make_float2(c.x, c.x), s, acc);
+    acc = ffma2(make_float2(-c.y, c.y), make_float2(s.y, s.x), acc);
+  } else {
+    acc.x += c.x * s.x - c.y * s.y;
+    acc.y += c.x * s.y + c.y * s.x;
+  }
+}
+
 template <typename R> __device__ __forceinline__ typename C2T<R>::T
 load_coef(const void* p, int idx) {
   return reinterpret_cast<const typename C2T<R>::T*>(p)[idx];
@@ -204,11 +239,6 @@ struct TileIO {
   // chunk for 32-byte columns, else rank = offset >> 5
   __device__ static __forceinline__ void load_ent(const C* tile, uint32_t ent, C (&v)[NR]) {
     const uint32_t off = ent & 0x7FFFFFFFu;
-    if (off == kEllNull) {   // empty slot of this lane: no shared-memory access
-#pragma unroll
-      for (int r = 0; r < NR; ++r) v[r] = czero<C>();
-      return;
-    }
     if constexpr (kBytes == 32) {
       const char* base = reinterpret_cast<const char*>(tile);
       const float4 a = *reinterpret_cast<const float4*>(base + off);
@@ -262,7 +292,7 @@ struct TileIO {
 
 // One CTA (256 threads) processes NR consecutive rows u0..u0+NR-1 of one
 // vector.  The rows are staged in shared memory column by column (TileIO),
-// followed by two zero columns that padding entries point to.  Thread t owns
+// followed by eight zero columns that empty ELL slots read.  Thread t owns
 // the column pairs p = pc + t + k*256 (k < PP) of every chunk pc, so a warp
 // covers 64 consecutive columns.
 //  * Diagonal: U * popcount(up & dn) (+ on-site energies).
@@ -299,8 +329,8 @@ k_apply(BatchArgs a, int j) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
-  C* tile = reinterpret_cast<C*>(smem_raw);              // [max_dim_dn + 2][NR]
-  C* coefS = tile + (size_t)(a.max_dim_dn + 2) * NR;    // [n_groups]
+  C* tile = reinterpret_cast<C*>(smem_raw);              // [max_dim_dn + kZeroCols][NR]
+  C* coefS = tile + (size_t)(a.max_dim_dn + kZeroCols) * NR;   // [n_groups]
 
   const void* cbase;
   if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
@@ -316,7 +346,7 @@ k_apply(BatchArgs a, int j) {
   const R U = (R)a.U;
 
   // ---- stage the NR rows column by column (pairs of columns per thread,
-  // all NR row loads of two pairs in flight), plus two zero columns
+  // all NR row loads of two pairs in flight), plus the zero pair past the end
   {
     const int np2 = npairs + 1;   // one extra pair: the zero columns
 #pragma unroll 2
@@ -342,6 +372,13 @@ k_apply(BatchArgs a, int j) {
         TIO::store(tile, d + 1, z);
       }
     }
+  }
+  // zero columns dim_dn .. dim_dn + 7 that empty ELL slots read
+  if (tid < kZeroCols) {
+    C z[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) z[r] = czero<C>();
+    TIO::store(tile, dim_dn + tid, z);
   }
   uint32_t uw[NR];
   R eu[NR];
@@ -423,10 +460,8 @@ k_apply(BatchArgs a, int j) {
               const C c = coefS[gcur];
 #pragma unroll
               for (int r = 0; r < NR; ++r) {
-                acc[r][2 * k].x += c.x * s0v[r].x - c.y * s0v[r].y;
-                acc[r][2 * k].y += c.x * s0v[r].y + c.y * s0v[r].x;
-                acc[r][2 * k + 1].x += c.x * s1v[r].x - c.y * s1v[r].y;
-                acc[r][2 * k + 1].y += c.x * s1v[r].y + c.y * s1v[r].x;
+                cmac(acc[r][2 * k], c, s0v[r]);
+                cmac(acc[r][2 * k + 1], c, s1v[r]);
                 s0v[r] = czero<C>();
                 s1v[r] = czero<C>();
               }
@@ -436,12 +471,8 @@ k_apply(BatchArgs a, int j) {
             const R g0 = sign_of<R>(e.x), g1 = sign_of<R>(e.y);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-              const C v0 = half ? b0[r] : a0[r];
-              const C v1 = half ? b1[r] : a1[r];
-              s0v[r].x += g0 * v0.x;
-              s0v[r].y += g0 * v0.y;
-              s1v[r].x += g1 * v1.x;
-              s1v[r].y += g1 * v1.y;
+              cax(s0v[r], g0, half ? b0[r] : a0[r]);
+              cax(s1v[r], g1, half ? b1[r] : a1[r]);
             }
           }
         }
@@ -449,10 +480,8 @@ k_apply(BatchArgs a, int j) {
           const C c = coefS[gcur];
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
-            acc[r][2 * k].x += c.x * s0v[r].x - c.y * s0v[r].y;
-            acc[r][2 * k].y += c.x * s0v[r].y + c.y * s0v[r].x;
-            acc[r][2 * k + 1].x += c.x * s1v[r].x - c.y * s1v[r].y;
-            acc[r][2 * k + 1].y += c.x * s1v[r].y + c.y * s1v[r].x;
+            cmac(acc[r][2 * k], c, s0v[r]);
+            cmac(acc[r][2 * k + 1], c, s1v[r]);
           }
         }
       }
@@ -538,27 +567,20 @@ k_apply(BatchArgs a, int j) {
               const C c = coefS[gcur];
 #pragma unroll
               for (int k = 0; k < 2 * PP; ++k) {
-                acc[r][k].x += c.x * sum[k].x - c.y * sum[k].y;
-                acc[r][k].y += c.x * sum[k].y + c.y * sum[k].x;
+                cmac(acc[r][k], c, sum[k]);
                 sum[k] = czero<C>();
               }
               gcur = g;
             }
             const R sg = (ents[qq] & kNullEntryBit) ? (R)0 : sign_of<R>(ents[qq]);
 #pragma unroll
-            for (int k = 0; k < 2 * PP; ++k) {
-              sum[k].x += sg * v[qq][k].x;
-              sum[k].y += sg * v[qq][k].y;
-            }
+            for (int k = 0; k < 2 * PP; ++k) cax(sum[k], sg, v[qq][k]);
           }
         }
         if (e0 < e1) {
           const C c = coefS[gcur];
 #pragma unroll
-          for (int k = 0; k < 2 * PP; ++k) {
-            acc[r][k].x += c.x * sum[k].x - c.y * sum[k].y;
-            acc[r][k].y += c.x * sum[k].y + c.y * sum[k].x;
-          }
+          for (int k = 0; k < 2 * PP; ++k) cmac(acc[r][k], c, sum[k]);
         }
       }
     }
@@ -644,8 +666,8 @@ k_apply_up(BatchArgs a, int j) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
-  C* tile = reinterpret_cast<C*>(smem_raw);               // [max_dim_up + 2][NC]
-  C* coefS = tile + (size_t)(a.max_dim_up + 2) * NC;     // [n_groups]
+  C* tile = reinterpret_cast<C*>(smem_raw);               // [max_dim_up + kZeroCols][NC]
+  C* coefS = tile + (size_t)(a.max_dim_up + kZeroCols) * NC;   // [n_groups]
   const void* cbase;
   if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
   else if (j == 0) cbase = a.coefs;
@@ -660,7 +682,7 @@ k_apply_up(BatchArgs a, int j) {
   // 32u + 16 (sw(u) ^ h) of the tile.  Four halves per thread in flight.
   {
     char* tb = reinterpret_cast<char*>(tile);
-    const int nunits = 2 * (dim_up + 2);
+    const int nunits = 2 * (dim_up + kZeroCols);
     for (int i0 = tid; i0 < nunits; i0 += 4 * T) {
       float4 v[4];
 #pragma unroll
@@ -738,10 +760,8 @@ k_apply_up(BatchArgs a, int j) {
               const C cf = coefS[gcur];
 #pragma unroll
               for (int c = 0; c < NC; ++c) {
-                acc[c][2 * k].x += cf.x * s0v[c].x - cf.y * s0v[c].y;
-                acc[c][2 * k].y += cf.x * s0v[c].y + cf.y * s0v[c].x;
-                acc[c][2 * k + 1].x += cf.x * s1v[c].x - cf.y * s1v[c].y;
-                acc[c][2 * k + 1].y += cf.x * s1v[c].y + cf.y * s1v[c].x;
+                cmac(acc[c][2 * k], cf, s0v[c]);
+                cmac(acc[c][2 * k + 1], cf, s1v[c]);
                 s0v[c] = czero<C>();
                 s1v[c] = czero<C>();
               }
@@ -751,12 +771,8 @@ k_apply_up(BatchArgs a, int j) {
             const R g0 = sign_of<R>(e.x), g1 = sign_of<R>(e.y);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-              const C v0 = half ? b0[c] : a0[c];
-              const C v1 = half ? b1[c] : a1[c];
-              s0v[c].x += g0 * v0.x;
-              s0v[c].y += g0 * v0.y;
-              s1v[c].x += g1 * v1.x;
-              s1v[c].y += g1 * v1.y;
+              cax(s0v[c], g0, half ? b0[c] : a0[c]);
+              cax(s1v[c], g1, half ? b1[c] : a1[c]);
             }
           }
         }
@@ -764,10 +780,8 @@ k_apply_up(BatchArgs a, int j) {
           const C cf = coefS[gcur];
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            acc[c][2 * k].x += cf.x * s0v[c].x - cf.y * s0v[c].y;
-            acc[c][2 * k].y += cf.x * s0v[c].y + cf.y * s0v[c].x;
-            acc[c][2 * k + 1].x += cf.x * s1v[c].x - cf.y * s1v[c].y;
-            acc[c][2 * k + 1].y += cf.x * s1v[c].y + cf.y * s1v[c].x;
+            cmac(acc[c][2 * k], cf, s0v[c]);
+            cmac(acc[c][2 * k + 1], cf, s1v[c]);
           }
         }
       }
@@ -1511,8 +1525,8 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     sh.nr = c.nr;
     sh.cfg = i;
     sh.split = c.split;
-    sh.smem = ((size_t)(max_dim_dn + 2) * c.nr + (size_t)n_groups) * csz;
-    sh.smem_c = c.split ? (size_t)(max_dim_up + 2) * 32 + (size_t)n_groups * csz : 0;
+    sh.smem = ((size_t)(max_dim_dn + kZeroCols) * c.nr + (size_t)n_groups) * csz;
+    sh.smem_c = c.split ? (size_t)(max_dim_up + kZeroCols) * 32 + (size_t)n_groups * csz : 0;
     return sh;
   };
   for (int i = 0; i < kNumApplyCfgs; ++i) {

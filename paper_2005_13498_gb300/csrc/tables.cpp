@@ -109,9 +109,13 @@ std::string make_lattice(LatticeHost& L, int Ns, int n_bonds, const int32_t* p,
 // and equal ranks are a broadcast.  Greedy, slot by slot: within each quarter
 // warp the lanes with the longest remaining lists choose first, each taking
 // the entry that adds the fewest conflicts; a lane with slack (fewer entries
-// left than slots) leaves the slot empty rather than add a conflict.  Returns
-// [K][64] entries, kEllNull where a lane has nothing in that slot.
-static std::vector<uint32_t> assign_slots(std::vector<std::vector<uint32_t>> lists, int K) {
+// left than slots) leaves the slot empty rather than add a conflict.  An
+// empty lane reads one of the eight zero columns dim .. dim + 7, the same one
+// for every empty lane of the quarter warp (a broadcast), picked in a bank
+// group the quarter warp's real entries leave free, so empty slots need no
+// test in the kernel.  Returns [K][64] entries (rank | sign << 31).
+static std::vector<uint32_t> assign_slots(std::vector<std::vector<uint32_t>> lists, int K,
+                                          uint32_t dim) {
   std::vector<uint32_t> out((size_t)K * 64, kEllNull);
   for (int k = 0; k < K; ++k) {
     const int slack = K - k;
@@ -143,6 +147,16 @@ static std::vector<uint32_t> assign_slots(std::vector<std::vector<uint32_t>> lis
           used.push_back(L[best] & 0xFFFFu);
           L.erase(L.begin() + best);
         }
+        // the zero column for this quarter warp's empty lanes
+        uint32_t zero = dim;
+        for (uint32_t z = 0; z < 8; ++z) {
+          bool free_bank = true;
+          for (uint32_t r : used)
+            if ((r & 7u) == ((dim + z) & 7u)) free_bank = false;
+          if (free_bank) { zero = dim + z; break; }
+        }
+        for (int i = 0; i < 8; ++i)
+          if (out[(size_t)k * 64 + cols[i]] == kEllNull) out[(size_t)k * 64 + cols[i]] = zero;
       }
     }
   }
@@ -217,19 +231,19 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
         K = std::max(K, (int)lists[l].size());
       }
       if (K == 0) continue;
-      std::vector<uint32_t> slots = assign_slots(lists, K);
+      std::vector<uint32_t> slots = assign_slots(lists, K, (uint32_t)T.dim);
       for (int k = 0; k < K; ++k) {
         T.slot_grp.push_back((uint32_t)g);
         for (int l = 0; l < 64; ++l) {   // l = 2 * lane + h
           const uint32_t e = slots[(size_t)k * 64 + l];
-          T.ell.push_back(e == kEllNull ? kEllNull : (tile_offset(e & 0xFFFFu) | (e & 0x80000000u)));
+          T.ell.push_back(tile_offset(e & 0xFFFFu) | (e & 0x80000000u));
         }
         ++tile_slots;
       }
     }
-    if (tile_slots % 2) {   // padding slot: no lane loads anything
+    if (tile_slots % 2) {   // padding slot: every lane reads zero column dim
       T.slot_grp.push_back(T.slot_grp.empty() ? 0u : T.slot_grp.back());
-      for (int l = 0; l < 64; ++l) T.ell.push_back(kEllNull);
+      for (int l = 0; l < 64; ++l) T.ell.push_back(tile_offset((uint32_t)T.dim));
       ++tile_slots;
     }
     nslots += tile_slots;

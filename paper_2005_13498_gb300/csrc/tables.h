@@ -73,7 +73,8 @@ struct SpinTable {
   // is chosen so that the eight lanes of each quarter warp read sources of
   // distinct rank mod 8 where possible (distinct 16-byte shared-memory bank
   // groups for 16- and 32-byte tile columns, see assign_slots).  A slot a
-  // column does not use holds kEllNull (the lane loads nothing).
+  // column does not use points to one of the zero columns dim .. dim + 7 of
+  // the tile, chosen in a bank group that slot's quarter warp leaves free.
   std::vector<int32_t> tslot_off;
   std::vector<uint32_t> slot_grp;
   std::vector<uint32_t> ell;
