@@ -1153,47 +1153,80 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
                      (eb.end & 1) == 0 && (((uintptr_t)x1 | (uintptr_t)V) & 15u) == 0 &&
                      (vd.D & 1) == 0;
   if (pairs) {
-    // two elements (one row, since dim_dn is even) per 16-byte access; the
-    // coefficient loop keeps eight vector loads in flight
+    // two elements (one row, since dim_dn is even) per 16-byte access.  The
+    // block sweeps sub-chunks of 4 x 256 pairs (16 KB of every vector) one
+    // Krylov vector at a time, so each vector is read in contiguous 16 KB
+    // pieces; four pairs per thread accumulate in registers, two vectors'
+    // loads (eight 16-byte loads) in flight.
+    constexpr int Q = 4;
     float4* x4 = reinterpret_cast<float4*>(x1);
     const float4* V4 = reinterpret_cast<const float4*>(V);
     const int64_t D2 = vd.D >> 1;
-    for (int64_t i = (eb.begin >> 1) + threadIdx.x; i < (eb.end >> 1); i += blockDim.x) {
-      float4 xv = x4[i];
-      float4 p;
+    const int64_t b2 = eb.begin >> 1, e2 = eb.end >> 1;
+    const int bd = blockDim.x;
+    for (int64_t base = b2; base < e2; base += (int64_t)Q * bd) {
+      int64_t idx[Q];
+      bool ok[Q];
+      float4 xv[Q], p[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        idx[q] = base + threadIdx.x + (int64_t)q * bd;
+        ok[q] = idx[q] < e2;
+        xv[q] = ok[q] ? x4[idx[q]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       if (COMBINE) {
         const float2 lo = *reinterpret_cast<const float2*>(&cf_lo);
-        p.x = lo.x * xv.x - lo.y * xv.y;
-        p.y = lo.x * xv.y + lo.y * xv.x;
-        p.z = lo.x * xv.z - lo.y * xv.w;
-        p.w = lo.x * xv.w + lo.y * xv.z;
-#pragma unroll 8
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          p[q].x = lo.x * xv[q].x - lo.y * xv[q].y;
+          p[q].y = lo.x * xv[q].y + lo.y * xv[q].x;
+          p[q].z = lo.x * xv[q].z - lo.y * xv[q].w;
+          p[q].w = lo.x * xv[q].w + lo.y * xv[q].z;
+        }
+#pragma unroll 2
         for (int jj = 1; jj < n; ++jj) {
-          const float4 v = V4[(size_t)(jj - 1) * D2 + i];
+          const float4* Vj = V4 + (size_t)(jj - 1) * D2;
           const float2 c = *reinterpret_cast<const float2*>(&cf[jj]);
-          p.x += c.x * v.x - c.y * v.y;
-          p.y += c.x * v.y + c.y * v.x;
-          p.z += c.x * v.z - c.y * v.w;
-          p.w += c.x * v.w + c.y * v.z;
+          float4 v[Q];
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+            v[q] = ok[q] ? __ldcs(Vj + idx[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            p[q].x += c.x * v[q].x - c.y * v[q].y;
+            p[q].y += c.x * v[q].y + c.y * v[q].x;
+            p[q].z += c.x * v[q].z - c.y * v[q].w;
+            p[q].w += c.x * v[q].w + c.y * v[q].z;
+          }
         }
         const float2 c0 = *reinterpret_cast<const float2*>(&cf[0]);
-        p.x += c0.x * xv.x - c0.y * xv.y;
-        p.y += c0.x * xv.y + c0.y * xv.x;
-        p.z += c0.x * xv.z - c0.y * xv.w;
-        p.w += c0.x * xv.w + c0.y * xv.z;
-        x4[i] = p;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          p[q].x += c0.x * xv[q].x - c0.y * xv[q].y;
+          p[q].y += c0.x * xv[q].y + c0.y * xv[q].x;
+          p[q].z += c0.x * xv[q].z - c0.y * xv[q].w;
+          p[q].w += c0.x * xv[q].w + c0.y * xv[q].z;
+          if (ok[q]) x4[idx[q]] = p[q];
+        }
       } else {
-        p = xv;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) p[q] = xv[q];
       }
-      const int64_t e = 2 * i;
-      const int u = (int)(e / dim_dn);
-      const int d = (int)(e - (int64_t)u * dim_dn);
-      const uint32_t uwd = __ldg(sd.up_word + u);
-      const R q0 = p.x * p.x + p.y * p.y, q1 = p.z * p.z + p.w * p.w;
-      nl += q0 + q1;
-      wl += (R)__popc(uwd & __ldg(sd.dn_word + d)) * q0 +
-            (R)__popc(uwd & __ldg(sd.dn_word + d + 1)) * q1;
-      if (++cnt == 4) { nd += (double)nl; wd += (double)wl; nl = wl = (R)0; cnt = 0; }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (!ok[q]) continue;
+        const int64_t e = 2 * idx[q];
+        const int u = (int)(e / dim_dn);
+        const int d = (int)(e - (int64_t)u * dim_dn);
+        const uint32_t uwd = __ldg(sd.up_word + u);
+        const R q0 = p[q].x * p[q].x + p[q].y * p[q].y, q1 = p[q].z * p[q].z + p[q].w * p[q].w;
+        nl += q0 + q1;
+        wl += (R)__popc(uwd & __ldg(sd.dn_word + d)) * q0 +
+              (R)__popc(uwd & __ldg(sd.dn_word + d + 1)) * q1;
+      }
+      nd += (double)nl;
+      wd += (double)wl;
+      nl = wl = (R)0;
     }
   } else {
     for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
