@@ -77,7 +77,7 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
     cmap->clear();
     for (size_t i = 0; i < t.dim_up.size(); ++i) {
       append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr);
-      if (sh.split) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64);
+      if (sh.split) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64, sh.cb);
     }
   };
   const int forced = forced_apply_config();

@@ -646,13 +646,14 @@ k_apply(BatchArgs a, int j) {
 // Reading and writing 32-byte row segments keeps the whole pass at one read
 // of x and one write of w; the row pass (k_apply with SPLIT) adds the
 // diagonal and T_dn and finishes the Lanczos epilogue.
-template <typename R, int PP, bool VEC, int MINB>
-__global__ void __launch_bounds__(kApplyThreads, MINB)
+template <typename R, int PP, bool VEC, int MINB, int CB, int TC>
+__global__ void __launch_bounds__(TC, MINB)
 k_apply_up(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
-  constexpr int NC = 32 / (int)sizeof(C);
+  constexpr int NC = CB / (int)sizeof(C);    // columns per block (CB = 32 or 16 bytes)
+  constexpr int UPR = CB / 16;               // 16-byte units per row segment
   using TIO = TileIO<C, NC>;
-  constexpr int T = kApplyThreads;
+  constexpr int T = TC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
   const ApplyBlock cb = a.col_map[blockIdx.x];
@@ -677,21 +678,22 @@ k_apply_up(BatchArgs a, int j) {
   const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
   C* w = static_cast<C*>(vd.w);
 
-  // ---- stage: 16-byte halves h of the 32-byte segment of each row u; half
-  // h holds columns h*NC/2 .. h*NC/2 + NC/2 - 1, stored at byte
-  // 32u + 16 (sw(u) ^ h) of the tile.  Four halves per thread in flight.
+  // ---- stage: the 16-byte units h of the CB-byte segment of each row u;
+  // unit h holds columns h*NC/UPR .. (h+1)*NC/UPR - 1, stored at byte
+  // 32u + 16 (sw(u) ^ h) of the tile for 32-byte segments, at 16u for 16-byte
+  // ones.  Four units per thread in flight.
   {
     char* tb = reinterpret_cast<char*>(tile);
-    const int nunits = 2 * (dim_up + kZeroCols);
+    const int nunits = UPR * (dim_up + kZeroCols);
     for (int i0 = tid; i0 < nunits; i0 += 4 * T) {
       float4 v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = i0 + q * T;
-        const int u = i >> 1, h = i & 1;
+        const int u = i / UPR, h = i % UPR;
         v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < nunits && u < dim_up) {
-          const C* src = x + (size_t)u * dim_dn + d0 + h * (NC / 2);
+          const C* src = x + (size_t)u * dim_dn + d0 + h * (NC / UPR);
           if constexpr (sizeof(C) == 16) {
             if (h < ncols) v[q] = __ldg(reinterpret_cast<const float4*>(src));
           } else if constexpr (VEC) {
@@ -706,8 +708,9 @@ k_apply_up(BatchArgs a, int j) {
       for (int q = 0; q < 4; ++q) {
         const int i = i0 + q * T;
         if (i < nunits) {
-          const int u = i >> 1, h = i & 1;
-          *reinterpret_cast<float4*>(tb + 32 * (size_t)u + 16 * (((u >> 2) & 1) ^ h)) = v[q];
+          const int u = i / UPR, h = i % UPR;
+          const size_t off = UPR == 2 ? 32 * (size_t)u + 16 * (((u >> 2) & 1) ^ h) : 16 * (size_t)u;
+          *reinterpret_cast<float4*>(tb + off) = v[q];
         }
       }
     }
@@ -800,7 +803,7 @@ k_apply_up(BatchArgs a, int j) {
               if (c < ncols) dst[c] = acc[c][2 * k + hh];
           } else if constexpr (VEC) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < NC / 2; ++h)
               if (2 * h < ncols)
                 reinterpret_cast<float4*>(dst)[h] =
                     make_float4(acc[2 * h][2 * k + hh].x, acc[2 * h][2 * k + hh].y,
@@ -989,16 +992,20 @@ __device__ void tridiag_expm_e1(const double* al, const double* be, int n,
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(32) k_expm(BatchArgs a) {
+// Two warps per vector: warp 0 computes y = exp(-i tau T_n) e_1, warp 1 the
+// one-smaller y^(n-1) that the a-posteriori delta compares with, at the same
+// time (each a chain of float64 warp operations).
+__global__ void __launch_bounds__(64) k_expm(BatchArgs a) {
   __shared__ double al[64], be[64], yre[64], yim[64], pre[64], pim[64];
-  __shared__ double tre[64], tim[64];
+  __shared__ double tre[2][64], tim[2][64];
   const int b = blockIdx.x;
   LanczosState* st = a.st + b;
   const VecDev vd = a.vec[b];
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int conv = st->conv_m;
   if (conv > 0 && conv < st->m_eff) {
     // adaptive exit at step conv: its check left y^(conv) and delta
+    if (warp != 0) return;
     const int n = conv;
     for (int i = lane; i < n; i += 32) {
       const double f = st->beta0 * st->inv_scale[i + 1];
@@ -1015,15 +1022,17 @@ __global__ void __launch_bounds__(32) k_expm(BatchArgs a) {
     return;
   }
   const int n = st->m_eff;
-  for (int i = lane; i < 64; i += 32) {
+  for (int i = threadIdx.x; i < 64; i += 64) {
     al[i] = i < n ? st->alpha[i + 1] : 0.0;
     be[i] = i < n - 1 ? st->beta[i + 1] : 0.0;
   }
-  __syncwarp();
-  tridiag_expm_e1(al, be, n, a.tau, yre, yim, tre, tim);
+  __syncthreads();
+  if (warp == 0) tridiag_expm_e1(al, be, n, a.tau, yre, yim, tre[0], tim[0]);
+  else if (n > 1) tridiag_expm_e1(al, be, n - 1, a.tau, pre, pim, tre[1], tim[1]);
+  __syncthreads();
+  if (warp != 0) return;
   double delta = 0.0;
   if (n > 1) {
-    tridiag_expm_e1(al, be, n - 1, a.tau, pre, pim, tre, tim);
     double dn = 0.0, yn = 0.0;
     for (int i = lane; i < n; i += 32) {
       const double pr = i < n - 1 ? pre[i] : 0.0, pi = i < n - 1 ? pim[i] : 0.0;
@@ -1522,15 +1531,18 @@ static int grid_for(int64_t n, int threads) {
 // register budget) of the row kernel; for the split apply also the pairs per
 // thread and occupancy of the column pass.  The autotuner times the feasible
 // ones.
-struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc; };
+struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc, cb, tc; };
 static const ApplyCfg kApplyCfgs[] = {
-    {false, 4, 2, 2, false, 0, 0}, {false, 2, 2, 3, false, 0, 0},
-    {false, 2, 1, 4, false, 0, 0}, {false, 1, 2, 2, false, 0, 0},
-    {true, 2, 1, 2, false, 0, 0},  {true, 1, 1, 4, false, 0, 0},
-    {true, 1, 1, 2, false, 0, 0},
-    {false, 4, 2, 2, true, 1, 2},  {false, 2, 2, 3, true, 1, 2},
-    {false, 2, 1, 4, true, 1, 2},  {false, 4, 2, 2, true, 2, 2},
-    {true, 2, 1, 2, true, 1, 2},   {true, 1, 1, 4, true, 1, 2},
+    {false, 4, 2, 2, false, 0, 0, 0, 0}, {false, 2, 2, 3, false, 0, 0, 0, 0},
+    {false, 2, 1, 4, false, 0, 0, 0, 0}, {false, 1, 2, 2, false, 0, 0, 0, 0},
+    {true, 2, 1, 2, false, 0, 0, 0, 0},  {true, 1, 1, 4, false, 0, 0, 0, 0},
+    {true, 1, 1, 2, false, 0, 0, 0, 0},
+    {false, 4, 2, 2, true, 1, 2, 32, 256}, {false, 2, 2, 3, true, 1, 2, 32, 256},
+    {false, 2, 1, 4, true, 1, 2, 32, 256}, {false, 4, 2, 2, true, 2, 2, 32, 256},
+    {true, 2, 1, 2, true, 1, 2, 32, 256},  {true, 1, 1, 4, true, 1, 2, 32, 256},
+    // long columns (vectors beyond L2): 16-byte column blocks, one 512-thread
+    // column CTA per SM
+    {false, 1, 2, 2, true, 1, 1, 16, 512}, {true, 1, 1, 1, true, 1, 1, 16, 512},
 };
 static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
 
@@ -1558,8 +1570,10 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     sh.nr = c.nr;
     sh.cfg = i;
     sh.split = c.split;
+    sh.cb = c.cb;
+    sh.tc = c.tc;
     sh.smem = ((size_t)(max_dim_dn + kZeroCols) * c.nr + (size_t)n_groups) * csz;
-    sh.smem_c = c.split ? (size_t)(max_dim_up + kZeroCols) * 32 + (size_t)n_groups * csz : 0;
+    sh.smem_c = c.split ? (size_t)(max_dim_up + kZeroCols) * c.cb + (size_t)n_groups * csz : 0;
     return sh;
   };
   for (int i = 0; i < kNumApplyCfgs; ++i) {
@@ -1571,7 +1585,9 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     if (c.split && (sh.smem_c * (size_t)c.minbc > 228 * 1024 || sh.smem_c > 227 * 1024)) continue;
     out.push_back(sh);
   }
-  if (out.empty()) {   // very long rows: one row per CTA, one CTA per SM;
+  bool have_fused = false;
+  for (const LaunchShape& sh : out) have_fused |= !sh.split;
+  if (!have_fused) {   // very long rows: one row per CTA, one CTA per SM;
     // of those entries the one with the fewest target CTAs per SM (the
     // largest register budget)
     int best = -1;
@@ -1598,13 +1614,13 @@ LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups)
   return c.front();
 }
 
-template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC>
+template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
   constexpr bool V = sizeof(R) == 4;
   if constexpr (SPLIT) {
-    if (sh.vec) k_apply_up<R, PPC, V, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
-    else k_apply_up<R, PPC, false, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
+    if (sh.vec) k_apply_up<R, PPC, V, MINBC, CB, TC><<<a.n_col_blocks, TC, sh.smem_c, s>>>(a, j);
+    else k_apply_up<R, PPC, false, MINBC, CB, TC><<<a.n_col_blocks, TC, sh.smem_c, s>>>(a, j);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1613,7 +1629,7 @@ static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShap
   return cudaGetLastError();
 }
 
-template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC>
+template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC>
 static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   constexpr bool V = sizeof(R) == 4;
   const int sm = (int)sh.smem;
@@ -1625,36 +1641,38 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   if (e != cudaSuccess) return e;
   if constexpr (SPLIT) {
     const int smc = (int)sh.smem_c;
-    e = cudaFuncSetAttribute(k_apply_up<R, PPC, false, MINBC>,
+    e = cudaFuncSetAttribute(k_apply_up<R, PPC, false, MINBC, CB, TC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_apply_up<R, PPC, V, MINBC>,
+    e = cudaFuncSetAttribute(k_apply_up<R, PPC, V, MINBC, CB, TC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
   }
   return e;
 }
 
 // One switch over the configuration table for both prepare and launch.
-#define ED_APPLY_CONFIGS(X)                    \
-  X(0, float, 4, 2, 2, false, 1, 1)            \
-  X(1, float, 2, 2, 3, false, 1, 1)            \
-  X(2, float, 2, 1, 4, false, 1, 1)            \
-  X(3, float, 1, 2, 2, false, 1, 1)            \
-  X(4, double, 2, 1, 2, false, 1, 1)           \
-  X(5, double, 1, 1, 4, false, 1, 1)           \
-  X(6, double, 1, 1, 2, false, 1, 1)           \
-  X(7, float, 4, 2, 2, true, 1, 2)             \
-  X(8, float, 2, 2, 3, true, 1, 2)             \
-  X(9, float, 2, 1, 4, true, 1, 2)             \
-  X(10, float, 4, 2, 2, true, 2, 2)            \
-  X(11, double, 2, 1, 2, true, 1, 2)           \
-  X(12, double, 1, 1, 4, true, 1, 2)
+#define ED_APPLY_CONFIGS(X)                          \
+  X(0, float, 4, 2, 2, false, 1, 1, 32, 256)         \
+  X(1, float, 2, 2, 3, false, 1, 1, 32, 256)         \
+  X(2, float, 2, 1, 4, false, 1, 1, 32, 256)         \
+  X(3, float, 1, 2, 2, false, 1, 1, 32, 256)         \
+  X(4, double, 2, 1, 2, false, 1, 1, 32, 256)        \
+  X(5, double, 1, 1, 4, false, 1, 1, 32, 256)        \
+  X(6, double, 1, 1, 2, false, 1, 1, 32, 256)        \
+  X(7, float, 4, 2, 2, true, 1, 2, 32, 256)          \
+  X(8, float, 2, 2, 3, true, 1, 2, 32, 256)          \
+  X(9, float, 2, 1, 4, true, 1, 2, 32, 256)          \
+  X(10, float, 4, 2, 2, true, 2, 2, 32, 256)         \
+  X(11, double, 2, 1, 2, true, 1, 2, 32, 256)        \
+  X(12, double, 1, 1, 4, true, 1, 2, 32, 256)        \
+  X(13, float, 1, 2, 2, true, 1, 1, 16, 512)         \
+  X(14, double, 1, 1, 1, true, 1, 1, 16, 512)
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
   (void)fp64;
   if (sh.nr < 1 || sh.smem > 227 * 1024 || sh.smem_c > 227 * 1024) return cudaErrorInvalidValue;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC) \
-  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC>(sh);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC) \
+  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC>(sh);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;
@@ -1665,8 +1683,8 @@ cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
                          int j, cudaStream_t s) {
   (void)fp64;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC) \
-  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC>(a, nblk, sh, j, s);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC) \
+  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC>(a, nblk, sh, j, s);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;
@@ -1686,7 +1704,7 @@ cudaError_t launch_conv_check(const BatchArgs& a, int j, cudaStream_t s) {
 }
 
 cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s) {
-  k_expm<<<a.nvec, 32, 0, s>>>(a);
+  k_expm<<<a.nvec, 64, 0, s>>>(a);
   return cudaGetLastError();
 }
 

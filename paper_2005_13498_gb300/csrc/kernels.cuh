@@ -19,6 +19,8 @@ struct LaunchShape {
   int cfg = 0;       // index of the kernel configuration (rows, pairs, occupancy)
   bool split = false;  // column pass (T_up) + row pass instead of one kernel
   size_t smem_c = 0;   // dynamic shared memory of the column pass
+  int cb = 32;         // column-pass block: bytes of columns per row (32 or 16)
+  int tc = 256;        // column-pass threads per CTA
 };
 
 // Feasible apply configurations for sectors of at most max_dim_up rows of
@@ -27,10 +29,11 @@ struct LaunchShape {
 std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool fp64,
                                           int n_groups);
 
-// Column blocks of the split apply: 32 bytes of columns (4 complex64 or 2
-// complex128) covering columns [0, dim_dn) of vector vec.
-inline void append_col_blocks(std::vector<ApplyBlock>& map, int vec, int dim_dn, bool fp64) {
-  const int nc = fp64 ? 2 : 4;
+// Column blocks of the split apply: cb bytes of columns (cb / element size
+// columns) covering columns [0, dim_dn) of vector vec.
+inline void append_col_blocks(std::vector<ApplyBlock>& map, int vec, int dim_dn, bool fp64,
+                              int cb) {
+  const int nc = cb / (fp64 ? 16 : 8);
   for (int d = 0; d < dim_dn; d += nc)
     map.push_back({vec, d, dim_dn - d < nc ? dim_dn - d : nc, 0});
 }
