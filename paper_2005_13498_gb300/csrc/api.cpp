@@ -58,6 +58,19 @@ cudaError_t upload_sector(SectorGPU& S) {
   if ((e = upload(S.up_tslot_off, S.up.tslot_off)) != cudaSuccess) return e;
   if ((e = upload(S.up_slot_grp, S.up.slot_grp)) != cudaSuccess) return e;
   if ((e = upload(S.up_ell, S.up.ell)) != cudaSuccess) return e;
+  {
+    // per-width copies: the byte offset of the source column (rank) in tiles
+    // of 16- and 8-byte columns, recovered from tile_offset = 32 rank + 16 sw
+    auto width_copy = [](const std::vector<uint32_t>& ell, uint32_t width) {
+      std::vector<uint32_t> out(ell.size());
+      for (size_t i = 0; i < ell.size(); ++i)
+        out[i] = (((ell[i] & 0x7FFFFFFFu) >> 5) * width) | (ell[i] & 0x80000000u);
+      return out;
+    };
+    if ((e = upload(S.dn_ell16, width_copy(S.dn.ell, 16))) != cudaSuccess) return e;
+    if ((e = upload(S.dn_ell8, width_copy(S.dn.ell, 8))) != cudaSuccess) return e;
+    if ((e = upload(S.up_ell16, width_copy(S.up.ell, 16))) != cudaSuccess) return e;
+  }
   if (S.has_eps) {
     if ((e = upload(S.up_eps, S.up.eps_sum)) != cudaSuccess) return e;
     if ((e = upload(S.dn_eps, S.dn.eps_sum)) != cudaSuccess) return e;
@@ -87,6 +100,9 @@ cudaError_t upload_sector(SectorGPU& S) {
   d.up_tslot_off = static_cast<const int32_t*>(S.up_tslot_off.p);
   d.up_slot_grp = static_cast<const uint32_t*>(S.up_slot_grp.p);
   d.up_ell = static_cast<const uint32_t*>(S.up_ell.p);
+  d.dn_ell16 = static_cast<const uint32_t*>(S.dn_ell16.p);
+  d.dn_ell8 = static_cast<const uint32_t*>(S.dn_ell8.p);
+  d.up_ell16 = static_cast<const uint32_t*>(S.up_ell16.p);
   S.uploaded = true;
   return cudaSuccess;
 }
@@ -287,7 +303,7 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
               S.up_word.bytes + S.dn_word.bytes + S.up_eps.bytes + S.dn_eps.bytes +
               S.up_pad_off.bytes + S.up_pad_ent.bytes + S.up_pad_row.bytes + S.dn_tslot_off.bytes +
               S.dn_slot_grp.bytes + S.dn_ell.bytes + S.up_tslot_off.bytes + S.up_slot_grp.bytes +
-              S.up_ell.bytes;
+              S.up_ell.bytes + S.dn_ell16.bytes + S.dn_ell8.bytes + S.up_ell16.bytes;
   if (ctx->engine) b += ctx->engine->device_bytes();
   if (ctx->spec_engine) b += ctx->spec_engine->device_bytes();
   *bytes = b;

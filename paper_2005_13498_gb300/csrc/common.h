@@ -46,6 +46,11 @@ struct SectorDev {
   const int32_t* up_tslot_off;
   const uint32_t* up_slot_grp;
   const uint32_t* up_ell;
+  // the same ELL entries with the byte offset of the source column in tiles
+  // of 16-byte and 8-byte columns (16 rank, 8 rank) instead of tile_offset
+  const uint32_t* dn_ell16;
+  const uint32_t* dn_ell8;
+  const uint32_t* up_ell16;
 };
 
 // Per-vector Lanczos scalars, all float64, 1-based Krylov index j.

@@ -235,8 +235,9 @@ struct TileIO {
       for (int r = 0; r < NR; ++r) v[r] = tile[(size_t)d * NR + r];
     }
   }
-  // load by a table entry: the precomputed byte offset of the column's first
-  // chunk for 32-byte columns, else rank = offset >> 5
+  // load by a table entry: the byte offset of the column (of its first
+  // chunk, tile_offset, for 32-byte columns) from the ELL copy of this
+  // column width (ell_for)
   __device__ static __forceinline__ void load_ent(const C* tile, uint32_t ent, C (&v)[NR]) {
     const uint32_t off = ent & 0x7FFFFFFFu;
     if constexpr (kBytes == 32) {
@@ -253,16 +254,26 @@ struct TileIO {
         v[1].y = __longlong_as_double(((long long)__float_as_int(b.w) << 32) | (unsigned)__float_as_int(b.z));
       }
     } else if constexpr (kBytes == 16) {
-      const float4 a = reinterpret_cast<const float4*>(tile)[off >> 5];
+      const float4 a = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(tile) + off);
       if constexpr (sizeof(C) == 8) {
         v[0].x = a.x; v[0].y = a.y; v[1].x = a.z; v[1].y = a.w;
       } else {
         v[0].x = __longlong_as_double(((long long)__float_as_int(a.y) << 32) | (unsigned)__float_as_int(a.x));
         v[0].y = __longlong_as_double(((long long)__float_as_int(a.w) << 32) | (unsigned)__float_as_int(a.z));
       }
+    } else if constexpr (kBytes == 8) {
+      v[0] = *reinterpret_cast<const C*>(reinterpret_cast<const char*>(tile) + off);
     } else {
       load(tile, (int)(off >> 5), v);
     }
+  }
+  // the ELL copy whose entries hold byte offsets for this column width
+  __device__ static __forceinline__ const uint32_t* ell_for(const uint32_t* ell32,
+                                                            const uint32_t* ell16,
+                                                            const uint32_t* ell8) {
+    if constexpr (kBytes == 16) return ell16;
+    else if constexpr (kBytes == 8) return ell8;
+    else return ell32;
   }
   __device__ static __forceinline__ void store(C* tile, int d, const C (&v)[NR]) {
     if constexpr (kBytes == 32) {
@@ -425,7 +436,8 @@ k_apply(BatchArgs a, int j) {
       if (pw0 < npairs) {                             // uniform over the warp
         const int tw = pw0 >> 5;
         const int q0 = __ldg(sd.dn_tslot_off + tw), q1 = __ldg(sd.dn_tslot_off + tw + 1);
-        const uint2* ell2 = reinterpret_cast<const uint2*>(sd.dn_ell);
+        const uint2* ell2 =
+            reinterpret_cast<const uint2*>(TIO::ell_for(sd.dn_ell, sd.dn_ell16, sd.dn_ell8));
         C s0v[NR], s1v[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) { s0v[r] = czero<C>(); s1v[r] = czero<C>(); }
@@ -652,6 +664,7 @@ k_apply_up(BatchArgs a, int j) {
   using C = typename C2T<R>::T;
   constexpr int NC = CB / (int)sizeof(C);    // columns per block (CB = 32 or 16 bytes)
   constexpr int UPR = CB / 16;               // 16-byte units per row segment
+  static_assert(CB == 16 || CB == 32, "column blocks of 16 or 32 bytes");
   using TIO = TileIO<C, NC>;
   constexpr int T = TC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -729,7 +742,8 @@ k_apply_up(BatchArgs a, int j) {
       if (pw0 < npairs) {                             // uniform over the warp
         const int tw = pw0 >> 5;
         const int q0 = __ldg(sd.up_tslot_off + tw), q1 = __ldg(sd.up_tslot_off + tw + 1);
-        const uint2* ell2 = reinterpret_cast<const uint2*>(sd.up_ell);
+        const uint2* ell2 =
+            reinterpret_cast<const uint2*>(TIO::ell_for(sd.up_ell, sd.up_ell16, sd.up_ell16));
         C s0v[NC], s1v[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) { s0v[c] = czero<C>(); s1v[c] = czero<C>(); }
