@@ -307,14 +307,17 @@ ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme);
  * thread block owns (rows_per_cta), the column pairs per thread, the target
  * thread blocks per SM, and whether the product runs as one kernel (split =
  * 0: the T_up rows are gathered across the matrix) or as a column pass for
- * T_up followed by a row pass for the diagonal and T_dn (split = 1).
+ * T_up followed by a row pass for the diagonal and T_dn (split = 1), and
+ * whether an extra producer warp stages the T_up source-row chunks in shared
+ * memory with TMA bulk copies (tma = 1; used only for even dim_dn and
+ * 16-byte aligned vectors).
  * ed_apply_config_count returns the number of entries; ed_apply_config_info
  * describes entry `config` (ED_ERR_ARG if out of range; any output pointer
  * may be NULL).                                                              */
 int ed_apply_config_count(void);
 ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
                                int* pairs_per_thread, int* ctas_per_sm,
-                               int* split);
+                               int* split, int* tma);
 
 /* Process-wide choice of the H v configuration for every propagation,
  * ed_apply_H plan and ground-state solve set up after the call (contexts

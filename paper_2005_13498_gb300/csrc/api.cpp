@@ -329,15 +329,16 @@ ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme) {
 int ed_apply_config_count(void) { return apply_config_count(); }
 
 ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
-                               int* pairs_per_thread, int* ctas_per_sm, int* split) {
-  int f, nr, pp, mb, sp;
-  if (!apply_config_info(config, &f, &nr, &pp, &mb, &sp))
+                               int* pairs_per_thread, int* ctas_per_sm, int* split, int* tma) {
+  int f, nr, pp, mb, sp, tm;
+  if (!apply_config_info(config, &f, &nr, &pp, &mb, &sp, &tm))
     return fail(nullptr, ED_ERR_ARG, "no apply configuration " + std::to_string(config));
   if (fp64) *fp64 = f;
   if (rows_per_cta) *rows_per_cta = nr;
   if (pairs_per_thread) *pairs_per_thread = pp;
   if (ctas_per_sm) *ctas_per_sm = mb;
   if (split) *split = sp;
+  if (tma) *tma = tm;
   return ED_OK;
 }
 
@@ -415,6 +416,7 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     tt.fp64 = fp64;
     tt.vec_ok = !fp64 && (ctx->dim_dn % 2 == 0) &&
                 ((((uintptr_t)v) | ((uintptr_t)w)) & 15u) == 0;
+    tt.tma_ok = (ctx->dim_dn % 2 == 0) && ((((uintptr_t)v) | ((uintptr_t)w)) & 15u) == 0;
     tt.max_dim_up = (int)ctx->dim_up;
     tt.max_dim_dn = (int)ctx->dim_dn;
     tt.n_groups = ng;

@@ -132,6 +132,7 @@ std::string gs_apply_setup(GsApply& G, ed_ctx* ctx, const double2* x, double2* w
   ApplyTuneTarget tt;
   tt.fp64 = true;
   tt.vec_ok = false;
+  tt.tma_ok = (ctx->dim_dn % 2 == 0) && ((((uintptr_t)x) | ((uintptr_t)w)) & 15u) == 0;
   tt.max_dim_up = (int)ctx->dim_up;
   tt.max_dim_dn = (int)ctx->dim_dn;
   tt.n_groups = ng;

@@ -70,6 +70,10 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
   static std::map<std::string, int> cache;
   std::vector<LaunchShape> cands =
       apply_candidates(t.max_dim_up, t.max_dim_dn, t.fp64, t.n_groups);
+  if (!t.tma_ok)
+    cands.erase(std::remove_if(cands.begin(), cands.end(),
+                               [](const LaunchShape& c) { return c.tma; }),
+                cands.end());
   if (cands.empty()) return "apply kernel: rows too long for shared memory";
   for (auto& c : cands) c.vec = t.vec_ok;
   auto build = [&](const LaunchShape& sh) {
@@ -246,12 +250,14 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     v.out_meff = reinterpret_cast<int*>(base + 4 * (ncap + 1));
   }
   n_ew_ = (int)emap.size();
-  // 16-byte pair accesses for complex64 when every row and buffer allows it
-  bool vec_ok = !cfg.fp64;
+  // 16-byte pair accesses for complex64 when every row and buffer allows it;
+  // the same conditions allow TMA row chunks in either precision
+  bool tma_ok = true;
   for (int i = 0; i < nv; ++i) {
-    if (sectors_[vecs_[i].sector].dim_dn & 1) vec_ok = false;
-    if (((uintptr_t)vd[i].x1 | (uintptr_t)vd[i].V | (uintptr_t)vd[i].w) & 15u) vec_ok = false;
+    if (sectors_[vecs_[i].sector].dim_dn & 1) tma_ok = false;
+    if (((uintptr_t)vd[i].x1 | (uintptr_t)vd[i].V | (uintptr_t)vd[i].w) & 15u) tma_ok = false;
   }
+  const bool vec_ok = !cfg.fp64 && tma_ok;
 
   ED_TRY(d_sec_.alloc(sizeof(SectorDev) * sectors_.size()));
   ED_TRY(d_vec_.alloc(sizeof(VecDev) * nv));
@@ -292,6 +298,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   ApplyTuneTarget tt;
   tt.fp64 = cfg.fp64;
   tt.vec_ok = vec_ok;
+  tt.tma_ok = tma_ok;
   tt.max_dim_up = max_dim_up;
   tt.max_dim_dn = max_dim_dn;
   tt.n_groups = n_groups;

@@ -51,6 +51,7 @@ struct EngineConfig {
 struct ApplyTuneTarget {
   bool fp64 = false;
   bool vec_ok = false;          // complex64 rows may be read as 16-byte pairs
+  bool tma_ok = false;          // even rows, 16-byte aligned bases (TMA row chunks)
   int max_dim_up = 1;
   int max_dim_dn = 1;
   int n_groups = 0;

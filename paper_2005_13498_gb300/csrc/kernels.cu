@@ -169,6 +169,63 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 //    block; each entry is a coalesced load of the source row along d.
 constexpr int kApplyThreads = 256;
 
+// ---- TMA pipeline for the T_up row segments (TMA apply configurations).
+// A producer warp copies the source-row chunk of every T_up entry into a ring
+// of shared-memory slots (the configuration's stage count) with
+// cp.async.bulk; "full" mbarriers carry the byte count, "empty" mbarriers
+// collect one arrival per consumer warp.  Every wait is bounded: after
+// kTmaWaitLimit failed polls the thread records ED_ERR_TIMEOUT in the
+// vector's status and a block-wide flag, and all later waits of the block
+// give up at once.
+constexpr uint32_t kTmaWaitLimit = 1u << 22;
+constexpr int kStatusTimeout = 4;    // ED_ERR_TIMEOUT
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false on timeout or when
+// another thread of the block has already timed out (err set).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err) {
+  for (uint32_t it = 0; it < kTmaWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*err) return false;
+  }
+  *err = 1;
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16), completing bytes on the mbarrier.
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Column pair (2p, 2p+1) of a row: one 16-byte access for aligned complex64
 // rows (VEC), else two element accesses with the second column checked.
 // STREAM: data read or written once in this pass (the previous Krylov vector,
@@ -318,15 +375,20 @@ struct TileIO {
 //    row per k, all in flight before they are summed by group.
 //  * Epilogue: w = s_j acc - beta_{j-1} s_{j-1} x_{j-1}, stored in pairs,
 //    and the partial of Re<x_j, w>.
-template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT>
-__global__ void __launch_bounds__(kApplyThreads, MINB)
+template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS>
+__global__ void __launch_bounds__(TMAS ? kApplyThreads + 32 : kApplyThreads, MINB)
 k_apply(BatchArgs a, int j) {
+  constexpr bool TMA = TMAS > 0;       // TMAS: ring stages of the TMA configurations
+  constexpr uint32_t S = TMAS > 0 ? (uint32_t)TMAS : 1u;
   using C = typename C2T<R>::T;
   using TIO = TileIO<C, NR>;
-  constexpr int T = kApplyThreads;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int T = kApplyThreads;           // consumer threads (all threads without TMA)
+  constexpr uint32_t kSlotBytes = (uint32_t)(T * PP * 2 * sizeof(C));   // one chunk of a row
+  static_assert(!(TMA && SPLIT), "the TMA ring serves the one-kernel T_up");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[32 * 2];
   __shared__ int flag;
+  __shared__ int tma_err;
 
   const ApplyBlock ab = a.apply_map[blockIdx.x];
   const VecDev vd = a.vec[ab.vec];
@@ -342,6 +404,27 @@ k_apply(BatchArgs a, int j) {
 
   C* tile = reinterpret_cast<C*>(smem_raw);              // [max_dim_dn + kZeroCols][NR]
   C* coefS = tile + (size_t)(a.max_dim_dn + kZeroCols) * NR;   // [n_groups]
+  // TMA configurations: ring of S row chunks (128-byte aligned after
+  // the coefficients), then S full and S empty mbarriers
+  char* ring = nullptr;
+  uint64_t* full = nullptr;
+  uint64_t* empty = nullptr;
+  if constexpr (TMA) {
+    size_t off = ((size_t)(a.max_dim_dn + kZeroCols) * NR + (size_t)a.n_groups) * sizeof(C);
+    off = (off + 127) & ~(size_t)127;
+    ring = reinterpret_cast<char*>(smem_raw) + off;
+    full = reinterpret_cast<uint64_t*>(ring + (size_t)S * kSlotBytes);
+    empty = full + S;
+    if (tid == 0) {
+      for (int q = 0; q < S; ++q) {
+        mbar_init(full + q, 1);
+        mbar_init(empty + q, T / 32);
+      }
+      tma_err = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+  }
 
   const void* cbase;
   if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
@@ -358,7 +441,7 @@ k_apply(BatchArgs a, int j) {
 
   // ---- stage the NR rows column by column (pairs of columns per thread,
   // all NR row loads of two pairs in flight), plus the zero pair past the end
-  {
+  if (!TMA || tid < T) {
     const int np2 = npairs + 1;   // one extra pair: the zero columns
 #pragma unroll 2
     for (int p = tid; p < np2; p += T) {
@@ -402,6 +485,47 @@ k_apply(BatchArgs a, int j) {
   __syncthreads();
 
   double dot_d = 0.0;
+  uint32_t cidx = 0;     // T_up entries consumed so far (TMA ring position)
+  if (TMA && tid >= T) {
+    // ---- producer warp (TMA configurations): one elected lane issues the
+    // row chunk of every T_up entry, chunk by chunk and row by row, in the
+    // order the consumers read them
+    if constexpr (TMA) {
+      if (lane == 0) {
+        uint32_t idx = 0;
+        bool ok = true;
+        for (int pc = 0; pc < npairs && ok; pc += T * PP) {
+          const int np_chunk = min(T * PP, npairs - pc);
+          const uint32_t bytes = (uint32_t)np_chunk * 2u * (uint32_t)sizeof(C);
+          for (int r = 0; r < nrows && ok; ++r) {
+            const int e0 = __ldg(sd.up_off + u0 + r), e1 = __ldg(sd.up_off + u0 + r + 1);
+            for (int e = e0; e < e1; ++e, ++idx) {
+              const uint32_t q = idx % S;
+              if (idx >= (uint32_t)S &&
+                  !mbar_wait(empty + q, ((idx / S) - 1u) & 1u, &tma_err)) {
+                ok = false;
+                break;
+              }
+              const uint32_t src = __ldg(sd.up_ent + e) & kEntRankMask;
+              const char* g = reinterpret_cast<const char*>(x) +
+                              ((size_t)src * dim_dn + 2 * (size_t)pc) * sizeof(C);
+              mbar_arrive_expect_tx(full + q, bytes);
+              tma_bulk_g2s(ring + (size_t)q * kSlotBytes, g, bytes, full + q);
+            }
+          }
+        }
+        if (!ok) {
+          st->status = kStatusTimeout;
+          // wait (bounded, ignoring the flag) for the copies still in flight
+          const uint32_t first = idx > (uint32_t)S ? idx - S : 0u;
+          for (uint32_t k = first; k < idx; ++k)
+            for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
+              if (mbar_try_wait(full + k % S, (k / S) & 1u)) break;
+        }
+      }
+      __syncwarp();
+    }
+  } else
   for (int pc = 0; pc < npairs; pc += T * PP) {
     C acc[NR][2 * PP];
     // ---- diagonal
@@ -527,12 +651,72 @@ k_apply(BatchArgs a, int j) {
           acc[r][k].y += tv[r][k].y;
         }
     }
+    // ---- T_up through the TMA ring: the row chunk of each entry (CSR order,
+    // sorted by group) waits in the next ring slot; read the thread's pairs,
+    // release the slot, sum by group
+    if constexpr (TMA) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nrows) {
+          const int e0 = __ldg(sd.up_off + u0 + r), e1 = __ldg(sd.up_off + u0 + r + 1);
+          C sum[2 * PP];
+#pragma unroll
+          for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
+          uint32_t nent = e0 < e1 ? __ldg(sd.up_ent + e0) : 0u;
+          uint32_t gcur = (nent >> kEntGroupShift) & 0xFFu;
+          for (int e = e0; e < e1; ++e, ++cidx) {
+            const uint32_t ent = nent;
+            if (e + 1 < e1) nent = __ldg(sd.up_ent + e + 1);   // next entry under this one
+            const uint32_t q = cidx % S;
+            const bool ready = mbar_wait(full + q, (cidx / S) & 1u, &tma_err);
+            const char* slot = ring + (size_t)q * kSlotBytes;
+            C v[2 * PP];
+#pragma unroll
+            for (int k = 0; k < PP; ++k) {
+              if (ready && pvalid[k]) {
+                if constexpr (sizeof(C) == 8) {
+                  const float4 f = *reinterpret_cast<const float4*>(slot + (size_t)(tid + k * T) * 16);
+                  v[2 * k].x = f.x; v[2 * k].y = f.y; v[2 * k + 1].x = f.z; v[2 * k + 1].y = f.w;
+                } else {
+                  const C* pr = reinterpret_cast<const C*>(slot) + 2 * (size_t)(tid + k * T);
+                  v[2 * k] = pr[0];
+                  v[2 * k + 1] = pr[1];
+                }
+              } else {
+                v[2 * k] = czero<C>();
+                v[2 * k + 1] = czero<C>();
+              }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + q);
+            const uint32_t g = (ent >> kEntGroupShift) & 0xFFu;
+            if (g != gcur) {                              // uniform over the block
+              const C c = coefS[gcur];
+#pragma unroll
+              for (int k = 0; k < 2 * PP; ++k) {
+                cmac(acc[r][k], c, sum[k]);
+                sum[k] = czero<C>();
+              }
+              gcur = g;
+            }
+            const R sg = sign_of<R>(ent);
+#pragma unroll
+            for (int k = 0; k < 2 * PP; ++k) cax(sum[k], sg, v[k]);
+          }
+          if (e0 < e1) {
+            const C c = coefS[gcur];
+#pragma unroll
+            for (int k = 0; k < 2 * PP; ++k) cmac(acc[r][k], c, sum[k]);
+          }
+        }
+      }
+    }
     // ---- T_up: the padded entry list of each row (uniform over the block),
     // four entries per batch with all their row loads in flight, coefficient
     // applied when the group changes
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      if (!SPLIT && r < nrows) {
+      if (!SPLIT && !TMA && r < nrows) {
         const int u = u0 + r;
         const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
         C sum[2 * PP];
@@ -631,6 +815,9 @@ k_apply(BatchArgs a, int j) {
       }
     }
     dot_d += (double)dot_acc;
+  }
+  if constexpr (TMA) {
+    if (tma_err && tid == 0) st->status = kStatusTimeout;
   }
   if (j == 0) return;
   double v[1] = {dot_d};
@@ -1545,7 +1732,9 @@ static int grid_for(int64_t n, int threads) {
 // register budget) of the row kernel; for the split apply also the pairs per
 // thread and occupancy of the column pass.  The autotuner times the feasible
 // ones.
-struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc, cb, tc; };
+struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc, cb, tc; int tma; };
+// tma: 0, or the ring stages of a configuration whose T_up row chunks are
+// staged by TMA
 static const ApplyCfg kApplyCfgs[] = {
     {false, 4, 2, 2, false, 0, 0, 0, 0}, {false, 2, 2, 3, false, 0, 0, 0, 0},
     {false, 2, 1, 4, false, 0, 0, 0, 0}, {false, 1, 2, 2, false, 0, 0, 0, 0},
@@ -1557,11 +1746,14 @@ static const ApplyCfg kApplyCfgs[] = {
     // long columns (vectors beyond L2): 16-byte column blocks, one 512-thread
     // column CTA per SM
     {false, 1, 2, 2, true, 1, 1, 16, 512}, {true, 1, 1, 1, true, 1, 1, 16, 512},
+    // one kernel with the T_up row chunks staged by TMA (a producer warp)
+    {false, 2, 2, 2, false, 0, 0, 0, 0, 6}, {false, 1, 2, 2, false, 0, 0, 0, 0, 8},
+    {true, 1, 1, 2, false, 0, 0, 0, 0, 6},
 };
 static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
 
 int apply_config_count() { return kNumApplyCfgs; }
-bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split) {
+bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split, int* tma) {
   if (i < 0 || i >= kNumApplyCfgs) return false;
   const ApplyCfg& c = kApplyCfgs[i];
   *fp64 = c.fp64;
@@ -1569,6 +1761,7 @@ bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split
   *pp = c.pp;
   *minb = c.minb;
   *split = c.split;
+  *tma = c.tma > 0;
   return true;
 }
 
@@ -1586,7 +1779,11 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     sh.split = c.split;
     sh.cb = c.cb;
     sh.tc = c.tc;
+    sh.tma = c.tma > 0;
     sh.smem = ((size_t)(max_dim_dn + kZeroCols) * c.nr + (size_t)n_groups) * csz;
+    if (c.tma)   // 128-byte aligned ring of row chunks + full/empty mbarriers
+      sh.smem = ((sh.smem + 127) & ~(size_t)127) +
+                (size_t)c.tma * kApplyThreads * c.pp * 2 * csz + 2 * (size_t)c.tma * 8;
     sh.smem_c = c.split ? (size_t)(max_dim_up + kZeroCols) * c.cb + (size_t)n_groups * csz : 0;
     return sh;
   };
@@ -1600,14 +1797,14 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     out.push_back(sh);
   }
   bool have_fused = false;
-  for (const LaunchShape& sh : out) have_fused |= !sh.split;
+  for (const LaunchShape& sh : out) have_fused |= !sh.split && !sh.tma;
   if (!have_fused) {   // very long rows: one row per CTA, one CTA per SM;
     // of those entries the one with the fewest target CTAs per SM (the
     // largest register budget)
     int best = -1;
     for (int i = 0; i < kNumApplyCfgs; ++i) {
       const ApplyCfg& c = kApplyCfgs[i];
-      if (c.fp64 != fp64 || c.nr != 1 || c.split) continue;
+      if (c.fp64 != fp64 || c.nr != 1 || c.split || c.tma) continue;
       if (best < 0 || c.minb < kApplyCfgs[best].minb) best = i;
     }
     if (best >= 0) {
@@ -1628,29 +1825,32 @@ LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups)
   return c.front();
 }
 
-template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC>
+template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC,
+          int TMA>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
   constexpr bool V = sizeof(R) == 4;
+  constexpr int threads = TMA ? kApplyThreads + 32 : kApplyThreads;
   if constexpr (SPLIT) {
     if (sh.vec) k_apply_up<R, PPC, V, MINBC, CB, TC><<<a.n_col_blocks, TC, sh.smem_c, s>>>(a, j);
     else k_apply_up<R, PPC, false, MINBC, CB, TC><<<a.n_col_blocks, TC, sh.smem_c, s>>>(a, j);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
-  else k_apply<R, NR, PP, false, MINB, SPLIT><<<nblk, kApplyThreads, sh.smem, s>>>(a, j);
+  if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT, TMA><<<nblk, threads, sh.smem, s>>>(a, j);
+  else k_apply<R, NR, PP, false, MINB, SPLIT, TMA><<<nblk, threads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
 }
 
-template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC>
+template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC,
+          int TMA>
 static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   constexpr bool V = sizeof(R) == 4;
   const int sm = (int)sh.smem;
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, SPLIT>,
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, SPLIT, TMA>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT>,
+  e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
   if constexpr (SPLIT) {
@@ -1665,28 +1865,31 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
 }
 
 // One switch over the configuration table for both prepare and launch.
-#define ED_APPLY_CONFIGS(X)                          \
-  X(0, float, 4, 2, 2, false, 1, 1, 32, 256)         \
-  X(1, float, 2, 2, 3, false, 1, 1, 32, 256)         \
-  X(2, float, 2, 1, 4, false, 1, 1, 32, 256)         \
-  X(3, float, 1, 2, 2, false, 1, 1, 32, 256)         \
-  X(4, double, 2, 1, 2, false, 1, 1, 32, 256)        \
-  X(5, double, 1, 1, 4, false, 1, 1, 32, 256)        \
-  X(6, double, 1, 1, 2, false, 1, 1, 32, 256)        \
-  X(7, float, 4, 2, 2, true, 1, 2, 32, 256)          \
-  X(8, float, 2, 2, 3, true, 1, 2, 32, 256)          \
-  X(9, float, 2, 1, 4, true, 1, 2, 32, 256)          \
-  X(10, float, 4, 2, 2, true, 2, 2, 32, 256)         \
-  X(11, double, 2, 1, 2, true, 1, 2, 32, 256)        \
-  X(12, double, 1, 1, 4, true, 1, 2, 32, 256)        \
-  X(13, float, 1, 2, 2, true, 1, 1, 16, 512)         \
-  X(14, double, 1, 1, 1, true, 1, 1, 16, 512)
+#define ED_APPLY_CONFIGS(X)                                \
+  X(0, float, 4, 2, 2, false, 1, 1, 32, 256, 0)        \
+  X(1, float, 2, 2, 3, false, 1, 1, 32, 256, 0)        \
+  X(2, float, 2, 1, 4, false, 1, 1, 32, 256, 0)        \
+  X(3, float, 1, 2, 2, false, 1, 1, 32, 256, 0)        \
+  X(4, double, 2, 1, 2, false, 1, 1, 32, 256, 0)       \
+  X(5, double, 1, 1, 4, false, 1, 1, 32, 256, 0)       \
+  X(6, double, 1, 1, 2, false, 1, 1, 32, 256, 0)       \
+  X(7, float, 4, 2, 2, true, 1, 2, 32, 256, 0)         \
+  X(8, float, 2, 2, 3, true, 1, 2, 32, 256, 0)         \
+  X(9, float, 2, 1, 4, true, 1, 2, 32, 256, 0)         \
+  X(10, float, 4, 2, 2, true, 2, 2, 32, 256, 0)        \
+  X(11, double, 2, 1, 2, true, 1, 2, 32, 256, 0)       \
+  X(12, double, 1, 1, 4, true, 1, 2, 32, 256, 0)       \
+  X(13, float, 1, 2, 2, true, 1, 1, 16, 512, 0)        \
+  X(14, double, 1, 1, 1, true, 1, 1, 16, 512, 0)       \
+  X(15, float, 2, 2, 2, false, 1, 1, 32, 256, 6)        \
+  X(16, float, 1, 2, 2, false, 1, 1, 32, 256, 8)        \
+  X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6)
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
   (void)fp64;
   if (sh.nr < 1 || sh.smem > 227 * 1024 || sh.smem_c > 227 * 1024) return cudaErrorInvalidValue;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC) \
-  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC>(sh);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM) \
+  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM>(sh);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;
@@ -1697,8 +1900,8 @@ cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
                          int j, cudaStream_t s) {
   (void)fp64;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC) \
-  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC>(a, nblk, sh, j, s);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM) \
+  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM>(a, nblk, sh, j, s);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;

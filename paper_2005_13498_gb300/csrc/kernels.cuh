@@ -21,6 +21,7 @@ struct LaunchShape {
   size_t smem_c = 0;   // dynamic shared memory of the column pass
   int cb = 32;         // column-pass block: bytes of columns per row (32 or 16)
   int tc = 256;        // column-pass threads per CTA
+  bool tma = false;    // T_up row chunks staged by TMA (one extra producer warp)
 };
 
 // Feasible apply configurations for sectors of at most max_dim_up rows of
@@ -47,7 +48,7 @@ inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_u
 // The configuration table: its size, and the precision, rows per CTA, pairs
 // per thread, CTAs per SM and split flag of entry i (false if out of range).
 int apply_config_count();
-bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split);
+bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split, int* tma);
 // The default configuration (first candidate).
 LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups);
 // Raise the dynamic shared-memory limit of the apply kernel for this shape

@@ -1,6 +1,7 @@
 """Every H v kernel configuration against the oracle, each pinned in turn
-with ed_set_apply_config: the one-kernel variants and the split variants
-(column pass for T_up, row pass for the diagonal and T_dn), with all their
+with ed_set_apply_config: the one-kernel variants, the split variants
+(column pass for T_up, row pass for the diagonal and T_dn) and the variants
+whose T_up row chunks a producer warp stages by TMA, with all their
 rows-per-block, pairs-per-thread and occupancy settings.
 
 The sectors put the column pass through each of its layout cases: dim_dn a
@@ -67,6 +68,12 @@ def test_every_config_matches_oracle(pinned, dtype, name, lat, nu, nd, U):
     for cfg in configs(ed, dtype):
         ed.ed_set_apply_config(cfg)
         wd = torch.full_like(vd, float("nan"))
+        if ed.ed_apply_config_info(cfg)["tma"] and h.dim_dn % 2:
+            # TMA row chunks need rows of an even number of elements
+            with pytest.raises(ed.EDError) as e:
+                ed.ed_apply_H(h.ctx, vd, wd, ed_dtype(ed, dtype), nvec=2)
+            assert "does not fit" in str(e.value)
+            continue
         ed.ed_apply_H(h.ctx, vd, wd, ed_dtype(ed, dtype), nvec=2)
         torch.cuda.synchronize()
         assert ed.ed_get_apply_config(h.ctx)[1] == cfg
@@ -77,9 +84,10 @@ def test_every_config_matches_oracle(pinned, dtype, name, lat, nu, nd, U):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_split_propagation_with_energy_matches_oracle(pinned, dtype):
-    """A short propagation of the 3x4 torus, (6,5), with every split
-    configuration of the precision pinned: state, <d>, norm and energy (the
-    energy runs H v once more per step) against the oracle's trajectory."""
+    """A short propagation of the 3x4 torus, (6,5), with every split and
+    every TMA configuration of the precision pinned: state, <d>, norm and
+    energy (the energy runs H v once more per step) against the oracle's
+    trajectory."""
     torch = torch_cuda()
     ed = pinned
     lat = LATTICES["torus3x4"]
@@ -87,7 +95,8 @@ def test_split_propagation_with_energy_matches_oracle(pinned, dtype):
     psi0 = synth.complex_normal(924 * 792, 11)
     psi0 /= np.linalg.norm(psi0)
     ref = oracle.propagate(lat, 6, 5, 8.0, psi0, pulse, 0.02, 6, 16, with_energy=True)
-    split = [c for c in configs(ed, dtype) if ed.ed_apply_config_info(c)["split"]]
+    split = [c for c in configs(ed, dtype)
+             if ed.ed_apply_config_info(c)["split"] or ed.ed_apply_config_info(c)["tma"]]
     for cfg in split:
         ed.ed_set_apply_config(cfg)
         h = ed.Hubbard(lat, 6, 5, 8.0)

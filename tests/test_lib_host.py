@@ -181,7 +181,7 @@ def test_apply_config_table_and_switch(ed):
     seen = set()
     for c in range(n):
         i = ed.ed_apply_config_info(c)
-        assert i["fp64"] in (0, 1) and i["split"] in (0, 1)
+        assert i["fp64"] in (0, 1) and i["split"] in (0, 1) and i["tma"] in (0, 1)
         assert i["rows_per_cta"] >= 1 and i["pairs_per_thread"] >= 1 and i["ctas_per_sm"] >= 1
         seen.add((i["fp64"], i["split"]))
     assert seen == {(0, 0), (0, 1), (1, 0), (1, 1)}
