@@ -385,7 +385,7 @@ k_apply(BatchArgs a, int j) {
   constexpr int T = kApplyThreads;           // consumer threads (all threads without TMA)
   constexpr uint32_t kSlotBytes = (uint32_t)(T * PP * 2 * sizeof(C));   // one chunk of a row
   static_assert(!(TMA && SPLIT), "the TMA ring serves the one-kernel T_up");
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32 * 2];
   __shared__ int flag;
   __shared__ int tma_err;
