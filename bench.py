@@ -426,7 +426,7 @@ def smaller_workloads_bench(ed, torch, synth, stream, barrier, steps):
             e1.record(stream)
             barrier()
             bms = e0.elapsed_time(e1) / steps
-            # A(nu, t_ref) at t_ref = 1.0 (Eq. (15) and Eq. (A_noneq_broad)):
+            # A(nu, t_ref) at t_ref = 1.0 (Eq. (15) and Eq. (37)):
             # psi to t_ref, the batch from t_ref, the broadened transform
             t_ref, n_tr = 1.0, 2 * steps
             x = g.clone()

@@ -7,9 +7,11 @@
  * time dependent Hubbard Hamiltonians" (arXiv:2005.13498): the Hubbard
  * Hamiltonian H(t) with Peierls phases (Sec. 2.1-2.2, Eqs. (1), (3)) in one
  * (n_up, n_dn) sector (Sec. 2.3, 3.1), applied matrix-free on the GPU inside a
- * fixed-dimension Lanczos approximation of exp(-i tau H(t_mid)) v (Sec. 3.4,
- * Algorithm 6) for the exponential midpoint rule (Eq. (32)), with the
- * observables of Sec. 3.5 and the nonequilibrium Green's functions of Eq. (15).
+ * Lanczos approximation of exp(-i tau H(t_mid)) v (Sec. 3.4, Algorithm 6;
+ * fixed dimension by default, or with the algorithm's adaptive exit) for the
+ * exponential midpoint rule (Eq. (32)) or a fourth-order commutator-free
+ * scheme, with the observables of Sec. 3.5, the nonequilibrium Green's
+ * functions of Eq. (15) and the spectral function of Eq. (37).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -82,8 +84,9 @@ typedef enum { ED_MIDPOINT = 0, ED_CFET4 = 1 } ed_integrator;
  * A(t).d_b (Eq. (3)); dir is used as given (not normalised).
  * shape ED_PULSE_SIN_GAUSS (0):
  *   A(t) = A0 exp(-(t-t0)^2/(2 sigma^2)) sin(omega (t - t0)) dir,
- *   the vector potential of the field pulse of Eq. (2) up to the integration.
- * shape ED_PULSE_COS_PHASE (1): the paper's simplified phase of Eq. (5),
+ *   a Gaussian-enveloped oscillation like the field pulse of Eq. (2); the
+ *   workloads define their pulses by A(t) directly.
+ * shape ED_PULSE_COS_PHASE (1): the paper's simplified phase of Eq. (4),
  *   A(t) = -A0 [cos(omega (t - t0)) - b] exp(-(t-t0)^2/(2 sigma^2)) dir,
  *   so that a hop p -> q with dir.d_b = 1 carries exactly the factor
  *   f(t) = exp(i a [cos(omega (t - t_p)) - b] exp(-(t-t_p)^2/(2 sigma^2)))
@@ -106,9 +109,12 @@ typedef struct {
   double* norm2;   /* [n_steps+1] |psi(t_n)|^2                                 */
   double* energy;  /* [n_steps+1] E(t_n) = (1/Ns) <psi|H(t_n)|psi>, Eq. (14);
                       costs one extra apply per step                          */
-  double* delta;   /* [n_steps] a-posteriori estimate delta of Algorithm 6
-                      (diagnostic only; the Krylov dimension stays fixed)      */
-  int32_t* m_eff;  /* [n_steps] Krylov dimension used (< m after breakdown)    */
+  double* delta;   /* [n_steps] a-posteriori estimate delta of Algorithm 6 for
+                      the step's Krylov approximation (a diagnostic unless
+                      ed_set_krylov_tol enabled the adaptive exit)             */
+  int32_t* m_eff;  /* [n_steps] Krylov dimension used (< m after a breakdown
+                      or the adaptive exit); with ED_CFET4 the larger of the
+                      step's two Krylov steps, likewise delta                   */
   int32_t profile; /* nonzero: launch kernels one by one (no CUDA graph) with
                       a CUDA event pair around every launch on the launching
                       stream, and report per-kind device time below           */
@@ -257,7 +263,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctxN, const void* psi0, double t_ref,
                                    double dt, int n_steps, int m,
                                    double* G_less, double* G_great, void* stream);
 
-/* Broadened Fourier transform of Eq. (A_noneq_broad) (Sec. 3.7), on the host:
+/* Broadened Fourier transform of Eq. (37) (Sec. 3.7), on the host:
  *   A[f][j] = (1/pi) Im int_0^{T} e^{-eps t} e^{i nu_f t} G_j(t) dt,
  * T = n_steps dt, by the trapezoid rule over the samples G_j(k dt),
  * k = 0..n_steps.  G: host array [n_steps+1][n_series] complex128

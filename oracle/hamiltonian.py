@@ -36,7 +36,7 @@ def pulse_A(t, pulse):
     """Vector potential A(t) (3-vector) of a pulse.
 
     shape "sin" (default): A0 exp(-s^2/(2 sigma^2)) sin(omega s) dir, s = t - t0.
-    shape "cos_phase": the paper's phase function of Eq. (5) written as a
+    shape "cos_phase": the paper's phase function of Eq. (4) written as a
     vector potential, A(t) = -A0 [cos(omega s) - b] exp(-s^2/(2 sigma^2)) dir,
     so a hop along dir (d_b . dir = 1) carries f(t) = exp(i a [cos(omega
     (t - t_p)) - b] e^{-(t-t_p)^2/(2 sigma^2)}) with a = A0, t_p = t0.

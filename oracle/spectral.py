@@ -150,7 +150,7 @@ def lehmann_overlaps(lattice, n_up, n_dn, U, psi0, E0, times, site, spin):
 
 
 def broadened_transform(G, dt, eps, nu):
-    """Eq. (A_noneq_broad), Sec. 3.7: A(nu) = (1/pi) Im int_0^T e^{-eps t}
+    """Eq. (37), Sec. 3.7: A(nu) = (1/pi) Im int_0^T e^{-eps t}
     e^{i nu t} G(t) dt with T = (len(G) - 1) dt, the integral by the
     trapezoid rule over the samples G[k] = G(k dt).  G: [n+1, ...]."""
     G = np.asarray(G, dtype=np.complex128)

@@ -449,7 +449,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
   return ED_OK;
 }
 
-// Eq. (A_noneq_broad), Sec. 3.7: A(nu) = (1/pi) Im int_0^T e^{-eps t} e^{i nu t}
+// Eq. (37), Sec. 3.7: A(nu) = (1/pi) Im int_0^T e^{-eps t} e^{i nu t}
 // G(t) dt over the samples G(k dt), k = 0..n_steps, by the trapezoid rule.
 ed_status ed_spectral_function(const double* G, int n_steps, int n_series, double dt,
                                double eps, const double* nu, int n_nu, double* A) {

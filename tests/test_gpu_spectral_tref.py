@@ -1,7 +1,7 @@
 """GPU parity of the Green's functions at a reference time t_ref > 0
 (ed_spectral_propagate_at, Eq. (15)) with the paper's own hopping phase of
-Eq. (5) (pulse shape "cos_phase"), and of A(nu, t_ref) of Eq.
-(A_noneq_broad) through the library's transform, against the oracle.
+Eq. (4) (pulse shape "cos_phase"), and of A(nu, t_ref) of Eq. (37) through
+the library's transform, against the oracle.
 complex128: 1e-9 on G, 1e-8 on A.
 """
 import numpy as np

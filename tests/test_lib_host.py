@@ -221,7 +221,7 @@ def test_integrator_argument_checks(ed):
 
 def test_spectral_function_host_transform_matches_oracle(ed):
     """ed_spectral_function (host code of the library) against the oracle's
-    broadened transform of Eq. (A_noneq_broad)."""
+    broadened transform of Eq. (37)."""
     rng = np.random.default_rng(1)
     G = rng.standard_normal((101, 3, 2)) + 1j * rng.standard_normal((101, 3, 2))
     nu = np.linspace(-5, 5, 17)

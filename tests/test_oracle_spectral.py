@@ -98,10 +98,10 @@ def test_dimer_green_function_closed_form(U):
             assert np.abs(r["G"][:, i, s] - G).max() < 1e-12
 
 
-# ------------------------------------------- reference time, Eq. (5) pulse, A(nu,t)
+# ------------------------------------------- reference time, Eq. (4) pulse, A(nu,t)
 
 def test_cos_phase_pulse_is_the_papers_hopping_factor():
-    """Eq. (5): with dir = (1,1,0) on the 3x4 torus every +x and +y hop
+    """Eq. (4): with dir = (1,1,0) on the 3x4 torus every +x and +y hop
     p -> q carries f(t) = exp(i a [cos(omega (t - t_p)) - b]
     e^{-(t-t_p)^2/(2 sigma^2)}) (one-electron sector, h[q, p] = -t f(t));
     b = cos(omega t_p) makes f(0) = 1."""
