@@ -188,6 +188,27 @@ def cpu_sample(w, lat, n_iter=2, reps=1):
                         f"scaled to build + {m} iterations + {m} axpys")
 
 
+def small_oracle_steps():
+    """The oracle's ms per midpoint step on the ring (complex128, m=12, 20
+    steps) and on the 3x4 torus (m=20, 2 steps), both from a seeded state
+    inside the pulse: bounded samples of those trajectories, beside the GPU
+    numbers of the same workloads."""
+    import oracle
+    import synth
+    out = {}
+    for name, steps in (("ring8", 20), ("torus3x4", 2)):
+        w = synth.workload(name)
+        lat = synth.lattice_from_name(w["lattice"])
+        D = oracle.sector_dims(lat["Ns"], w["n_up"], w["n_dn"])[2]
+        psi = synth.complex_normal(D, 0)
+        t0 = time.perf_counter()
+        oracle.propagate(lat, w["n_up"], w["n_dn"], w["U"], psi, w["pulse_params"], w["dt"],
+                         steps, w["m"], t_start=w["pulse_params"]["t0"] - 1.0)
+        out[name] = {"ms_per_step": (time.perf_counter() - t0) * 1e3 / steps, "steps": steps,
+                     "m": w["m"], "kind": "oracle (float64, NumPy/SciPy)"}
+    return out
+
+
 def spectral_bench(ed, torch, synth, lat, w, pulse, h, psi64, stream, barrier, steps):
     m_spec = 20
     t0 = pulse["t0"] - 1.0
@@ -699,6 +720,8 @@ def main():
             cores = _t.get_num_threads()
             line["cpu_baseline"] = {"value": cms, "unit": UNIT, "cores": cores,
                                     "kind": "oracle", "sample": desc}
+            if not args.no_small:
+                line["cpu_baseline_small"] = small_oracle_steps()
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
