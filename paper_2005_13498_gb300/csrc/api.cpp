@@ -51,6 +51,13 @@ cudaError_t upload_sector(SectorGPU& S) {
     for (size_t i = 0; i < rows.size(); ++i)
       rows[i] = (S.up.pad_ent[i] & kEntRankMask) * (uint32_t)S.dn.dim;
     if ((e = upload(S.up_pad_row, rows)) != cudaSuccess) return e;
+    std::vector<uint32_t> cs(S.up.pad_ent.size());
+    for (size_t i = 0; i < cs.size(); ++i) {
+      const uint32_t en = S.up.pad_ent[i];
+      cs[i] = (en & kNullEntryBit) ? 0u
+                                   : 1u + 2u * ((en >> kEntGroupShift) & 0xFFu) + (en >> 31);
+    }
+    if ((e = upload(S.up_pad_cs, cs)) != cudaSuccess) return e;
   }
   if ((e = upload(S.dn_tslot_off, S.dn.tslot_off)) != cudaSuccess) return e;
   if ((e = upload(S.dn_slot_grp, S.dn.slot_grp)) != cudaSuccess) return e;
@@ -94,6 +101,7 @@ cudaError_t upload_sector(SectorGPU& S) {
   d.up_pad_off = static_cast<const int32_t*>(S.up_pad_off.p);
   d.up_pad_ent = static_cast<const uint32_t*>(S.up_pad_ent.p);
   d.up_pad_row = static_cast<const uint32_t*>(S.up_pad_row.p);
+  d.up_pad_cs = static_cast<const uint32_t*>(S.up_pad_cs.p);
   d.dn_tslot_off = static_cast<const int32_t*>(S.dn_tslot_off.p);
   d.dn_slot_grp = static_cast<const uint32_t*>(S.dn_slot_grp.p);
   d.dn_ell = static_cast<const uint32_t*>(S.dn_ell.p);
@@ -301,7 +309,8 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
   const SectorGPU& S = ctx->sec;
   int64_t b = S.up_off.bytes + S.up_ent.bytes + S.dn_off.bytes + S.dn_ent.bytes +
               S.up_word.bytes + S.dn_word.bytes + S.up_eps.bytes + S.dn_eps.bytes +
-              S.up_pad_off.bytes + S.up_pad_ent.bytes + S.up_pad_row.bytes + S.dn_tslot_off.bytes +
+              S.up_pad_off.bytes + S.up_pad_ent.bytes + S.up_pad_row.bytes + S.up_pad_cs.bytes +
+              S.dn_tslot_off.bytes +
               S.dn_slot_grp.bytes + S.dn_ell.bytes + S.up_tslot_off.bytes + S.up_slot_grp.bytes +
               S.up_ell.bytes + S.dn_ell16.bytes + S.dn_ell8.bytes + S.up_ell16.bytes;
   if (ctx->engine) b += ctx->engine->device_bytes();

@@ -38,6 +38,7 @@ struct SectorDev {
   const int32_t* up_pad_off;   // [dim_up + 1]
   const uint32_t* up_pad_ent;  // entries; bit 30 = null (contributes zero)
   const uint32_t* up_pad_row;  // element offset of the source row: rank * dim_dn
+  const uint32_t* up_pad_cs;   // coefficient slot: 0 padding, else 1 + 2 group + sign
   // down spin: warp-tiled ELL over 64-column tiles (within-row gathers)
   const int32_t* dn_tslot_off; // [ceil(dim_dn/64) + 1], even slot counts
   const uint32_t* dn_slot_grp; // group of each slot

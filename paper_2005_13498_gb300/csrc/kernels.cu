@@ -358,6 +358,162 @@ struct TileIO {
   }
 };
 
+// T_up gathers of one chunk of the apply (k_apply): for each of the CTA's
+// rows u the padded entry list of u (uniform over the block) is walked four
+// entries at a time, each a coalesced load of the thread's column pairs of
+// the source row per column-pair group k < KA, all loads of a batch in
+// flight before they are used.  KA counts the groups of this chunk that hold
+// valid pairs; in the last of them the pair index is clamped to the last
+// pair of the row (those sums are never stored).
+//  * complex64: no group sums.  Each entry reads its signed coefficient
+//    s c_g from the CTA's table coefQ[cs] = (s Re c, s Re c, s Im c, s Im c)
+//    (cs = 1 + 2 g + [s < 0], cs = 0 for padding: zero), one broadcast load,
+//    and accumulates a += (Re, Re) v, b += (Im, Im) v with two packed FMAs
+//    and no operand swaps; the row ends with acc += (a.x - b.y, a.y + b.x).
+//  * complex128 (FP64-pipe bound): signed sums per bond group, multiplied
+//    by c_g once per group.
+template <int NR, int PP, int KA, bool VEC>
+__device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2* x,
+                                              const float4* coefQ, int u0, int nrows, int pc,
+                                              int npairs, int dim_dn, float2 (&acc)[NR][2 * PP]) {
+  constexpr int T = kApplyThreads;
+  int pk[KA];
+#pragma unroll
+  for (int k = 0; k < KA; ++k) pk[k] = min(pc + (int)threadIdx.x + k * T, npairs - 1);
+  const uint4* cs4p = reinterpret_cast<const uint4*>(sd.up_pad_cs);
+  const uint4* row4p = reinterpret_cast<const uint4*>(sd.up_pad_row);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r >= nrows) continue;   // uniform over the block
+    const int u = u0 + r;
+    const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
+    if (e0 >= e1) continue;
+    float2 sa[2 * KA], sb[2 * KA];
+#pragma unroll
+    for (int k = 0; k < 2 * KA; ++k) { sa[k] = make_float2(0.f, 0.f); sb[k] = sa[k]; }
+    uint4 ncs = __ldg(cs4p + (e0 >> 2)), nrow = __ldg(row4p + (e0 >> 2));
+    for (int e = e0; e < e1; e += 4) {
+      const uint4 cs4 = ncs, row4 = nrow;
+      if (e + 4 < e1) {   // the next batch's entries load under this batch's rows
+        ncs = __ldg(cs4p + ((e + 4) >> 2));
+        nrow = __ldg(row4p + ((e + 4) >> 2));
+      }
+      const uint32_t css[4] = {cs4.x, cs4.y, cs4.z, cs4.w};
+      const uint32_t rows[4] = {row4.x, row4.y, row4.z, row4.w};
+      float2 v[4][2 * KA];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        const float2* src = x + rows[qq];
+#pragma unroll
+        for (int k = 0; k < KA; ++k) {
+          if constexpr (VEC) {
+            const float4 f = reinterpret_cast<const float4*>(src)[pk[k]];
+            v[qq][2 * k] = make_float2(f.x, f.y);
+            v[qq][2 * k + 1] = make_float2(f.z, f.w);
+          } else {
+            load_pair<float2, false>(src, pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        const float4 q = coefQ[css[qq]];
+#pragma unroll
+        for (int k = 0; k < 2 * KA; ++k) {
+          sa[k] = ffma2(make_float2(q.x, q.y), v[qq][k], sa[k]);
+          sb[k] = ffma2(make_float2(q.z, q.w), v[qq][k], sb[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * KA; ++k) {
+      acc[r][k].x += sa[k].x - sb[k].y;
+      acc[r][k].y += sa[k].y + sb[k].x;
+    }
+  }
+}
+
+template <int NR, int PP, int KA>
+__device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double2* x,
+                                               const double2* coefS, int u0, int nrows, int pc,
+                                               int npairs, int dim_dn,
+                                               double2 (&acc)[NR][2 * PP]) {
+  using C = double2;
+  constexpr int T = kApplyThreads;
+  int pk[KA];
+#pragma unroll
+  for (int k = 0; k < KA; ++k) pk[k] = min(pc + (int)threadIdx.x + k * T, npairs - 1);
+  const uint4* ent4p = reinterpret_cast<const uint4*>(sd.up_pad_ent);
+  const uint4* row4p = reinterpret_cast<const uint4*>(sd.up_pad_row);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r >= nrows) continue;   // uniform over the block
+    const int u = u0 + r;
+    const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
+    if (e0 >= e1) continue;
+    C sum[2 * KA];
+#pragma unroll
+    for (int k = 0; k < 2 * KA; ++k) sum[k] = czero<C>();
+    uint4 nent = __ldg(ent4p + (e0 >> 2)), nrow = __ldg(row4p + (e0 >> 2));
+    uint32_t gcur = (nent.x >> kEntGroupShift) & 0xFFu;
+    for (int e = e0; e < e1; e += 4) {
+      const uint4 ent4 = nent, row4 = nrow;
+      if (e + 4 < e1) {   // the next batch's entries load under this batch's rows
+        nent = __ldg(ent4p + ((e + 4) >> 2));
+        nrow = __ldg(row4p + ((e + 4) >> 2));
+      }
+      const uint32_t ents[4] = {ent4.x, ent4.y, ent4.z, ent4.w};
+      const uint32_t rows[4] = {row4.x, row4.y, row4.z, row4.w};
+      C v[4][2 * KA];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+        for (int k = 0; k < KA; ++k)
+          load_pair<C, false>(x + rows[qq], pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        const uint32_t g = (ents[qq] >> kEntGroupShift) & 0xFFu;
+        if (g != gcur) {                              // uniform over the block
+          const C c = coefS[gcur];
+#pragma unroll
+          for (int k = 0; k < 2 * KA; ++k) {
+            cmac(acc[r][k], c, sum[k]);
+            sum[k] = czero<C>();
+          }
+          gcur = g;
+        }
+        const double sg = (ents[qq] & kNullEntryBit) ? 0.0 : sign_of<double>(ents[qq]);
+#pragma unroll
+        for (int k = 0; k < 2 * KA; ++k) cax(sum[k], sg, v[qq][k]);
+      }
+    }
+    const C c = coefS[gcur];
+#pragma unroll
+    for (int k = 0; k < 2 * KA; ++k) cmac(acc[r][k], c, sum[k]);
+  }
+}
+
+template <typename R, int NR, int PP, int KA, bool VEC>
+__device__ __forceinline__ void tup_chunk(const SectorDev& sd, const typename C2T<R>::T* x,
+                                          const typename C2T<R>::T* coefS, const float4* coefQ,
+                                          int u0, int nrows, int pc, int npairs, int dim_dn,
+                                          typename C2T<R>::T (&acc)[NR][2 * PP]) {
+  if constexpr (sizeof(R) == 4)
+    tup_chunk_c64<NR, PP, KA, VEC>(sd, x, coefQ, u0, nrows, pc, npairs, dim_dn, acc);
+  else
+    tup_chunk_c128<NR, PP, KA>(sd, x, coefS, u0, nrows, pc, npairs, dim_dn, acc);
+}
+
+// Shared-memory bytes in front of the TMA ring / end of the apply's dynamic
+// shared memory: the tile, the group coefficients, and for complex64 the
+// signed coefficient quads of the T_up gathers (16-byte aligned).
+__host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_groups, bool fp64) {
+  const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
+  size_t off = ((size_t)(max_dim_dn + kZeroCols) * nr + (size_t)n_groups) * csz;
+  if (!fp64) off = ((off + 15) & ~(size_t)15) + (size_t)(1 + 2 * n_groups) * sizeof(float4);
+  return off;
+}
+
 // One CTA (256 threads) processes NR consecutive rows u0..u0+NR-1 of one
 // vector.  The rows are staged in shared memory column by column (TileIO),
 // followed by eight zero columns that empty ELL slots read.  Thread t owns
@@ -404,13 +560,17 @@ k_apply(BatchArgs a, int j) {
 
   C* tile = reinterpret_cast<C*>(smem_raw);              // [max_dim_dn + kZeroCols][NR]
   C* coefS = tile + (size_t)(a.max_dim_dn + kZeroCols) * NR;   // [n_groups]
+  // complex64: signed coefficient quads of the T_up gathers, [1 + 2 n_groups]
+  float4* coefQ = reinterpret_cast<float4*>(
+      smem_raw + ((((size_t)(a.max_dim_dn + kZeroCols) * NR + (size_t)a.n_groups) * sizeof(C) + 15) &
+                  ~(size_t)15));
   // TMA configurations: ring of S row chunks (128-byte aligned after
   // the coefficients), then S full and S empty mbarriers
   char* ring = nullptr;
   uint64_t* full = nullptr;
   uint64_t* empty = nullptr;
   if constexpr (TMA) {
-    size_t off = ((size_t)(a.max_dim_dn + kZeroCols) * NR + (size_t)a.n_groups) * sizeof(C);
+    size_t off = apply_coef_end(a.max_dim_dn, NR, a.n_groups, sizeof(R) == 8);
     off = (off + 127) & ~(size_t)127;
     ring = reinterpret_cast<char*>(smem_raw) + off;
     full = reinterpret_cast<uint64_t*>(ring + (size_t)S * kSlotBytes);
@@ -431,6 +591,17 @@ k_apply(BatchArgs a, int j) {
   else if (j == 0) cbase = a.coefs;
   else cbase = static_cast<const char*>(a.coefs_obs) + (size_t)st->step * a.n_groups * sizeof(C);
   for (int g = tid; g < a.n_groups; g += T) coefS[g] = reinterpret_cast<const C*>(cbase)[g];
+  if constexpr (sizeof(R) == 4) {
+    for (int i = tid; i <= 2 * a.n_groups; i += T) {
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i > 0) {
+        const float2 c = reinterpret_cast<const float2*>(cbase)[(i - 1) >> 1];
+        const float sg = ((i - 1) & 1) ? -1.f : 1.f;
+        q = make_float4(sg * c.x, sg * c.x, sg * c.y, sg * c.y);
+      }
+      coefQ[i] = q;
+    }
+  }
 
   const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
   const C* xp = (j >= 2) ? static_cast<const C*>(xptr(vd, j - 1, sizeof(C))) : nullptr;
@@ -624,13 +795,8 @@ k_apply(BatchArgs a, int j) {
     }
     // per-thread pair bases of this chunk
     bool pvalid[PP];
-    const float4* xb4[PP];
 #pragma unroll
-    for (int k = 0; k < PP; ++k) {
-      const int p = pc + tid + k * T;
-      pvalid[k] = p < npairs;
-      xb4[k] = reinterpret_cast<const float4*>(x) + p;
-    }
+    for (int k = 0; k < PP; ++k) pvalid[k] = pc + tid + k * T < npairs;
     // ---- split apply: the column pass stored (T_up x) in w; add its rows
     if constexpr (SPLIT) {
       C tv[NR][2 * PP];
@@ -711,74 +877,13 @@ k_apply(BatchArgs a, int j) {
         }
       }
     }
-    // ---- T_up: the padded entry list of each row (uniform over the block),
-    // four entries per batch with all their row loads in flight, coefficient
-    // applied when the group changes
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (!SPLIT && !TMA && r < nrows) {
-        const int u = u0 + r;
-        const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
-        C sum[2 * PP];
-#pragma unroll
-        for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
-        uint32_t gcur = e0 < e1 ? ((__ldg(sd.up_pad_ent + e0) >> kEntGroupShift) & 0xFFu) : 0u;
-        uint4 nent = make_uint4(0u, 0u, 0u, 0u), nrow = nent;
-        if (e0 < e1) {
-          nent = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_ent + e0));
-          nrow = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_row + e0));
-        }
-        for (int e = e0; e < e1; e += 4) {
-          const uint4 ent4 = nent, row4 = nrow;
-          if (e + 4 < e1) {   // the next batch's entries load under this batch's rows
-            nent = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_ent + e + 4));
-            nrow = __ldg(reinterpret_cast<const uint4*>(sd.up_pad_row + e + 4));
-          }
-          const uint32_t ents[4] = {ent4.x, ent4.y, ent4.z, ent4.w};
-          const uint32_t rows[4] = {row4.x, row4.y, row4.z, row4.w};
-          C v[4][2 * PP];
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-#pragma unroll
-            for (int k = 0; k < PP; ++k) {
-              if constexpr (VEC) {
-                // rows are 16-byte aligned: one 16-byte load per pair at the
-                // per-thread pair base plus the source row's offset
-                if (pvalid[k]) {
-                  const float4 f = xb4[k][rows[qq] >> 1];
-                  v[qq][2 * k].x = f.x; v[qq][2 * k].y = f.y;
-                  v[qq][2 * k + 1].x = f.z; v[qq][2 * k + 1].y = f.w;
-                } else { v[qq][2 * k] = czero<C>(); v[qq][2 * k + 1] = czero<C>(); }
-              } else {
-                const int p = pc + tid + k * T;
-                if (pvalid[k]) load_pair<C, false>(x + rows[qq], p, dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
-                else { v[qq][2 * k] = czero<C>(); v[qq][2 * k + 1] = czero<C>(); }
-              }
-            }
-          }
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            const uint32_t g = (ents[qq] >> kEntGroupShift) & 0xFFu;
-            if (g != gcur) {                              // uniform over the block
-              const C c = coefS[gcur];
-#pragma unroll
-              for (int k = 0; k < 2 * PP; ++k) {
-                cmac(acc[r][k], c, sum[k]);
-                sum[k] = czero<C>();
-              }
-              gcur = g;
-            }
-            const R sg = (ents[qq] & kNullEntryBit) ? (R)0 : sign_of<R>(ents[qq]);
-#pragma unroll
-            for (int k = 0; k < 2 * PP; ++k) cax(sum[k], sg, v[qq][k]);
-          }
-        }
-        if (e0 < e1) {
-          const C c = coefS[gcur];
-#pragma unroll
-          for (int k = 0; k < 2 * PP; ++k) cmac(acc[r][k], c, sum[k]);
-        }
-      }
+    // ---- T_up: the padded entry lists of the rows (uniform over the block);
+    // versioned on how many column-pair groups of this chunk hold valid pairs
+    if constexpr (!SPLIT && !TMA) {
+      if (PP > 1 && pc + (PP - 1) * T < npairs)
+        tup_chunk<R, NR, PP, PP, VEC>(sd, x, coefS, coefQ, u0, nrows, pc, npairs, dim_dn, acc);
+      else
+        tup_chunk<R, NR, PP, 1, VEC>(sd, x, coefS, coefQ, u0, nrows, pc, npairs, dim_dn, acc);
     }
     // ---- epilogue: previous-vector loads first, then scale, subtract, store
     C pv[NR][2 * PP];
@@ -1780,7 +1885,7 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     sh.cb = c.cb;
     sh.tc = c.tc;
     sh.tma = c.tma > 0;
-    sh.smem = ((size_t)(max_dim_dn + kZeroCols) * c.nr + (size_t)n_groups) * csz;
+    sh.smem = apply_coef_end(max_dim_dn, c.nr, n_groups, fp64);
     if (c.tma)   // 128-byte aligned ring of row chunks + full/empty mbarriers
       sh.smem = ((sh.smem + 127) & ~(size_t)127) +
                 (size_t)c.tma * kApplyThreads * c.pp * 2 * csz + 2 * (size_t)c.tma * 8;
