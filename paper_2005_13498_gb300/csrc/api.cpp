@@ -431,6 +431,7 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     tt.n_groups = ng;
     tt.dim_up.assign(nvec, (int)ctx->dim_up);
     tt.dim_dn.assign(nvec, (int)ctx->dim_dn);
+    tt.up.assign(nvec, &ctx->sec.up);
     tt.args = P.args;
     std::vector<ApplyBlock> amap, cmap;
     CKS(ctx, tune_apply(tt, s, &P.shape, &amap, &cmap));
@@ -499,7 +500,8 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
     ctx->engine.reset(new Engine());
     cfg.n_steps_cap = std::max(cfg.n_steps_cap, 64);
     std::string err = ctx->engine->setup(cfg, {ctx->sec.dev}, vecs, 2 * ctx->lat.n_classes,
-                                         ctx->Ns, ctx->lat.U, fp64 ? 1e-13 : 1e-6, s);
+                                         ctx->Ns, ctx->lat.U, fp64 ? 1e-13 : 1e-6, s,
+                                         {&ctx->sec.up});
     if (!err.empty()) {
       ctx->engine.reset();
       return fail(ctx, err.find("memory") != std::string::npos ? ED_ERR_OOM : ED_ERR_CUDA, err);

@@ -138,6 +138,7 @@ std::string gs_apply_setup(GsApply& G, ed_ctx* ctx, const double2* x, double2* w
   tt.n_groups = ng;
   tt.dim_up = {(int)ctx->dim_up};
   tt.dim_dn = {(int)ctx->dim_dn};
+  tt.up = {&ctx->sec.up};
   tt.args = G.args;
   std::vector<ApplyBlock> amap, cmap;
   std::string err = tune_apply(tt, s, &G.shape, &amap, &cmap);
@@ -338,6 +339,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
                         {ctx->n_up + 1, ctx->n_dn}, {ctx->n_up, ctx->n_dn + 1}};
   int sector_of[4];
   std::vector<SectorDev> secs = {ctx->sec.dev};
+  std::vector<const SpinTable*> up_tabs = {&ctx->sec.up};
   if (ctx->spec_sectors.empty()) {
     for (int k = 0; k < 4; ++k) {
       std::unique_ptr<SectorGPU> S;
@@ -352,6 +354,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
     if (ctx->spec_sectors[k]) {
       sector_of[k] = (int)secs.size();
       secs.push_back(ctx->spec_sectors[k]->dev);
+      up_tabs.push_back(&ctx->spec_sectors[k]->up);
     } else {
       sector_of[k] = -1;
     }
@@ -391,7 +394,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
     ctx->spec_engine.reset(new Engine());
     cfg.n_steps_cap = std::max(cfg.n_steps_cap, 64);
     std::string err = ctx->spec_engine->setup(cfg, secs, vecs, 2 * ctx->lat.n_classes, Ns,
-                                              ctx->lat.U, fp64 ? 1e-13 : 1e-6, s);
+                                              ctx->lat.U, fp64 ? 1e-13 : 1e-6, s, up_tabs);
     if (!err.empty()) {
       ctx->spec_engine.reset();
       return fail(ctx, err.find("memory") != std::string::npos ? ED_ERR_OOM : ED_ERR_CUDA, err);

@@ -1,5 +1,6 @@
 // Batched midpoint-rule propagation engine (see engine.h).
 #include "engine.h"
+#include "tables.h"
 
 #include <algorithm>
 #include <cstring>
@@ -80,7 +81,12 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
     map->clear();
     cmap->clear();
     for (size_t i = 0; i < t.dim_up.size(); ++i) {
-      append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr);
+      if (i < t.up.size() && t.up[i] && t.up[i]->dim == t.dim_up[i]) {
+        for (int r0 : block_order(*t.up[i], sh.nr))
+          map->push_back({(int)i, r0, std::min(sh.nr, t.dim_up[i] - r0), 0});
+      } else {
+        append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr);
+      }
       if (sh.split) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64, sh.cb);
     }
   };
@@ -170,7 +176,8 @@ static int64_t ew_chunk(int64_t D) {
 
 std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>& sectors,
                           const std::vector<EngineVector>& vecs, int n_groups, int Ns,
-                          double U, double break_tol, cudaStream_t stream) {
+                          double U, double break_tol, cudaStream_t stream,
+                          const std::vector<const SpinTable*>& up_tabs) {
   if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
   if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
   cfg_ = cfg;
@@ -305,6 +312,8 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   for (int i = 0; i < nv; ++i) {
     tt.dim_up.push_back(sectors_[vecs_[i].sector].dim_up);
     tt.dim_dn.push_back(sectors_[vecs_[i].sector].dim_dn);
+    tt.up.push_back((size_t)vecs_[i].sector < up_tabs.size() ? up_tabs[vecs_[i].sector]
+                                                               : nullptr);
   }
   tt.args = args_;
   std::vector<ApplyBlock> cmap;

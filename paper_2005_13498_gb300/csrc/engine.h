@@ -20,6 +20,8 @@
 
 namespace ed {
 
+struct SpinTable;   // tables.h
+
 struct DevMem {
   void* p = nullptr;
   size_t bytes = 0;
@@ -57,6 +59,7 @@ struct ApplyTuneTarget {
   int n_groups = 0;
   std::vector<int> dim_up;      // per vector
   std::vector<int> dim_dn;      // per vector
+  std::vector<const SpinTable*> up;   // per vector: up-spin table (CTA order), or empty
   BatchArgs args{};             // vec / sec / coefs valid; the block maps are set here
 };
 // Process-wide choice of the apply configuration: -1 lets the autotuner pick
@@ -74,9 +77,11 @@ class Engine {
  public:
   ~Engine();
   // Allocate everything; sectors must stay alive while the engine exists.
+  // up_tabs (optional, one per sector) give the CTA order of the apply.
   std::string setup(const EngineConfig& cfg, const std::vector<SectorDev>& sectors,
                     const std::vector<EngineVector>& vecs, int n_groups, int Ns,
-                    double U, double break_tol, cudaStream_t stream);
+                    double U, double break_tol, cudaStream_t stream,
+                    const std::vector<const SpinTable*>& up_tabs = {});
   bool compatible(const EngineConfig& cfg, const std::vector<EngineVector>& vecs) const;
   int apply_config() const { return shape_.cfg; }
   // Upload per-step coefficients ([n_steps][n_groups] complex double; energy

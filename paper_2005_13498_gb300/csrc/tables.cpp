@@ -261,6 +261,52 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
   return T;
 }
 
+std::vector<int> block_order(const SpinTable& T, int nr) {
+  const int nb = nr > 0 ? (T.dim + nr - 1) / nr : 0;
+  std::vector<std::vector<int>> adj(nb);
+  for (int r = 0; r < T.dim; ++r)
+    for (int e = T.off[r]; e < T.off[r + 1]; ++e) {
+      const int b = r / nr, c = (int)(T.ent[e] & kEntRankMask) / nr;
+      if (b != c) {
+        adj[b].push_back(c);
+        adj[c].push_back(b);
+      }
+    }
+  std::vector<int> deg(nb);
+  for (int b = 0; b < nb; ++b) {
+    std::sort(adj[b].begin(), adj[b].end());
+    adj[b].erase(std::unique(adj[b].begin(), adj[b].end()), adj[b].end());
+    deg[b] = (int)adj[b].size();
+  }
+  // Cuthill-McKee: breadth-first from a block of least degree, neighbours
+  // visited by increasing degree; repeated for every connected component
+  std::vector<int> order;
+  order.reserve(nb);
+  std::vector<char> seen(nb, 0);
+  while ((int)order.size() < nb) {
+    int s0 = -1;
+    for (int b = 0; b < nb; ++b)
+      if (!seen[b] && (s0 < 0 || deg[b] < deg[s0])) s0 = b;
+    seen[s0] = 1;
+    size_t head = order.size();
+    order.push_back(s0);
+    while (head < order.size()) {
+      const int b = order[head++];
+      std::vector<int> nxt;
+      for (int c : adj[b])
+        if (!seen[c]) {
+          seen[c] = 1;
+          nxt.push_back(c);
+        }
+      std::stable_sort(nxt.begin(), nxt.end(), [&](int x, int y) { return deg[x] < deg[y]; });
+      order.insert(order.end(), nxt.begin(), nxt.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  for (int& b : order) b *= nr;
+  return order;
+}
+
 void group_coefficients(const LatticeHost& L, const double A[3], double* out) {
   for (int c = 0; c < L.n_classes; ++c) {
     const double phi = A[0] * L.class_d[3 * c] + A[1] * L.class_d[3 * c + 1] +

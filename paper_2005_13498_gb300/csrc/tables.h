@@ -81,6 +81,13 @@ struct SpinTable {
 };
 SpinTable build_spin_table(const LatticeHost& L, int n);
 
+// First rows of the blocks of nr consecutive rows of the target space of T
+// (the apply's CTAs), in reverse Cuthill-McKee order of the graph in which
+// two blocks are adjacent when a row of one has a source row in the other.
+// Launched in this order, the CTAs resident at one time gather from a
+// compact set of source rows (the working set the L2 must hold shrinks).
+std::vector<int> block_order(const SpinTable& T, int nr);
+
 // Per-group hopping coefficients for a vector potential A:
 //   group 2c   (hop p -> q of class c): -t_c exp(-i A.d_c)
 //   group 2c+1 (hop q -> p):            -t_c exp(+i A.d_c)
