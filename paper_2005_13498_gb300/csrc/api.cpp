@@ -61,22 +61,41 @@ cudaError_t upload_sector(SectorGPU& S) {
   }
   if ((e = upload(S.dn_tslot_off, S.dn.tslot_off)) != cudaSuccess) return e;
   if ((e = upload(S.dn_slot_grp, S.dn.slot_grp)) != cudaSuccess) return e;
-  if ((e = upload(S.dn_ell, S.dn.ell)) != cudaSuccess) return e;
   if ((e = upload(S.up_tslot_off, S.up.tslot_off)) != cudaSuccess) return e;
   if ((e = upload(S.up_slot_grp, S.up.slot_grp)) != cudaSuccess) return e;
   if ((e = upload(S.up_ell, S.up.ell)) != cudaSuccess) return e;
   {
-    // per-width copies: the byte offset of the source column (rank) in tiles
-    // of 16- and 8-byte columns, recovered from tile_offset = 32 rank + 16 sw
+    // 16-byte-column copy of the up ELL: the byte offset of the source
+    // (rank) in tiles of 16-byte columns, from tile_offset = 32 rank + 16 sw
     auto width_copy = [](const std::vector<uint32_t>& ell, uint32_t width) {
       std::vector<uint32_t> out(ell.size());
       for (size_t i = 0; i < ell.size(); ++i)
         out[i] = (((ell[i] & 0x7FFFFFFFu) >> 5) * width) | (ell[i] & 0x80000000u);
       return out;
     };
-    if ((e = upload(S.dn_ell16, width_copy(S.dn.ell, 16))) != cudaSuccess) return e;
-    if ((e = upload(S.dn_ell8, width_copy(S.dn.ell, 8))) != cudaSuccess) return e;
     if ((e = upload(S.up_ell16, width_copy(S.up.ell, 16))) != cudaSuccess) return e;
+    // packed copies of the down-spin ELL: lane words of two 15-bit column
+    // units (unit = byte offset / 16, or / 8 for 8-byte columns) and signs
+    auto packed_copy = [](const std::vector<uint32_t>& ell, int width, std::vector<uint32_t>* out) {
+      out->resize(ell.size() / 2);
+      for (size_t i = 0; i < out->size(); ++i) {
+        uint32_t u[2], sg[2];
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t en = ell[2 * i + h];
+          const uint32_t off = en & 0x7FFFFFFFu;          // 32 rank + 16 swizzle
+          u[h] = width == 32 ? off >> 4 : (off >> 5);
+          sg[h] = en >> 31;
+          if (u[h] > 0x7FFFu) return false;
+        }
+        (*out)[i] = u[0] | (sg[1] << 15) | (u[1] << 16) | (sg[0] << 31);
+      }
+      return true;
+    };
+    std::vector<uint32_t> pk;
+    if (!packed_copy(S.dn.ell, 32, &pk)) return cudaErrorInvalidValue;
+    if ((e = upload(S.dn_ellp32, pk)) != cudaSuccess) return e;
+    if (!packed_copy(S.dn.ell, 16, &pk)) return cudaErrorInvalidValue;   // units = rank
+    if ((e = upload(S.dn_ellpr, pk)) != cudaSuccess) return e;
   }
   if (S.has_eps) {
     if ((e = upload(S.up_eps, S.up.eps_sum)) != cudaSuccess) return e;
@@ -104,13 +123,12 @@ cudaError_t upload_sector(SectorGPU& S) {
   d.up_pad_cs = static_cast<const uint32_t*>(S.up_pad_cs.p);
   d.dn_tslot_off = static_cast<const int32_t*>(S.dn_tslot_off.p);
   d.dn_slot_grp = static_cast<const uint32_t*>(S.dn_slot_grp.p);
-  d.dn_ell = static_cast<const uint32_t*>(S.dn_ell.p);
   d.up_tslot_off = static_cast<const int32_t*>(S.up_tslot_off.p);
   d.up_slot_grp = static_cast<const uint32_t*>(S.up_slot_grp.p);
   d.up_ell = static_cast<const uint32_t*>(S.up_ell.p);
-  d.dn_ell16 = static_cast<const uint32_t*>(S.dn_ell16.p);
-  d.dn_ell8 = static_cast<const uint32_t*>(S.dn_ell8.p);
   d.up_ell16 = static_cast<const uint32_t*>(S.up_ell16.p);
+  d.dn_ellp32 = static_cast<const uint32_t*>(S.dn_ellp32.p);
+  d.dn_ellpr = static_cast<const uint32_t*>(S.dn_ellpr.p);
   S.uploaded = true;
   return cudaSuccess;
 }
@@ -311,8 +329,9 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
               S.up_word.bytes + S.dn_word.bytes + S.up_eps.bytes + S.dn_eps.bytes +
               S.up_pad_off.bytes + S.up_pad_ent.bytes + S.up_pad_row.bytes + S.up_pad_cs.bytes +
               S.dn_tslot_off.bytes +
-              S.dn_slot_grp.bytes + S.dn_ell.bytes + S.up_tslot_off.bytes + S.up_slot_grp.bytes +
-              S.up_ell.bytes + S.dn_ell16.bytes + S.dn_ell8.bytes + S.up_ell16.bytes;
+              S.dn_slot_grp.bytes + S.up_tslot_off.bytes + S.up_slot_grp.bytes +
+              S.up_ell.bytes + S.up_ell16.bytes +
+              S.dn_ellp32.bytes + S.dn_ellpr.bytes;
   if (ctx->engine) b += ctx->engine->device_bytes();
   if (ctx->spec_engine) b += ctx->spec_engine->device_bytes();
   *bytes = b;

@@ -39,18 +39,24 @@ struct SectorDev {
   const uint32_t* up_pad_ent;  // entries; bit 30 = null (contributes zero)
   const uint32_t* up_pad_row;  // element offset of the source row: rank * dim_dn
   const uint32_t* up_pad_cs;   // coefficient slot: 0 padding, else 1 + 2 group + sign
-  // down spin: warp-tiled ELL over 64-column tiles (within-row gathers)
+  // down spin: warp-tiled ELL over 64-column tiles (within-row gathers),
+  // slot lists as in SpinTable (tables.h)
   const int32_t* dn_tslot_off; // [ceil(dim_dn/64) + 1], even slot counts
   const uint32_t* dn_slot_grp; // group of each slot
-  const uint32_t* dn_ell;      // [slots][32 lanes][2]: tile_offset(rank) | sign << 31
-  // up spin, same layout over 64-row tiles (the column pass of the split apply)
+  // packed: one word per lane and slot [slots][32 lanes] with both entries
+  // of the lane as 15-bit column units and signs (bits 0-14 unit of the
+  // first column's entry, 15 sign of the second, 16-30 unit of the second,
+  // 31 sign of the first); units of 16 bytes in 32-byte tile columns
+  // (2 rank + swizzle bit), and in 16- and 8-byte columns the unit is the
+  // column width, so the units are the source ranks
+  const uint32_t* dn_ellp32;
+  const uint32_t* dn_ellpr;
+  // up spin, same tiling over 64-row tiles (the column pass of the split
+  // apply), entries tile_offset(rank) | sign << 31 for 32-byte tile columns
+  // and 16 rank | sign << 31 for 16-byte ones
   const int32_t* up_tslot_off;
   const uint32_t* up_slot_grp;
   const uint32_t* up_ell;
-  // the same ELL entries with the byte offset of the source column in tiles
-  // of 16-byte and 8-byte columns (16 rank, 8 rank) instead of tile_offset
-  const uint32_t* dn_ell16;
-  const uint32_t* dn_ell8;
   const uint32_t* up_ell16;
 };
 

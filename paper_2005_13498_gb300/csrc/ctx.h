@@ -18,8 +18,9 @@ struct SectorGPU {
   int Ns = 0, n_up = 0, n_dn = 0;
   SpinTable up, dn;
   DevMem up_off, up_ent, dn_off, dn_ent, up_word, dn_word, up_eps, dn_eps;
-  DevMem up_pad_off, up_pad_ent, up_pad_row, up_pad_cs, dn_tslot_off, dn_slot_grp, dn_ell;
-  DevMem up_tslot_off, up_slot_grp, up_ell, dn_ell16, dn_ell8, up_ell16;
+  DevMem up_pad_off, up_pad_ent, up_pad_row, up_pad_cs, dn_tslot_off, dn_slot_grp;
+  DevMem up_tslot_off, up_slot_grp, up_ell, up_ell16;
+  DevMem dn_ellp32, dn_ellpr;
   SectorDev dev{};
   bool has_eps = false;
   bool uploaded = false;

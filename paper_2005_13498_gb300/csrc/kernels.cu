@@ -324,6 +324,31 @@ struct TileIO {
       load(tile, (int)(off >> 5), v);
     }
   }
+  // load by a byte offset: of the column (of its first chunk for 32-byte
+  // columns, whose second chunk is at offset ^ 16)
+  __device__ static __forceinline__ void load_off(const C* tile, uint32_t off, C (&v)[NR]) {
+    load_ent(tile, off, v);
+  }
+  // packed ELL word of one lane and slot: bits 0-14 the column unit of the
+  // lane's first column's entry, bit 15 the sign of the second, bits 16-30
+  // the unit of the second, bit 31 the sign of the first; a unit is 8 bytes
+  // for 8-byte columns and 16 bytes otherwise (only 8-, 16- and 32-byte
+  // columns occur in the configuration table)
+  static_assert(kBytes == 8 || kBytes == 16 || kBytes == 32, "packed ELL column widths");
+  static constexpr int kUnitShift = kBytes == 8 ? 3 : 4;
+  template <typename R>
+  __device__ static __forceinline__ void unpack(uint32_t e, uint32_t& off0, uint32_t& off1,
+                                                R& g0, R& g1) {
+    off0 = (e & 0x7FFFu) << kUnitShift;
+    off1 = ((e >> 16) & 0x7FFFu) << kUnitShift;
+    g0 = sign_of<R>(e);
+    g1 = sign_of<R>(e << 16);
+  }
+  __device__ static __forceinline__ const uint32_t* ellp_for(const uint32_t* p32,
+                                                             const uint32_t* prank) {
+    if constexpr (kBytes == 32) return p32;
+    else return prank;
+  }
   // the ELL copy whose entries hold byte offsets for this column width
   __device__ static __forceinline__ const uint32_t* ell_for(const uint32_t* ell32,
                                                             const uint32_t* ell16,
@@ -407,7 +432,7 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2*
 #pragma unroll
         for (int k = 0; k < KA; ++k) {
           if constexpr (VEC) {
-            const float4 f = reinterpret_cast<const float4*>(src)[pk[k]];
+            const float4 f = __ldcg(reinterpret_cast<const float4*>(src) + pk[k]);
             v[qq][2 * k] = make_float2(f.x, f.y);
             v[qq][2 * k + 1] = make_float2(f.z, f.w);
           } else {
@@ -519,7 +544,6 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
 // followed by eight zero columns that empty ELL slots read.  Thread t owns
 // the column pairs p = pc + t + k*256 (k < PP) of every chunk pc, so a warp
 // covers 64 consecutive columns.
-//  * Diagonal: U * popcount(up & dn) (+ on-site energies).
 //  * T_dn (within a row): the warp walks the flat slot list of its 64-column
 //    ELL tile (slots grouped by bond group, trip count uniform over the
 //    warp), each lane loading the two entries of its columns per slot and
@@ -528,9 +552,10 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
 //    coefficient once.
 //  * T_up (across rows): the padded entry list of row u is uniform over the
 //    block; four entries at a time, each a coalesced pair load of the source
-//    row per k, all in flight before they are summed by group.
-//  * Epilogue: w = s_j acc - beta_{j-1} s_{j-1} x_{j-1}, stored in pairs,
-//    and the partial of Re<x_j, w>.
+//    row per k, all in flight before they are used (tup_chunk).
+//  * Epilogue: the diagonal U * popcount(up & dn) (+ on-site energies) times
+//    the staged x joins the sums, w = s_j acc - beta_{j-1} s_{j-1} x_{j-1} is
+//    stored in pairs, and the partial of Re<x_j, w> is accumulated.
 template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS>
 __global__ void __launch_bounds__(TMAS ? kApplyThreads + 32 : kApplyThreads, MINB)
 k_apply(BatchArgs a, int j) {
@@ -610,40 +635,22 @@ k_apply(BatchArgs a, int j) {
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
 
-  // ---- stage the NR rows column by column (pairs of columns per thread,
-  // all NR row loads of two pairs in flight), plus the zero pair past the end
+  // ---- stage the NR rows column by column, one column per thread and
+  // iteration (consecutive lanes write consecutive tile columns: no bank
+  // conflicts in any TileIO layout), four columns' loads in flight; the
+  // columns dim_dn .. dim_dn + 7 are the zero columns empty ELL slots read.
+  // The staged rows and the T_up row gathers are read through L2 only
+  // (ld.global.cg), which leaves the L1 to the ELL entries.
   if (!TMA || tid < T) {
-    const int np2 = npairs + 1;   // one extra pair: the zero columns
-#pragma unroll 2
-    for (int p = tid; p < np2; p += T) {
-      C va[NR], vb[NR];
+    const int ncol = dim_dn + kZeroCols;
+#pragma unroll 4
+    for (int d = tid; d < ncol; d += T) {
+      C v[NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r < nrows && p < npairs) {
-          load_pair<C, VEC>(x + (size_t)(u0 + r) * dim_dn, p, dim_dn, va[r], vb[r]);
-        } else {
-          va[r] = czero<C>();
-          vb[r] = czero<C>();
-        }
-      }
-      int d = 2 * p;
-      if (p == npairs) d = dim_dn;              // zero columns dim_dn, dim_dn + 1
-      TIO::store(tile, d, va);
-      TIO::store(tile, d + 1, (p < npairs && 2 * p + 1 < dim_dn) ? vb : va);
-      if (p < npairs && 2 * p + 1 >= dim_dn) {  // odd dim: the pair's 2nd column is dim_dn
-        C z[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) z[r] = czero<C>();
-        TIO::store(tile, d + 1, z);
-      }
+      for (int r = 0; r < NR; ++r)
+        v[r] = (r < nrows && d < dim_dn) ? __ldcg(x + (size_t)(u0 + r) * dim_dn + d) : czero<C>();
+      TIO::store(tile, d, v);
     }
-  }
-  // zero columns dim_dn .. dim_dn + 7 that empty ELL slots read
-  if (tid < kZeroCols) {
-    C z[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) z[r] = czero<C>();
-    TIO::store(tile, dim_dn + tid, z);
   }
   uint32_t uw[NR];
   R eu[NR];
@@ -698,71 +705,57 @@ k_apply(BatchArgs a, int j) {
     }
   } else
   for (int pc = 0; pc < npairs; pc += T * PP) {
-    C acc[NR][2 * PP];
-    // ---- diagonal
+    C acc[NR][2 * PP];   // off-diagonal sums; the diagonal joins in the epilogue
 #pragma unroll
-    for (int k = 0; k < PP; ++k) {
+    for (int r = 0; r < NR; ++r)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int d = 2 * (pc + tid + k * T) + h;
-        if (d < dim_dn) {
-          const uint32_t dw = __ldg(sd.dn_word + d);
-          const R de = sd.dn_eps ? (R)__ldg(sd.dn_eps + d) : (R)0;
-          C xv[NR];
-          TIO::load(tile, d, xv);
-#pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            const R dg = U * (R)__popc(uw[r] & dw) + eu[r] + de;
-            acc[r][2 * k + h].x = dg * xv[r].x;
-            acc[r][2 * k + h].y = dg * xv[r].y;
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < NR; ++r) acc[r][2 * k + h] = czero<C>();
-        }
-      }
-    }
+      for (int k = 0; k < 2 * PP; ++k) acc[r][k] = czero<C>();
     // ---- T_dn through the 64-column ELL tiles: flat slot list (grouped by
     // bond group, uniform over the warp), two slots of entries and their
-    // tile gathers in flight, coefficient applied when the group changes
+    // tile gathers in flight, coefficient applied when the group changes.
+    // One 32-bit word per lane and slot packs the lane's two entries as
+    // 15-bit column units plus sign bits (TileIO::unpack); the slot groups
+    // are read two at a time (tiles hold even slot counts)
 #pragma unroll
     for (int k = 0; k < PP; ++k) {
       const int pw0 = pc + (tid - lane) + k * T;     // first pair of the warp
       if (pw0 < npairs) {                             // uniform over the warp
         const int tw = pw0 >> 5;
         const int q0 = __ldg(sd.dn_tslot_off + tw), q1 = __ldg(sd.dn_tslot_off + tw + 1);
-        const uint2* ell2 =
-            reinterpret_cast<const uint2*>(TIO::ell_for(sd.dn_ell, sd.dn_ell16, sd.dn_ell8));
+        const uint32_t* ellp = TIO::ellp_for(sd.dn_ellp32, sd.dn_ellpr) + lane;
+        const uint2* grp2 = reinterpret_cast<const uint2*>(sd.dn_slot_grp);
         C s0v[NR], s1v[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) { s0v[r] = czero<C>(); s1v[r] = czero<C>(); }
-        uint32_t gcur = q0 < q1 ? __ldg(sd.dn_slot_grp + q0) : 0u;
         // entries of the next two slots are loaded while this pair is gathered
-        uint2 na = make_uint2(0u, 0u), nb = na;
-        uint32_t nga = 0u, ngb = 0u;
+        uint32_t na = 0u, nb = 0u;
+        uint2 ng = make_uint2(0u, 0u);
         if (q0 < q1) {
-          na = __ldg(ell2 + (size_t)q0 * 32 + lane);
-          nb = __ldg(ell2 + (size_t)(q0 + 1) * 32 + lane);
-          nga = __ldg(sd.dn_slot_grp + q0);
-          ngb = __ldg(sd.dn_slot_grp + q0 + 1);
+          na = __ldg(ellp + (size_t)q0 * 32);
+          nb = __ldg(ellp + (size_t)(q0 + 1) * 32);
+          ng = __ldg(grp2 + (q0 >> 1));
         }
+        uint32_t gcur = ng.x;
         for (int q = q0; q < q1; q += 2) {
-          const uint2 ea = na, eb = nb;
-          const uint32_t ga = nga, gb = ngb;
+          const uint32_t ea = na, eb = nb;
+          const uint2 gg = ng;
           if (q + 2 < q1) {
-            na = __ldg(ell2 + (size_t)(q + 2) * 32 + lane);
-            nb = __ldg(ell2 + (size_t)(q + 3) * 32 + lane);
-            nga = __ldg(sd.dn_slot_grp + q + 2);
-            ngb = __ldg(sd.dn_slot_grp + q + 3);
+            na = __ldg(ellp + (size_t)(q + 2) * 32);
+            nb = __ldg(ellp + (size_t)(q + 3) * 32);
+            ng = __ldg(grp2 + ((q + 2) >> 1));
           }
+          uint32_t oa0, oa1, ob0, ob1;
+          R ga0, ga1, gb0, gb1;
+          TIO::template unpack<R>(ea, oa0, oa1, ga0, ga1);
+          TIO::template unpack<R>(eb, ob0, ob1, gb0, gb1);
           C a0[NR], a1[NR], b0[NR], b1[NR];
-          TIO::load_ent(tile, ea.x, a0);
-          TIO::load_ent(tile, ea.y, a1);
-          TIO::load_ent(tile, eb.x, b0);
-          TIO::load_ent(tile, eb.y, b1);
+          TIO::load_off(tile, oa0, a0);
+          TIO::load_off(tile, oa1, a1);
+          TIO::load_off(tile, ob0, b0);
+          TIO::load_off(tile, ob1, b1);
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
-            const uint32_t g = half ? gb : ga;
+            const uint32_t g = half ? gg.y : gg.x;
             if (g != gcur) {                            // uniform over the warp
               const C c = coefS[gcur];
 #pragma unroll
@@ -774,8 +767,7 @@ k_apply(BatchArgs a, int j) {
               }
               gcur = g;
             }
-            const uint2 e = half ? eb : ea;
-            const R g0 = sign_of<R>(e.x), g1 = sign_of<R>(e.y);
+            const R g0 = half ? gb0 : ga0, g1 = half ? gb1 : ga1;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
               cax(s0v[r], g0, half ? b0[r] : a0[r]);
@@ -902,17 +894,31 @@ k_apply(BatchArgs a, int j) {
     for (int k = 0; k < PP; ++k) {
       const int p = pc + tid + k * T;
       if (p < npairs) {
+        // diagonal U popcount(up & dn) + eps of the pair's two columns
+        const int d0 = 2 * p;
+        const bool has1 = d0 + 1 < dim_dn;
+        const uint32_t dw0 = __ldg(sd.dn_word + d0);
+        const uint32_t dw1 = has1 ? __ldg(sd.dn_word + d0 + 1) : 0u;
+        const R de0 = sd.dn_eps ? (R)__ldg(sd.dn_eps + d0) : (R)0;
+        const R de1 = (sd.dn_eps && has1) ? (R)__ldg(sd.dn_eps + d0 + 1) : (R)0;
         C xa[NR], xb[NR];
-        TIO::load(tile, 2 * p, xa);
-        TIO::load(tile, 2 * p + 1, xb);    // zero column past the end
+        TIO::load(tile, d0, xa);
+        TIO::load(tile, d0 + 1, xb);    // zero column past the end
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (r < nrows) {
+            const R g0 = U * (R)__popc(uw[r] & dw0) + eu[r] + de0;
+            const R g1 = U * (R)__popc(uw[r] & dw1) + eu[r] + de1;
+            C a0 = acc[r][2 * k], a1 = acc[r][2 * k + 1];
+            a0.x += g0 * xa[r].x;
+            a0.y += g0 * xa[r].y;
+            a1.x += g1 * xb[r].x;
+            a1.y += g1 * xb[r].y;
             C o0, o1;
-            o0.x = s_in * acc[r][2 * k].x - s_prev * pv[r][2 * k].x;
-            o0.y = s_in * acc[r][2 * k].y - s_prev * pv[r][2 * k].y;
-            o1.x = s_in * acc[r][2 * k + 1].x - s_prev * pv[r][2 * k + 1].x;
-            o1.y = s_in * acc[r][2 * k + 1].y - s_prev * pv[r][2 * k + 1].y;
+            o0.x = s_in * a0.x - s_prev * pv[r][2 * k].x;
+            o0.y = s_in * a0.y - s_prev * pv[r][2 * k].y;
+            o1.x = s_in * a1.x - s_prev * pv[r][2 * k + 1].x;
+            o1.y = s_in * a1.y - s_prev * pv[r][2 * k + 1].y;
             store_pair<C, VEC, true>(w + (size_t)(u0 + r) * dim_dn, p, dim_dn, o0, o1);
             dot_acc += xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
           }
