@@ -715,7 +715,9 @@ k_apply(BatchArgs a, int j) {
     // tile gathers in flight, coefficient applied when the group changes.
     // One 32-bit word per lane and slot packs the lane's two entries as
     // 15-bit column units plus sign bits (TileIO::unpack); the slot groups
-    // are read two at a time (tiles hold even slot counts)
+    // are read two at a time (tiles hold even slot counts).  The entries are
+    // loaded two iterations (four slots) ahead of their gathers: the ELL
+    // does not stay in L1, and its L2 latency was the exposed one
 #pragma unroll
     for (int k = 0; k < PP; ++k) {
       const int pw0 = pc + (tid - lane) + k * T;     // first pair of the warp
@@ -727,22 +729,27 @@ k_apply(BatchArgs a, int j) {
         C s0v[NR], s1v[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) { s0v[r] = czero<C>(); s1v[r] = czero<C>(); }
-        // entries of the next two slots are loaded while this pair is gathered
-        uint32_t na = 0u, nb = 0u;
-        uint2 ng = make_uint2(0u, 0u);
+        uint32_t na = 0u, nb = 0u, nc = 0u, nd = 0u;
+        uint2 ng = make_uint2(0u, 0u), nh = ng;
         if (q0 < q1) {
           na = __ldg(ellp + (size_t)q0 * 32);
           nb = __ldg(ellp + (size_t)(q0 + 1) * 32);
           ng = __ldg(grp2 + (q0 >> 1));
         }
+        if (q0 + 2 < q1) {
+          nc = __ldg(ellp + (size_t)(q0 + 2) * 32);
+          nd = __ldg(ellp + (size_t)(q0 + 3) * 32);
+          nh = __ldg(grp2 + ((q0 + 2) >> 1));
+        }
         uint32_t gcur = ng.x;
         for (int q = q0; q < q1; q += 2) {
           const uint32_t ea = na, eb = nb;
           const uint2 gg = ng;
-          if (q + 2 < q1) {
-            na = __ldg(ellp + (size_t)(q + 2) * 32);
-            nb = __ldg(ellp + (size_t)(q + 3) * 32);
-            ng = __ldg(grp2 + ((q + 2) >> 1));
+          na = nc; nb = nd; ng = nh;
+          if (q + 4 < q1) {
+            nc = __ldg(ellp + (size_t)(q + 4) * 32);
+            nd = __ldg(ellp + (size_t)(q + 5) * 32);
+            nh = __ldg(grp2 + ((q + 4) >> 1));
           }
           uint32_t oa0, oa1, ob0, ob1;
           R ga0, ga1, gb0, gb1;
