@@ -262,7 +262,7 @@ def profiled_traffic(apply_config):
     if not (want and val and cfg) or int(cfg.group(1)) != apply_config:
         return None
     h = hashlib.sha256()
-    for f in ("kernels.cu", "tables.cpp"):
+    for f in ("kernels.cu", "tables.cpp", "engine.cpp"):
         h.update(open(os.path.join(ROOT, "paper_2005_13498_gb300", "csrc", f), "rb").read())
     return int(val.group(1)) if h.hexdigest() == want.group(1) else None
 
