@@ -115,13 +115,15 @@ struct EwBlock {
   int64_t begin, end;
 };
 
-// Apply block: rows [row0, row0 + nrows) of vector vec (for the column pass
-// of the split apply: columns [row0, row0 + nrows)).
+// Apply block: the nrows (<= 4) rows row[0..nrows) of vector vec, not
+// necessarily consecutive (row0 = row[0]); for the column pass of the split
+// apply: columns [row0, row0 + nrows).
 struct ApplyBlock {
   int vec;
   int row0;
   int nrows;
   int pad;
+  int row[4];
 };
 
 // Everything the batched kernels need, passed by value.

@@ -82,8 +82,8 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
     cmap->clear();
     for (size_t i = 0; i < t.dim_up.size(); ++i) {
       if (i < t.up.size() && t.up[i] && t.up[i]->dim == t.dim_up[i]) {
-        for (int r0 : block_order(*t.up[i], sh.nr))
-          map->push_back({(int)i, r0, std::min(sh.nr, t.dim_up[i] - r0), 0});
+        const std::vector<int> rows = block_order(*t.up[i], 1);
+        append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr, &rows);
       } else {
         append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr);
       }

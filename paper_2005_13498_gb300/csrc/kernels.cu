@@ -155,18 +155,7 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 // ------------------------------------------------------------------- apply
 // j >= 1: Lanczos pass j; j == 0: plain apply (coefs row 0, x1 -> w);
 // j == -1: energy of x1 with coefs_obs[step].
-// One CTA processes NR consecutive rows u0..u0+NR-1 of one vector.  The rows
-// are staged in shared memory transposed, tile[d*NR + r], with one extra zero
-// column (index dim_dn) that padding entries point to.  Threads own columns
-// d = c0 + tid + k*blockDim (k < CPT) of every chunk c0, so the 32 lanes of a
-// warp cover one aligned tile of 32 columns.
-//  * T_dn (within a row) walks the warp-tiled ELL of the down table: for each
-//    bond group the 32 lanes read one coalesced slot of entries at a time (the
-//    trip count is uniform over the warp), gather the NR row values of the
-//    source column from the tile, sum them with their signs and multiply by
-//    the group coefficient once.
-//  * T_up (across rows) walks the group segments of row u, uniform over the
-//    block; each entry is a coalesced load of the source row along d.
+// (The apply kernel and its phases are described at k_apply below.)
 constexpr int kApplyThreads = 256;
 
 // ---- TMA pipeline for the T_up row segments (TMA apply configurations).
@@ -399,7 +388,8 @@ struct TileIO {
 //    by c_g once per group.
 template <int NR, int PP, int KA, bool VEC>
 __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2* x,
-                                              const float4* coefQ, int u0, int nrows, int pc,
+                                              const float4* coefQ, const int (&urow)[NR],
+                                              int nrows, int pc,
                                               int npairs, int dim_dn, float2 (&acc)[NR][2 * PP]) {
   constexpr int T = kApplyThreads;
   int pk[KA];
@@ -410,7 +400,7 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2*
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     if (r >= nrows) continue;   // uniform over the block
-    const int u = u0 + r;
+    const int u = urow[r];
     const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
     if (e0 >= e1) continue;
     float2 sa[2 * KA], sb[2 * KA];
@@ -460,7 +450,8 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2*
 
 template <int NR, int PP, int KA>
 __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double2* x,
-                                               const double2* coefS, int u0, int nrows, int pc,
+                                               const double2* coefS, const int (&urow)[NR],
+                                               int nrows, int pc,
                                                int npairs, int dim_dn,
                                                double2 (&acc)[NR][2 * PP]) {
   using C = double2;
@@ -473,7 +464,7 @@ __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     if (r >= nrows) continue;   // uniform over the block
-    const int u = u0 + r;
+    const int u = urow[r];
     const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
     if (e0 >= e1) continue;
     C sum[2 * KA];
@@ -521,12 +512,13 @@ __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double
 template <typename R, int NR, int PP, int KA, bool VEC>
 __device__ __forceinline__ void tup_chunk(const SectorDev& sd, const typename C2T<R>::T* x,
                                           const typename C2T<R>::T* coefS, const float4* coefQ,
-                                          int u0, int nrows, int pc, int npairs, int dim_dn,
+                                          const int (&urow)[NR], int nrows, int pc, int npairs,
+                                          int dim_dn,
                                           typename C2T<R>::T (&acc)[NR][2 * PP]) {
   if constexpr (sizeof(R) == 4)
-    tup_chunk_c64<NR, PP, KA, VEC>(sd, x, coefQ, u0, nrows, pc, npairs, dim_dn, acc);
+    tup_chunk_c64<NR, PP, KA, VEC>(sd, x, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
   else
-    tup_chunk_c128<NR, PP, KA>(sd, x, coefS, u0, nrows, pc, npairs, dim_dn, acc);
+    tup_chunk_c128<NR, PP, KA>(sd, x, coefS, urow, nrows, pc, npairs, dim_dn, acc);
 }
 
 // Shared-memory bytes in front of the TMA ring / end of the apply's dynamic
@@ -539,8 +531,9 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
   return off;
 }
 
-// One CTA (256 threads) processes NR consecutive rows u0..u0+NR-1 of one
-// vector.  The rows are staged in shared memory column by column (TileIO),
+// One CTA (256 threads) processes NR rows of one vector, the rows of its
+// ApplyBlock (consecutive entries of the block order the host chose).  The
+// rows are staged in shared memory column by column (TileIO),
 // followed by eight zero columns that empty ELL slots read.  Thread t owns
 // the column pairs p = pc + t + k*256 (k < PP) of every chunk pc, so a warp
 // covers 64 consecutive columns.
@@ -578,8 +571,10 @@ k_apply(BatchArgs a, int j) {
   const SectorDev sd = a.sec[vd.sector];
   const int dim_dn = sd.dim_dn;
   const int npairs = (dim_dn + 1) >> 1;
-  const int u0 = ab.row0;
   const int nrows = ab.nrows;
+  int urow[NR];   // the block's rows (padding slots repeat the first row)
+#pragma unroll
+  for (int r = 0; r < NR; ++r) urow[r] = r < nrows ? ab.row[r] : ab.row[0];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
@@ -648,7 +643,7 @@ k_apply(BatchArgs a, int j) {
       C v[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r)
-        v[r] = (r < nrows && d < dim_dn) ? __ldcg(x + (size_t)(u0 + r) * dim_dn + d) : czero<C>();
+        v[r] = (r < nrows && d < dim_dn) ? __ldcg(x + (size_t)urow[r] * dim_dn + d) : czero<C>();
       TIO::store(tile, d, v);
     }
   }
@@ -656,7 +651,7 @@ k_apply(BatchArgs a, int j) {
   R eu[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
-    const int u = r < nrows ? u0 + r : u0;
+    const int u = urow[r];
     uw[r] = __ldg(sd.up_word + u);
     eu[r] = sd.up_eps ? (R)__ldg(sd.up_eps + u) : (R)0;
   }
@@ -676,7 +671,7 @@ k_apply(BatchArgs a, int j) {
           const int np_chunk = min(T * PP, npairs - pc);
           const uint32_t bytes = (uint32_t)np_chunk * 2u * (uint32_t)sizeof(C);
           for (int r = 0; r < nrows && ok; ++r) {
-            const int e0 = __ldg(sd.up_off + u0 + r), e1 = __ldg(sd.up_off + u0 + r + 1);
+            const int e0 = __ldg(sd.up_off + urow[r]), e1 = __ldg(sd.up_off + urow[r] + 1);
             for (int e = e0; e < e1; ++e, ++idx) {
               const uint32_t q = idx % S;
               if (idx >= (uint32_t)S &&
@@ -804,7 +799,7 @@ k_apply(BatchArgs a, int j) {
 #pragma unroll
         for (int k = 0; k < PP; ++k) {
           if (r < nrows && pvalid[k])
-            load_pair<C, VEC, true>(w + (size_t)(u0 + r) * dim_dn, pc + tid + k * T, dim_dn,
+            load_pair<C, VEC, true>(w + (size_t)urow[r] * dim_dn, pc + tid + k * T, dim_dn,
                                     tv[r][2 * k], tv[r][2 * k + 1]);
           else { tv[r][2 * k] = czero<C>(); tv[r][2 * k + 1] = czero<C>(); }
         }
@@ -823,7 +818,7 @@ k_apply(BatchArgs a, int j) {
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (r < nrows) {
-          const int e0 = __ldg(sd.up_off + u0 + r), e1 = __ldg(sd.up_off + u0 + r + 1);
+          const int e0 = __ldg(sd.up_off + urow[r]), e1 = __ldg(sd.up_off + urow[r] + 1);
           C sum[2 * PP];
 #pragma unroll
           for (int k = 0; k < 2 * PP; ++k) sum[k] = czero<C>();
@@ -880,9 +875,9 @@ k_apply(BatchArgs a, int j) {
     // versioned on how many column-pair groups of this chunk hold valid pairs
     if constexpr (!SPLIT && !TMA) {
       if (PP > 1 && pc + (PP - 1) * T < npairs)
-        tup_chunk<R, NR, PP, PP, VEC>(sd, x, coefS, coefQ, u0, nrows, pc, npairs, dim_dn, acc);
+        tup_chunk<R, NR, PP, PP, VEC>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
       else
-        tup_chunk<R, NR, PP, 1, VEC>(sd, x, coefS, coefQ, u0, nrows, pc, npairs, dim_dn, acc);
+        tup_chunk<R, NR, PP, 1, VEC>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
     }
     // ---- epilogue: previous-vector loads first, then scale, subtract, store
     C pv[NR][2 * PP];
@@ -892,7 +887,7 @@ k_apply(BatchArgs a, int j) {
       for (int k = 0; k < PP; ++k) {
         const int p = pc + tid + k * T;
         if (xp && r < nrows && p < npairs)
-          load_pair<C, VEC, true>(xp + (size_t)(u0 + r) * dim_dn, p, dim_dn, pv[r][2 * k],
+          load_pair<C, VEC, true>(xp + (size_t)urow[r] * dim_dn, p, dim_dn, pv[r][2 * k],
                                   pv[r][2 * k + 1]);
         else { pv[r][2 * k] = czero<C>(); pv[r][2 * k + 1] = czero<C>(); }
       }
@@ -926,7 +921,7 @@ k_apply(BatchArgs a, int j) {
             o0.y = s_in * a0.y - s_prev * pv[r][2 * k].y;
             o1.x = s_in * a1.x - s_prev * pv[r][2 * k + 1].x;
             o1.y = s_in * a1.y - s_prev * pv[r][2 * k + 1].y;
-            store_pair<C, VEC, true>(w + (size_t)(u0 + r) * dim_dn, p, dim_dn, o0, o1);
+            store_pair<C, VEC, true>(w + (size_t)urow[r] * dim_dn, p, dim_dn, o0, o1);
             dot_acc += xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
           }
         }

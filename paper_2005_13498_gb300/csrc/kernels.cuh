@@ -39,10 +39,17 @@ inline void append_col_blocks(std::vector<ApplyBlock>& map, int vec, int dim_dn,
     map.push_back({vec, d, dim_dn - d < nc ? dim_dn - d : nc, 0});
 }
 
-// Apply blocks of nr rows covering rows [0, dim_up) of vector vec.
-inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_up, int nr) {
-  for (int r = 0; r < dim_up; r += nr)
-    map.push_back({vec, r, dim_up - r < nr ? dim_up - r : nr, 0});
+// Apply blocks of nr <= 4 rows covering rows [0, dim_up) of vector vec:
+// consecutive rows in the order given (all rows once), or in natural order
+// when order is null.
+inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_up, int nr,
+                                const std::vector<int>* order = nullptr) {
+  for (int i = 0; i < dim_up; i += nr) {
+    ApplyBlock b{vec, 0, dim_up - i < nr ? dim_up - i : nr, 0, {0, 0, 0, 0}};
+    for (int r = 0; r < b.nrows; ++r) b.row[r] = order ? (*order)[i + r] : i + r;
+    b.row0 = b.row[0];
+    map.push_back(b);
+  }
 }
 
 // The configuration table: its size, and the precision, rows per CTA, pairs
