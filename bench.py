@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--spectral-steps", type=int, default=2)
     ap.add_argument("--apply-only", choices=["c64", "c128"], default=None,
                     help="run 4 plain applies at the bench size and exit (profiler target)")
+    ap.add_argument("--apply-workload", default=WORKLOAD,
+                    help="workload of --apply-only (default: the bench's ladder)")
     return ap.parse_args()
 
 
@@ -534,6 +536,9 @@ def main():
     if args.apply_config is not None:
         ed.ed_set_apply_config(args.apply_config)
     if args.apply_only:
+        if args.apply_workload != WORKLOAD:
+            w = synth.workload(args.apply_workload)
+            lat = synth.lattice_from_name(w["lattice"])
         h = ed.Hubbard(lat, w["n_up"], w["n_dn"], w["U"])
         ed.ed_set_field(h.ctx, [0.3, 0.0, 0.0])
         tt, code = ((torch.complex64, ed.ED_C64) if args.apply_only == "c64"

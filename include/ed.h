@@ -312,8 +312,10 @@ ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme);
  * entry of the library's table fixes the precision, the rows of Psi one
  * thread block owns (rows_per_cta), the column pairs per thread, the target
  * thread blocks per SM, and whether the product runs as one kernel (split =
- * 0: the T_up rows are gathered across the matrix) or as a column pass for
- * T_up followed by a row pass for the diagonal and T_dn (split = 1), and
+ * 0: the T_up rows are gathered across the matrix) or as a T_up pass
+ * followed by a row pass for the diagonal and T_dn (split = 1; the T_up pass
+ * either stages column blocks of all rows in shared memory or gathers rows
+ * one chunk of columns at a time, for vectors larger than the L2), and
  * whether an extra producer warp stages the T_up source-row chunks in shared
  * memory with TMA bulk copies (tma = 1; used only for even dim_dn and
  * 16-byte aligned vectors).

@@ -117,12 +117,13 @@ struct EwBlock {
 
 // Apply block: the nrows (<= 4) rows row[0..nrows) of vector vec, not
 // necessarily consecutive (row0 = row[0]); for the column pass of the split
-// apply: columns [row0, row0 + nrows).
+// apply: columns [row0, row0 + nrows); for its row-gather T_up pass: the
+// rows row[0..nrows) and the column pairs from pc on (one chunk).
 struct ApplyBlock {
   int vec;
   int row0;
   int nrows;
-  int pad;
+  int pc;
   int row[4];
 };
 

@@ -77,17 +77,27 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
                 cands.end());
   if (cands.empty()) return "apply kernel: rows too long for shared memory";
   for (auto& c : cands) c.vec = t.vec_ok;
+  // row orders of the vectors' up spaces (reverse Cuthill-McKee), computed once
+  std::vector<std::vector<int>> orders(t.dim_up.size());
+  for (size_t i = 0; i < t.dim_up.size(); ++i)
+    if (i < t.up.size() && t.up[i] && t.up[i]->dim == t.dim_up[i])
+      orders[i] = block_order(*t.up[i], 1);
+  auto order_of = [&](size_t i) { return orders[i].empty() ? nullptr : &orders[i]; };
   auto build = [&](const LaunchShape& sh) {
     map->clear();
     cmap->clear();
     for (size_t i = 0; i < t.dim_up.size(); ++i) {
-      if (i < t.up.size() && t.up[i] && t.up[i]->dim == t.dim_up[i]) {
-        const std::vector<int> rows = block_order(*t.up[i], 1);
-        append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr, &rows);
-      } else {
-        append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr);
-      }
-      if (sh.split) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64, sh.cb);
+      append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr, order_of(i));
+      if (sh.split && sh.cb > 0) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64, sh.cb);
+    }
+    if (sh.split && sh.cb == 0) {   // row-gather T_up pass: chunk-major over the batch
+      const int chunk = sh.threads * sh.ppc;
+      int max_pairs = 0;
+      for (int d : t.dim_dn) max_pairs = std::max(max_pairs, (d + 1) / 2);
+      for (int pc = 0; pc < max_pairs; pc += chunk)
+        for (size_t i = 0; i < t.dim_up.size(); ++i)
+          if (pc < (t.dim_dn[i] + 1) / 2)
+            append_tup_chunk(*cmap, (int)i, t.dim_up[i], kTupRows, pc, order_of(i));
     }
   };
   const int forced = forced_apply_config();

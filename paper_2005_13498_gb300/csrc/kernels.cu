@@ -947,6 +947,81 @@ k_apply(BatchArgs a, int j) {
   }
 }
 
+// --------------------------------------------- split apply: T_up by rows
+// T_up pass of the split apply for sectors whose vector does not fit L2:
+// w[u, chunk] = sum_{u'} T_up[u, u'] x[u', chunk] for the kTupRows rows of
+// the block (ApplyBlock.row) over one chunk of kApplyThreads * PP column
+// pairs from ApplyBlock.pc on, with the gathers of tup_chunk.  The blocks
+// come chunk by chunk (append_tup_chunk), so the CTAs resident together
+// gather from one chunk of columns of all rows, a working set the L2 holds
+// even when the whole vector does not fit; w goes out with evict-first
+// stores.  The row pass (k_apply with SPLIT) adds its rows of w.
+template <typename R, int PP, bool VEC, int MINB>
+__global__ void __launch_bounds__(kApplyThreads, MINB)
+k_apply_tup(BatchArgs a, int j) {
+  using C = typename C2T<R>::T;
+  constexpr int T = kApplyThreads;
+  constexpr int NR = kTupRows;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ApplyBlock ab = a.col_map[blockIdx.x];
+  const VecDev vd = a.vec[ab.vec];
+  const LanczosState* st = a.st + ab.vec;
+  if (j >= 1 && lanczos_done(st, j)) return;   // uniform over the vector's blocks
+  const SectorDev sd = a.sec[vd.sector];
+  const int dim_dn = sd.dim_dn;
+  const int npairs = (dim_dn + 1) >> 1;
+  const int pc = ab.pc;
+  const int nrows = ab.nrows;
+  const int tid = threadIdx.x;
+  int urow[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) urow[r] = r < nrows ? ab.row[r] : ab.row[0];
+
+  // the group coefficients and (complex64) their signed quads, laid out as
+  // in k_apply with an empty tile
+  C* coefS = reinterpret_cast<C*>(smem_raw);
+  float4* coefQ = reinterpret_cast<float4*>(
+      smem_raw + (((size_t)a.n_groups * sizeof(C) + 15) & ~(size_t)15));
+  const void* cbase;
+  if (j >= 1) cbase = static_cast<const char*>(a.coefs) + (size_t)st->step * a.n_groups * sizeof(C);
+  else if (j == 0) cbase = a.coefs;
+  else cbase = static_cast<const char*>(a.coefs_obs) + (size_t)st->step * a.n_groups * sizeof(C);
+  for (int g = tid; g < a.n_groups; g += T) coefS[g] = reinterpret_cast<const C*>(cbase)[g];
+  if constexpr (sizeof(R) == 4) {
+    for (int i = tid; i <= 2 * a.n_groups; i += T) {
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i > 0) {
+        const float2 c = reinterpret_cast<const float2*>(cbase)[(i - 1) >> 1];
+        const float sg = ((i - 1) & 1) ? -1.f : 1.f;
+        q = make_float4(sg * c.x, sg * c.x, sg * c.y, sg * c.y);
+      }
+      coefQ[i] = q;
+    }
+  }
+  __syncthreads();
+
+  const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
+  C* w = static_cast<C*>(vd.w);
+  C acc[NR][2 * PP];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int k = 0; k < 2 * PP; ++k) acc[r][k] = czero<C>();
+  if (PP > 1 && pc + (PP - 1) * T < npairs)
+    tup_chunk<R, NR, PP, PP, VEC>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
+  else
+    tup_chunk<R, NR, PP, 1, VEC>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+      const int p = pc + tid + k * T;
+      if (r < nrows && p < npairs)
+        store_pair<C, VEC, true>(w + (size_t)urow[r] * dim_dn, p, dim_dn, acc[r][2 * k],
+                                 acc[r][2 * k + 1]);
+    }
+}
+
 // ------------------------------------------------------- split apply: columns
 // Column pass of the split apply: w[u, d] = sum_u' T_up[u, u'] x[u', d] for
 // the NC = 32 bytes / sizeof(C) columns d0 .. d0 + ncols - 1 of every row u
@@ -1862,6 +1937,9 @@ static const ApplyCfg kApplyCfgs[] = {
     // one kernel with the T_up row chunks staged by TMA (a producer warp)
     {false, 2, 2, 2, false, 0, 0, 0, 0, 6}, {false, 1, 2, 2, false, 0, 0, 0, 0, 8},
     {true, 1, 1, 2, false, 0, 0, 0, 0, 6},
+    // split with the row-gather T_up pass (chunk-major; vectors beyond L2):
+    // chunks of 256 or 512 column pairs
+    {false, 1, 2, 2, true, 1, 4, 0, 256}, {false, 1, 2, 2, true, 2, 3, 0, 256},
 };
 static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
 
@@ -1897,7 +1975,10 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     if (c.tma)   // 128-byte aligned ring of row chunks + full/empty mbarriers
       sh.smem = ((sh.smem + 127) & ~(size_t)127) +
                 (size_t)c.tma * kApplyThreads * c.pp * 2 * csz + 2 * (size_t)c.tma * 8;
-    sh.smem_c = c.split ? (size_t)(max_dim_up + kZeroCols) * c.cb + (size_t)n_groups * csz : 0;
+    sh.ppc = c.ppc;
+    sh.smem_c = !c.split ? 0
+                : c.cb == 0 ? apply_coef_end(0, 0, n_groups, fp64)   // coefficients only
+                            : (size_t)(max_dim_up + kZeroCols) * c.cb + (size_t)n_groups * csz;
     return sh;
   };
   for (int i = 0; i < kNumApplyCfgs; ++i) {
@@ -1944,7 +2025,12 @@ static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShap
                                   int j, cudaStream_t s) {
   constexpr bool V = sizeof(R) == 4;
   constexpr int threads = TMA ? kApplyThreads + 32 : kApplyThreads;
-  if constexpr (SPLIT) {
+  if constexpr (SPLIT && CB == 0) {
+    if (sh.vec) k_apply_tup<R, PPC, V, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
+    else k_apply_tup<R, PPC, false, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else if constexpr (SPLIT) {
     if (sh.vec) k_apply_up<R, PPC, V, MINBC, CB, TC><<<a.n_col_blocks, TC, sh.smem_c, s>>>(a, j);
     else k_apply_up<R, PPC, false, MINBC, CB, TC><<<a.n_col_blocks, TC, sh.smem_c, s>>>(a, j);
     cudaError_t e = cudaGetLastError();
@@ -1966,7 +2052,14 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
-  if constexpr (SPLIT) {
+  if constexpr (SPLIT && CB == 0) {
+    const int smc = (int)sh.smem_c;
+    e = cudaFuncSetAttribute(k_apply_tup<R, PPC, false, MINBC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_apply_tup<R, PPC, V, MINBC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
+  } else if constexpr (SPLIT) {
     const int smc = (int)sh.smem_c;
     e = cudaFuncSetAttribute(k_apply_up<R, PPC, false, MINBC, CB, TC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
@@ -1996,7 +2089,9 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   X(14, double, 1, 1, 1, true, 1, 1, 16, 512, 0)       \
   X(15, float, 2, 2, 2, false, 1, 1, 32, 256, 6)        \
   X(16, float, 1, 2, 2, false, 1, 1, 32, 256, 8)        \
-  X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6)
+  X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6)      \
+  X(18, float, 1, 2, 2, true, 1, 4, 0, 256, 0)         \
+  X(19, float, 1, 2, 2, true, 2, 3, 0, 256, 0)
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
   (void)fp64;

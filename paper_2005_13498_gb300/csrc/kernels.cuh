@@ -19,8 +19,10 @@ struct LaunchShape {
   int cfg = 0;       // index of the kernel configuration (rows, pairs, occupancy)
   bool split = false;  // column pass (T_up) + row pass instead of one kernel
   size_t smem_c = 0;   // dynamic shared memory of the column pass
-  int cb = 32;         // column-pass block: bytes of columns per row (32 or 16)
+  int cb = 32;         // column-pass block: bytes of columns per row (32 or 16);
+                       // 0: the T_up pass gathers rows (k_apply_tup) instead
   int tc = 256;        // column-pass threads per CTA
+  int ppc = 1;         // T_up pass: column pairs per thread (chunk = 256 ppc pairs)
   bool tma = false;    // T_up row chunks staged by TMA (one extra producer warp)
 };
 
@@ -37,6 +39,24 @@ inline void append_col_blocks(std::vector<ApplyBlock>& map, int vec, int dim_dn,
   const int nc = cb / (fp64 ? 16 : 8);
   for (int d = 0; d < dim_dn; d += nc)
     map.push_back({vec, d, dim_dn - d < nc ? dim_dn - d : nc, 0});
+}
+
+// Rows per block of the row-gather T_up pass (k_apply_tup).
+constexpr int kTupRows = 4;
+
+// Blocks of the row-gather T_up pass of the split apply for one chunk of
+// column pairs (from pc on) of vector vec: nr <= 4 rows per block, rows in
+// the given order (natural when order is null).  The engine appends the
+// chunks of all vectors chunk-major, so that the CTAs resident together
+// gather from one chunk of columns of all rows.
+inline void append_tup_chunk(std::vector<ApplyBlock>& map, int vec, int dim_up, int nr, int pc,
+                             const std::vector<int>* order = nullptr) {
+  for (int i = 0; i < dim_up; i += nr) {
+    ApplyBlock b{vec, 0, dim_up - i < nr ? dim_up - i : nr, pc, {0, 0, 0, 0}};
+    for (int r = 0; r < b.nrows; ++r) b.row[r] = order ? (*order)[i + r] : i + r;
+    b.row0 = b.row[0];
+    map.push_back(b);
+  }
 }
 
 // Apply blocks of nr <= 4 rows covering rows [0, dim_up) of vector vec:
