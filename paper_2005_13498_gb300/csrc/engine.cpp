@@ -91,7 +91,7 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
       if (sh.split && sh.cb > 0) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64, sh.cb);
     }
     if (sh.split && sh.cb == 0) {   // row-gather T_up pass: chunk-major over the batch
-      const int chunk = sh.threads * sh.ppc;
+      const int chunk = kApplyThreads * sh.ppc;   // k_apply_tup runs kApplyThreads threads
       int max_pairs = 0;
       for (int d : t.dim_dn) max_pairs = std::max(max_pairs, (d + 1) / 2);
       for (int pc = 0; pc < max_pairs; pc += chunk)

@@ -156,7 +156,6 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 // j >= 1: Lanczos pass j; j == 0: plain apply (coefs row 0, x1 -> w);
 // j == -1: energy of x1 with coefs_obs[step].
 // (The apply kernel and its phases are described at k_apply below.)
-constexpr int kApplyThreads = 256;
 
 // ---- TMA pipeline for the T_up row segments (TMA apply configurations).
 // A producer warp copies the source-row chunk of every T_up entry into a ring
@@ -386,12 +385,12 @@ struct TileIO {
 //    and no operand swaps; the row ends with acc += (a.x - b.y, a.y + b.x).
 //  * complex128 (FP64-pipe bound): signed sums per bond group, multiplied
 //    by c_g once per group.
-template <int NR, int PP, int KA, bool VEC>
+template <int NR, int PP, int KA, bool VEC, int NT>
 __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2* x,
                                               const float4* coefQ, const int (&urow)[NR],
                                               int nrows, int pc,
                                               int npairs, int dim_dn, float2 (&acc)[NR][2 * PP]) {
-  constexpr int T = kApplyThreads;
+  constexpr int T = NT;
   int pk[KA];
 #pragma unroll
   for (int k = 0; k < KA; ++k) pk[k] = min(pc + (int)threadIdx.x + k * T, npairs - 1);
@@ -448,14 +447,14 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2*
   }
 }
 
-template <int NR, int PP, int KA>
+template <int NR, int PP, int KA, int NT>
 __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double2* x,
                                                const double2* coefS, const int (&urow)[NR],
                                                int nrows, int pc,
                                                int npairs, int dim_dn,
                                                double2 (&acc)[NR][2 * PP]) {
   using C = double2;
-  constexpr int T = kApplyThreads;
+  constexpr int T = NT;
   int pk[KA];
 #pragma unroll
   for (int k = 0; k < KA; ++k) pk[k] = min(pc + (int)threadIdx.x + k * T, npairs - 1);
@@ -509,16 +508,16 @@ __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double
   }
 }
 
-template <typename R, int NR, int PP, int KA, bool VEC>
+template <typename R, int NR, int PP, int KA, bool VEC, int NT = kApplyThreads>
 __device__ __forceinline__ void tup_chunk(const SectorDev& sd, const typename C2T<R>::T* x,
                                           const typename C2T<R>::T* coefS, const float4* coefQ,
                                           const int (&urow)[NR], int nrows, int pc, int npairs,
                                           int dim_dn,
                                           typename C2T<R>::T (&acc)[NR][2 * PP]) {
   if constexpr (sizeof(R) == 4)
-    tup_chunk_c64<NR, PP, KA, VEC>(sd, x, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
+    tup_chunk_c64<NR, PP, KA, VEC, NT>(sd, x, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
   else
-    tup_chunk_c128<NR, PP, KA>(sd, x, coefS, urow, nrows, pc, npairs, dim_dn, acc);
+    tup_chunk_c128<NR, PP, KA, NT>(sd, x, coefS, urow, nrows, pc, npairs, dim_dn, acc);
 }
 
 // Shared-memory bytes in front of the TMA ring / end of the apply's dynamic
@@ -531,11 +530,12 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
   return off;
 }
 
-// One CTA (256 threads) processes NR rows of one vector, the rows of its
+// One CTA (NT threads: 256, or 512 for a row pass on long rows) processes NR
+// rows of one vector, the rows of its
 // ApplyBlock (consecutive entries of the block order the host chose).  The
 // rows are staged in shared memory column by column (TileIO),
 // followed by eight zero columns that empty ELL slots read.  Thread t owns
-// the column pairs p = pc + t + k*256 (k < PP) of every chunk pc, so a warp
+// the column pairs p = pc + t + k*NT (k < PP) of every chunk pc, so a warp
 // covers 64 consecutive columns.
 //  * T_dn (within a row): the warp walks the flat slot list of its 64-column
 //    ELL tile (slots grouped by bond group, trip count uniform over the
@@ -549,14 +549,14 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
 //  * Epilogue: the diagonal U * popcount(up & dn) (+ on-site energies) times
 //    the staged x joins the sums, w = s_j acc - beta_{j-1} s_{j-1} x_{j-1} is
 //    stored in pairs, and the partial of Re<x_j, w> is accumulated.
-template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS>
-__global__ void __launch_bounds__(TMAS ? kApplyThreads + 32 : kApplyThreads, MINB)
+template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS, int NT>
+__global__ void __launch_bounds__(TMAS ? NT + 32 : NT, MINB)
 k_apply(BatchArgs a, int j) {
   constexpr bool TMA = TMAS > 0;       // TMAS: ring stages of the TMA configurations
   constexpr uint32_t S = TMAS > 0 ? (uint32_t)TMAS : 1u;
   using C = typename C2T<R>::T;
   using TIO = TileIO<C, NR>;
-  constexpr int T = kApplyThreads;           // consumer threads (all threads without TMA)
+  constexpr int T = NT;                      // consumer threads (all threads without TMA)
   constexpr uint32_t kSlotBytes = (uint32_t)(T * PP * 2 * sizeof(C));   // one chunk of a row
   static_assert(!(TMA && SPLIT), "the TMA ring serves the one-kernel T_up");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -875,9 +875,9 @@ k_apply(BatchArgs a, int j) {
     // versioned on how many column-pair groups of this chunk hold valid pairs
     if constexpr (!SPLIT && !TMA) {
       if (PP > 1 && pc + (PP - 1) * T < npairs)
-        tup_chunk<R, NR, PP, PP, VEC>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
+        tup_chunk<R, NR, PP, PP, VEC, NT>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
       else
-        tup_chunk<R, NR, PP, 1, VEC>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
+        tup_chunk<R, NR, PP, 1, VEC, NT>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
     }
     // ---- epilogue: previous-vector loads first, then scale, subtract, store
     C pv[NR][2 * PP];
@@ -1920,7 +1920,7 @@ static int grid_for(int64_t n, int threads) {
 // register budget) of the row kernel; for the split apply also the pairs per
 // thread and occupancy of the column pass.  The autotuner times the feasible
 // ones.
-struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc, cb, tc; int tma; };
+struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc, cb, tc; int tma; int nt; };
 // tma: 0, or the ring stages of a configuration whose T_up row chunks are
 // staged by TMA
 static const ApplyCfg kApplyCfgs[] = {
@@ -1940,6 +1940,8 @@ static const ApplyCfg kApplyCfgs[] = {
     // split with the row-gather T_up pass (chunk-major; vectors beyond L2):
     // chunks of 256 or 512 column pairs
     {false, 1, 2, 2, true, 1, 4, 0, 256}, {false, 1, 2, 2, true, 2, 3, 0, 256},
+    // the same with a 512-thread row pass (twice the warps per SM on long rows)
+    {false, 1, 1, 2, true, 2, 3, 0, 256, 0, 512},
 };
 static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
 
@@ -1963,7 +1965,7 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
   auto make = [&](int i) {
     const ApplyCfg& c = kApplyCfgs[i];
     LaunchShape sh;
-    sh.threads = kApplyThreads;
+    sh.threads = c.nt ? c.nt : kApplyThreads;
     sh.ept = c.pp;
     sh.nr = c.nr;
     sh.cfg = i;
@@ -2020,11 +2022,11 @@ LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups)
 }
 
 template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC,
-          int TMA>
+          int TMA, int NT>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
   constexpr bool V = sizeof(R) == 4;
-  constexpr int threads = TMA ? kApplyThreads + 32 : kApplyThreads;
+  constexpr int threads = TMA ? NT + 32 : NT;
   if constexpr (SPLIT && CB == 0) {
     if (sh.vec) k_apply_tup<R, PPC, V, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
     else k_apply_tup<R, PPC, false, MINBC><<<a.n_col_blocks, kApplyThreads, sh.smem_c, s>>>(a, j);
@@ -2036,20 +2038,20 @@ static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShap
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT, TMA><<<nblk, threads, sh.smem, s>>>(a, j);
-  else k_apply<R, NR, PP, false, MINB, SPLIT, TMA><<<nblk, threads, sh.smem, s>>>(a, j);
+  if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
+  else k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
 }
 
 template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC,
-          int TMA>
+          int TMA, int NT>
 static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   constexpr bool V = sizeof(R) == 4;
   const int sm = (int)sh.smem;
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, SPLIT, TMA>,
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA>,
+  e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
   if constexpr (SPLIT && CB == 0) {
@@ -2072,32 +2074,33 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
 
 // One switch over the configuration table for both prepare and launch.
 #define ED_APPLY_CONFIGS(X)                                \
-  X(0, float, 4, 2, 2, false, 1, 1, 32, 256, 0)        \
-  X(1, float, 2, 2, 3, false, 1, 1, 32, 256, 0)        \
-  X(2, float, 2, 1, 4, false, 1, 1, 32, 256, 0)        \
-  X(3, float, 1, 2, 2, false, 1, 1, 32, 256, 0)        \
-  X(4, double, 2, 1, 2, false, 1, 1, 32, 256, 0)       \
-  X(5, double, 1, 1, 4, false, 1, 1, 32, 256, 0)       \
-  X(6, double, 1, 1, 2, false, 1, 1, 32, 256, 0)       \
-  X(7, float, 4, 2, 2, true, 1, 2, 32, 256, 0)         \
-  X(8, float, 2, 2, 3, true, 1, 2, 32, 256, 0)         \
-  X(9, float, 2, 1, 4, true, 1, 2, 32, 256, 0)         \
-  X(10, float, 4, 2, 2, true, 2, 2, 32, 256, 0)        \
-  X(11, double, 2, 1, 2, true, 1, 2, 32, 256, 0)       \
-  X(12, double, 1, 1, 4, true, 1, 2, 32, 256, 0)       \
-  X(13, float, 1, 2, 2, true, 1, 1, 16, 512, 0)        \
-  X(14, double, 1, 1, 1, true, 1, 1, 16, 512, 0)       \
-  X(15, float, 2, 2, 2, false, 1, 1, 32, 256, 6)        \
-  X(16, float, 1, 2, 2, false, 1, 1, 32, 256, 8)        \
-  X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6)      \
-  X(18, float, 1, 2, 2, true, 1, 4, 0, 256, 0)         \
-  X(19, float, 1, 2, 2, true, 2, 3, 0, 256, 0)
+  X(0, float, 4, 2, 2, false, 1, 1, 32, 256, 0, 256)        \
+  X(1, float, 2, 2, 3, false, 1, 1, 32, 256, 0, 256)        \
+  X(2, float, 2, 1, 4, false, 1, 1, 32, 256, 0, 256)        \
+  X(3, float, 1, 2, 2, false, 1, 1, 32, 256, 0, 256)        \
+  X(4, double, 2, 1, 2, false, 1, 1, 32, 256, 0, 256)       \
+  X(5, double, 1, 1, 4, false, 1, 1, 32, 256, 0, 256)       \
+  X(6, double, 1, 1, 2, false, 1, 1, 32, 256, 0, 256)       \
+  X(7, float, 4, 2, 2, true, 1, 2, 32, 256, 0, 256)         \
+  X(8, float, 2, 2, 3, true, 1, 2, 32, 256, 0, 256)         \
+  X(9, float, 2, 1, 4, true, 1, 2, 32, 256, 0, 256)         \
+  X(10, float, 4, 2, 2, true, 2, 2, 32, 256, 0, 256)        \
+  X(11, double, 2, 1, 2, true, 1, 2, 32, 256, 0, 256)       \
+  X(12, double, 1, 1, 4, true, 1, 2, 32, 256, 0, 256)       \
+  X(13, float, 1, 2, 2, true, 1, 1, 16, 512, 0, 256)        \
+  X(14, double, 1, 1, 1, true, 1, 1, 16, 512, 0, 256)       \
+  X(15, float, 2, 2, 2, false, 1, 1, 32, 256, 6, 256)        \
+  X(16, float, 1, 2, 2, false, 1, 1, 32, 256, 8, 256)        \
+  X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6, 256)      \
+  X(18, float, 1, 2, 2, true, 1, 4, 0, 256, 0, 256)         \
+  X(19, float, 1, 2, 2, true, 2, 3, 0, 256, 0, 256)       \
+  X(20, float, 1, 1, 2, true, 2, 3, 0, 256, 0, 512)
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
   (void)fp64;
   if (sh.nr < 1 || sh.smem > 227 * 1024 || sh.smem_c > 227 * 1024) return cudaErrorInvalidValue;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM) \
-  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM>(sh);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT) \
+  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT>(sh);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;
@@ -2108,8 +2111,8 @@ cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
                          int j, cudaStream_t s) {
   (void)fp64;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM) \
-  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM>(a, nblk, sh, j, s);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT) \
+  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT>(a, nblk, sh, j, s);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;

@@ -41,7 +41,10 @@ inline void append_col_blocks(std::vector<ApplyBlock>& map, int vec, int dim_dn,
     map.push_back({vec, d, dim_dn - d < nc ? dim_dn - d : nc, 0});
 }
 
-// Rows per block of the row-gather T_up pass (k_apply_tup).
+// Threads per CTA of the apply kernels (the default; a configuration may
+// run its row pass with more) and rows per block of the row-gather T_up
+// pass (k_apply_tup).
+constexpr int kApplyThreads = 256;
 constexpr int kTupRows = 4;
 
 // Blocks of the row-gather T_up pass of the split apply for one chunk of
