@@ -1940,8 +1940,9 @@ static const ApplyCfg kApplyCfgs[] = {
     // split with the row-gather T_up pass (chunk-major; vectors beyond L2):
     // chunks of 256 or 512 column pairs
     {false, 1, 2, 2, true, 1, 4, 0, 256}, {false, 1, 2, 2, true, 2, 3, 0, 256},
-    // the same with a 512-thread row pass (twice the warps per SM on long rows)
-    {false, 1, 1, 2, true, 2, 3, 0, 256, 0, 512},
+    // the same with a 512-thread row pass (twice the warps per SM on long rows),
+    // and with two rows in one 1024-thread CTA per SM
+    {false, 1, 1, 2, true, 2, 3, 0, 256, 0, 512}, {false, 2, 1, 1, true, 2, 3, 0, 256, 0, 1024},
 };
 static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
 
@@ -2094,7 +2095,8 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6, 256)      \
   X(18, float, 1, 2, 2, true, 1, 4, 0, 256, 0, 256)         \
   X(19, float, 1, 2, 2, true, 2, 3, 0, 256, 0, 256)       \
-  X(20, float, 1, 1, 2, true, 2, 3, 0, 256, 0, 512)
+  X(20, float, 1, 1, 2, true, 2, 3, 0, 256, 0, 512)       \
+  X(21, float, 2, 1, 1, true, 2, 3, 0, 256, 0, 1024)
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
   (void)fp64;
