@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <vector>
 
+#include "kernels.cuh"
 #include "tables.h"
 
 int main() {
@@ -63,7 +64,31 @@ int main() {
       u_nat = window_union(nat);
       u_ord = window_union(rows);
     }
-    std::printf("%d %d %d %.6f %.6f\n", nr, nblk, perm ? 1 : 0, u_nat, u_ord);
+    // the engine's block maps on this order: the apply blocks (nr rows) and
+    // the row-gather T_up blocks (kTupRows rows, chunks of 256 pairs of a
+    // row of dim_dn = dim columns) cover every row, and every (row, chunk),
+    // exactly once
+    bool maps_ok = perm;
+    if (perm) {
+      std::vector<ed::ApplyBlock> map;
+      ed::append_apply_blocks(map, 0, T.dim, nr, &rows);
+      std::vector<int> cnt(T.dim, 0);
+      for (const ed::ApplyBlock& b : map) {
+        if (b.nrows < 1 || b.nrows > nr || b.nrows > 4 || b.row0 != b.row[0]) maps_ok = false;
+        for (int r = 0; r < b.nrows && maps_ok; ++r) ++cnt[b.row[r]];
+      }
+      const int npairs = (T.dim + 1) / 2, chunk = 256;
+      std::vector<ed::ApplyBlock> tmap;
+      for (int pc = 0; pc < npairs; pc += chunk) ed::append_tup_chunk(tmap, 0, T.dim, ed::kTupRows, pc, &rows);
+      std::vector<int> tcnt((size_t)T.dim * ((npairs + chunk - 1) / chunk), 0);
+      for (const ed::ApplyBlock& b : tmap) {
+        if (b.nrows < 1 || b.nrows > ed::kTupRows || b.pc % chunk != 0) { maps_ok = false; break; }
+        for (int r = 0; r < b.nrows; ++r) ++tcnt[(size_t)b.row[r] * ((npairs + chunk - 1) / chunk) + b.pc / chunk];
+      }
+      for (int c : cnt) maps_ok = maps_ok && c == 1;
+      for (int c : tcnt) maps_ok = maps_ok && c == 1;
+    }
+    std::printf("%d %d %d %.6f %.6f %d\n", nr, nblk, perm ? 1 : 0, u_nat, u_ord, maps_ok ? 1 : 0);
   }
   return 0;
 }

@@ -47,15 +47,16 @@ def run(exe, lat, n, nrs):
     res = []
     for ln in out.strip().splitlines():
         a = ln.split()
-        res.append((int(a[0]), int(a[1]), int(a[2]), float(a[3]), float(a[4])))
+        res.append((int(a[0]), int(a[1]), int(a[2]), float(a[3]), float(a[4]), int(a[5])))
     return res
 
 
 @pytest.mark.parametrize("name,n", [("ladder2x7", 7), ("torus3x4", 6), ("ring8", 4)])
 def test_block_order_is_a_permutation_with_a_smaller_working_set(checker, name, n):
     lat = synth.lattice_from_name(name)
-    for nr, nblk, perm, u_nat, u_ord in run(checker, lat, n, [1, 2, 4]):
+    for nr, nblk, perm, u_nat, u_ord, maps_ok in run(checker, lat, n, [1, 2, 4]):
         assert perm == 1, (name, nr)
+        assert maps_ok == 1, (name, nr)   # block maps cover every row (and chunk) once
         assert nblk > 1
         assert 0 < u_ord <= u_nat, (name, nr, u_nat, u_ord)
         if name == "ladder2x7":
