@@ -1,8 +1,12 @@
 """Every H v kernel configuration against the oracle, each pinned in turn
-with ed_set_apply_config: the one-kernel variants, the split variants
-(column pass for T_up, row pass for the diagonal and T_dn) and the variants
-whose T_up row chunks a producer warp stages by TMA, with all their
-rows-per-block, pairs-per-thread and occupancy settings.
+with ed_set_apply_config: the one-kernel variants, the split variants (a
+T_up pass, either column blocks staged in shared memory or row gathers one
+chunk of columns at a time, then a row pass for the diagonal and T_dn, with
+256, 512 or 1024 threads) and the variants whose T_up row chunks a producer
+warp stages by TMA, with all their rows-per-block, pairs-per-thread and
+occupancy settings.  The 924 x 792 sector gives the row-gather pass a
+ragged second chunk (256-pair chunks) and a partly valid second column-pair
+group (512-pair chunks).
 
 The sectors put the column pass through each of its layout cases: dim_dn a
 multiple of 4 (16-byte pairs, full 4-column blocks), dim_dn = 2 mod 4 (a
