@@ -46,6 +46,7 @@ inline void append_col_blocks(std::vector<ApplyBlock>& map, int vec, int dim_dn,
 // pass (k_apply_tup).
 constexpr int kApplyThreads = 256;
 constexpr int kTupRows = 4;
+static_assert(kTupRows <= 4, "an ApplyBlock lists at most 4 rows");
 
 // Blocks of the row-gather T_up pass of the split apply for one chunk of
 // column pairs (from pc on) of vector vec: nr <= 4 rows per block, rows in
@@ -67,6 +68,7 @@ inline void append_tup_chunk(std::vector<ApplyBlock>& map, int vec, int dim_up, 
 // when order is null.
 inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_up, int nr,
                                 const std::vector<int>* order = nullptr) {
+  // every configuration of the table has nr <= 4 (the rows an ApplyBlock holds)
   for (int i = 0; i < dim_up; i += nr) {
     ApplyBlock b{vec, 0, dim_up - i < nr ? dim_up - i : nr, 0, {0, 0, 0, 0}};
     for (int r = 0; r < b.nrows; ++r) b.row[r] = order ? (*order)[i + r] : i + r;
