@@ -38,6 +38,10 @@
  * - Streams: `stream` is a cudaStream_t passed as void*; NULL = the legacy
  *   default stream.  Calls on one context must not run concurrently from
  *   several host threads.
+ * - Devices: a context's tables go to the device that is current at its
+ *   first GPU call.  Every later GPU call on it must run with that device
+ *   current (else ED_ERR_STATE, nothing launched), and device vectors passed
+ *   to it must live on that device (else ED_ERR_ARG).
  * - Errors: every call returns an ed_status; no C++ exception crosses the
  *   ABI.  ed_last_error() returns a human-readable message for the last
  *   failing call on that context (or on any context when ctx is NULL).
@@ -340,6 +344,34 @@ ed_status ed_set_apply_config(int config);
 /* The configuration the context's propagation engine (*propagate) and its
  * ed_apply_H plan (*apply) use, or -1 where none has been set up yet.        */
 ed_status ed_get_apply_config(const ed_ctx* ctx, int* propagate, int* apply);
+
+/* Cap on the device memory that the Krylov workspace of this context's
+ * ed_propagate and ed_spectral_propagate engines (the propagated states the
+ * library owns, the m - 1 stored Krylov vectors and one scratch vector per
+ * propagated vector) and of its ed_ground_state solves (the restart basis)
+ * may take; 0 (the default) = no cap.  A call whose workspace would exceed the
+ * cap returns ED_ERR_OOM before allocating anything; a smaller cap set later
+ * makes the next call rebuild (and re-check) its workspace.  Tables and the
+ * few kilobytes of per-call bookkeeping are not counted.  ED_ERR_ARG for a
+ * negative size.  (No passage of the paper: a deployment control.)          */
+ed_status ed_set_workspace_limit(ed_ctx* ctx, int64_t bytes);
+
+/* Test hook for the bounded device-side waits (process-wide; applies to the
+ * propagation engines, ed_apply_H plans and ground-state solves set up after
+ * the call, which rebuild when it changes).  The TMA configurations of the
+ * H v kernel (tma = 1 in ed_apply_config_info) wait on shared-memory
+ * barriers for the T_up row copies of a producer warp; every such wait gives
+ * up after wait_polls polls (0 = the default, 2^22), records ED_ERR_TIMEOUT
+ * in the vector's status and lets the kernel finish, so that the context
+ * stays usable.  withhold_copy >= 0 makes the producer of every thread block
+ * stop before that copy (counted from 0 per block) instead of issuing it, so
+ * that the consumers' wait for it runs out: ed_propagate and
+ * ed_spectral_propagate then return ED_ERR_TIMEOUT (ed_apply_H runs
+ * asynchronously and does not read the status).  No copy is left in flight
+ * when a block ends.  withhold_copy = -1 (the default) turns the hook off.
+ * ED_ERR_ARG for withhold_copy < -1 or wait_polls outside 0..2^32-1.
+ * (No passage of the paper: a check of the library's own failure path.)    */
+ed_status ed_set_wait_fault(int withhold_copy, int64_t wait_polls);
 
 /* Bytes of device memory the context currently holds (tables + workspace).  */
 ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes);

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "ctx.h"
+#include "device_guard.h"
 
 using namespace ed;
 
@@ -144,6 +145,31 @@ ed_status ensure_device(ed_ctx* ctx) {
   CK(ctx, cudaGetDevice(&ctx->device));
   if (!ctx->stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
   CK(ctx, upload_sector(ctx->sec));
+  return ED_OK;
+}
+
+ed_status check_device(ed_ctx* ctx, std::initializer_list<const void*> bufs) {
+  int cur = -1;
+  CK(ctx, cudaGetDevice(&cur));
+  if (device_verdict(ctx->device, cur, -1) == kDeviceWrongCurrent)
+    return fail(ctx, ED_ERR_STATE,
+                "the context's tables live on device " + std::to_string(ctx->device) +
+                    " but device " + std::to_string(cur) +
+                    " is current; make that device current first");
+  for (const void* p : bufs) {
+    if (!p) continue;
+    int dev = -1;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) == cudaSuccess) {
+      if (a.type == cudaMemoryTypeDevice) dev = a.device;
+    } else {
+      cudaGetLastError();
+    }
+    if (device_verdict(ctx->device, cur, dev) == kDeviceForeignBuffer)
+      return fail(ctx, ED_ERR_ARG,
+                  "a vector lives on device " + std::to_string(dev) +
+                      ", the context's tables on device " + std::to_string(ctx->device));
+  }
   return ED_OK;
 }
 
@@ -346,6 +372,20 @@ ed_status ed_set_krylov_tol(ed_ctx* ctx, double tol) {
   return ED_OK;
 }
 
+ed_status ed_set_workspace_limit(ed_ctx* ctx, int64_t bytes) {
+  if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
+  if (bytes < 0) return fail(ctx, ED_ERR_ARG, "bytes must be >= 0");
+  ctx->workspace_limit = bytes;
+  return ED_OK;
+}
+
+ed_status ed_set_wait_fault(int withhold_copy, int64_t wait_polls) {
+  if (withhold_copy < -1 || wait_polls < 0 || wait_polls > 0xFFFFFFFFll)
+    return fail(nullptr, ED_ERR_ARG, "withhold_copy must be >= -1, wait_polls in 0..2^32-1");
+  set_wait_fault(withhold_copy, (uint32_t)wait_polls);
+  return ED_OK;
+}
+
 ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme) {
   if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
   if (scheme != ED_MIDPOINT && scheme != ED_CFET4)
@@ -391,12 +431,17 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
   if (!v || !w || nvec < 1) return fail(ctx, ED_ERR_ARG, "v, w must be non-NULL and nvec >= 1");
   if (dtype != ED_C128 && dtype != ED_C64) return fail(ctx, ED_ERR_ARG, "bad dtype");
   if (v == w) return fail(ctx, ED_ERR_ARG, "v and w must not alias");
+  if (ed_status e = check_device(ctx, {v, w})) return e;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool fp64 = dtype == ED_C128;
   ApplyPlan& P = ctx->plan;
   const bool same_field = P.A[0] == ctx->A[0] && P.A[1] == ctx->A[1] && P.A[2] == ctx->A[2];
   const int forced = forced_apply_config();
-  const bool same_cfg = forced < 0 || forced == P.shape.cfg;
+  BatchArgs now;
+  init_batch_args(&now);
+  const bool same_cfg = (forced < 0 || forced == P.shape.cfg) &&
+                        now.wait_limit == P.args.wait_limit &&
+                        now.tma_withhold == P.args.tma_withhold;
   if (!(P.valid && P.nvec == nvec && P.v == v && P.w == w && P.fp64 == fp64 && same_field &&
         same_cfg)) {
     if (!is_device_ptr(v) || !is_device_ptr(w))
@@ -426,7 +471,7 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     CK(ctx, cudaMemset(P.counters.p, 0, sizeof(unsigned) * nvec));
     if (fp64) CK(ctx, upload(P.coefs, cf));
     else CK(ctx, upload(P.coefs, cff));
-    std::memset(&P.args, 0, sizeof(P.args));
+    init_batch_args(&P.args);
     P.args.sec = static_cast<const SectorDev*>(P.sec.p);
     P.args.vec = static_cast<VecDev*>(P.vec.p);
     P.args.st = static_cast<LanczosState*>(P.st.p);
@@ -494,6 +539,7 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   if (!std::isfinite(dt) || !std::isfinite(t_start)) return fail(ctx, ED_ERR_ARG, "dt/t_start not finite");
   if (ed_status e = check_pulse(ctx, pulse)) return e;
   if (ed_status e = ensure_device(ctx)) return e;
+  if (ed_status e = check_device(ctx, {psi})) return e;
   cudaStream_t us = static_cast<cudaStream_t>(stream);
   cudaStream_t s = ctx->stream;
   const bool fp64 = dtype == ED_C128;
@@ -513,6 +559,7 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   cfg.energy = energy;
   cfg.n_steps_cap = std::max(1, n_sub);
   cfg.eps_tol = ctx->krylov_tol;
+  cfg.workspace_limit = ctx->workspace_limit;
   std::vector<EngineVector> vecs = {{0, D, on_device ? psi : nullptr, !on_device}};
   CK(ctx, join_streams(us, s));
   if (!ctx->engine || !ctx->engine->compatible(cfg, vecs)) {
@@ -569,6 +616,8 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
     CK(ctx, cudaStreamSynchronize(s));
   }
   CK(ctx, join_streams(s, us));
+  if (status == ED_ERR_TIMEOUT)
+    return fail(ctx, ED_ERR_TIMEOUT, "a bounded device-side wait of the apply kernel gave up");
   if (status != 0) return fail(ctx, ED_ERR_NUMERIC, "non-finite norm or inner product during propagation");
   return ED_OK;
 }
@@ -576,7 +625,9 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
 ed_status ed_double_occupation(ed_ctx* ctx, const void* psi, ed_dtype dtype, double* d_avg,
                                double* d_site) {
   if (!ctx || !psi || !d_avg) return fail(ctx, ED_ERR_ARG, "NULL argument");
+  if (dtype != ED_C128 && dtype != ED_C64) return fail(ctx, ED_ERR_ARG, "bad dtype");
   if (ed_status e = ensure_device(ctx)) return e;
+  if (ed_status e = check_device(ctx, {psi})) return e;
   const bool fp64 = dtype == ED_C128;
   const int64_t D = ctx->dim_up * ctx->dim_dn;
   const size_t esz = fp64 ? 16 : 8;
@@ -611,9 +662,11 @@ ed_status ed_apply_fermion_op(ed_ctx* ctx, ed_ctx* dst, int site, int spin, int 
   const int tu = ctx->n_up + (spin == 0 ? dn : 0), td = ctx->n_dn + (spin == 1 ? dn : 0);
   if (dst->Ns != ctx->Ns || dst->n_up != tu || dst->n_dn != td)
     return fail(ctx, ED_ERR_ARG, "destination context has the wrong sector");
+  if (dtype != ED_C128 && dtype != ED_C64) return fail(ctx, ED_ERR_ARG, "bad dtype");
   if (ed_status e = ensure_device(ctx)) return e;
   if (!is_device_ptr(psi) || !is_device_ptr(out))
     return fail(ctx, ED_ERR_ARG, "device pointers required");
+  if (ed_status e = check_device(ctx, {psi, out})) return e;
   std::vector<int32_t> map = fermion_map(ctx->Ns, ctx->n_up, ctx->n_dn, site, spin, create != 0);
   DevMem dmap;
   CK(ctx, upload(dmap, map));

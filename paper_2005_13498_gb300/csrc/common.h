@@ -148,6 +148,16 @@ struct BatchArgs {
   double U;
   double tau;
   double break_tol;
+  // bounded device-side waits (TMA configurations of the apply): polls of
+  // every mbarrier wait before it gives up with ED_ERR_TIMEOUT, and a test
+  // hook, the index (per thread block) of the T_up row-chunk copy that the
+  // producer warp stops at without issuing it (-1: none), which makes the
+  // consumers' wait for that copy run out
+  uint32_t wait_limit;
+  int tma_withhold;
 };
+
+// Default poll limit of the bounded mbarrier waits.
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;
 
 }  // namespace ed

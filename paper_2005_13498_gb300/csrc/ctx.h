@@ -3,6 +3,7 @@
 
 #include "../../include/ed.h"
 
+#include <initializer_list>
 #include <memory>
 #include <string>
 #include <vector>
@@ -50,6 +51,7 @@ struct ed_ctx {
   ed::SectorGPU sec;
   double A[3] = {0, 0, 0};
   double krylov_tol = 0.0;   // > 0: adaptive Krylov dimension (Algorithm 6)
+  int64_t workspace_limit = 0;   // > 0: cap on Krylov workspace allocations (bytes)
   int integrator = 0;        // ED_MIDPOINT or ED_CFET4
   std::string err;
   cudaStream_t stream = nullptr;
@@ -69,6 +71,10 @@ void build_sector_host(SectorGPU& S, const LatticeHost& L, int n_up, int n_dn);
 cudaError_t upload_sector(SectorGPU& S);
 // Upload the context's tables and create its stream on first GPU use.
 ed_status ensure_device(ed_ctx* ctx);
+// Refuse to launch when the current device is not the one the context's
+// tables live on (ED_ERR_STATE), or when a caller's device buffer belongs to
+// another device (ED_ERR_ARG); null entries of bufs are skipped.
+ed_status check_device(ed_ctx* ctx, std::initializer_list<const void*> bufs);
 bool is_device_ptr(const void* p);
 cudaError_t join_streams(cudaStream_t from, cudaStream_t to);
 std::vector<double> step_coefficients(const LatticeHost& L, const ed_pulse* pulse,

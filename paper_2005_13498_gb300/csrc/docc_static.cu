@@ -112,6 +112,9 @@ extern "C" ed_status ed_double_occupation_static(ed_ctx* ctx, const void* psi, e
                 "ed_double_occupation_static needs the context's tables on the device "
                 "already (call any GPU entry point on this context first)");
   if (!is_device_ptr(psi)) return fail(ctx, ED_ERR_ARG, "psi must be a device pointer");
+  // the tables and psi must live on the current device, whose scratch array
+  // the kernels below use
+  if (ed_status e = check_device(ctx, {psi})) return e;
   double* scratch = nullptr;
   CK(ctx, scratch_address(&scratch));
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -117,7 +117,7 @@ std::string gs_apply_setup(GsApply& G, ed_ctx* ctx, const double2* x, double2* w
   ED_TRY(upload(G.coefs, cf));
   ED_TRY(G.counters.alloc(sizeof(unsigned)));
   ED_TRY(cudaMemset(G.counters.p, 0, sizeof(unsigned)));
-  std::memset(&G.args, 0, sizeof(G.args));
+  init_batch_args(&G.args);
   G.args.sec = static_cast<const SectorDev*>(G.sec.p);
   G.args.vec = static_cast<VecDev*>(G.vec.p);
   G.args.st = static_cast<LanczosState*>(G.st.p);
@@ -181,15 +181,21 @@ ed_status ed_ground_state(ed_ctx* ctx, void* psi, double* E0, double tol, int ma
   if (!ctx || !psi || !E0) return fail(ctx, ED_ERR_ARG, "NULL argument");
   if (ed_status e = ensure_device(ctx)) return e;
   if (!(tol > 0.0) || max_iter < 1) return fail(ctx, ED_ERR_ARG, "tol must be > 0, max_iter >= 1");
+  if (ed_status e = check_device(ctx, {psi})) return e;
   cudaStream_t s = ctx->stream;
   const int64_t D = ctx->dim_up * ctx->dim_dn;
   // Krylov subspace size per restart, bounded by memory and by the multi-dot
   size_t free_b = 0, total_b = 0;
   CK(ctx, cudaMemGetInfo(&free_b, &total_b));
   int64_t kfit = (int64_t)(0.5 * (double)free_b / ((double)D * 16.0)) - 4;
+  // V holds K + 1 vectors, w and y one each
+  if (ctx->workspace_limit > 0)
+    kfit = std::min<int64_t>(kfit, ctx->workspace_limit / ((int64_t)D * 16) - 3);
   int K = (int)std::min<int64_t>(std::min<int64_t>(200, kfit), D);
   K = std::min(K, max_iter);
-  if (K < 2 && D > 1) return fail(ctx, ED_ERR_OOM, "not enough device memory for two Lanczos vectors");
+  if (K < 2 && D > 1)
+    return fail(ctx, ED_ERR_OOM,
+                "not enough device memory (or workspace limit) for two Lanczos vectors");
   if (D == 1) K = 1;
   DevMem V, w, y, part, red, cvec, cdev, sdev;
   CK(ctx, V.alloc((size_t)(K + 1) * D * 16));
@@ -260,8 +266,6 @@ ed_status ed_ground_state(ed_ctx* ctx, void* psi, double* E0, double tol, int ma
         ++k;
         break;
       }
-      double bb = b;
-      CK(ctx, cudaMemcpyAsync(redp, &bb, sizeof(double), cudaMemcpyHostToDevice, s));
       CK(ctx, cudaMemcpyAsync(vk(k + 1), wp, (size_t)D * 16, cudaMemcpyDeviceToDevice, s));
       CK(ctx, cudaMemcpyAsync(redp, &nd[0], sizeof(double), cudaMemcpyHostToDevice, s));
       CK(ctx, launch_scale(vk(k + 1), D, redp, true, s));
@@ -329,6 +333,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
   if (!std::isfinite(dt) || !std::isfinite(t_ref)) return fail(ctx, ED_ERR_ARG, "dt/t_ref not finite");
   if (ed_status e = check_pulse(ctx, pulse)) return e;
   if (ed_status e = ensure_device(ctx)) return e;
+  if (ed_status e = check_device(ctx, {psi0})) return e;
   cudaStream_t us = static_cast<cudaStream_t>(stream);
   cudaStream_t s = ctx->stream;
   const bool fp64 = dtype == ED_C128;
@@ -389,6 +394,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
   const int n_sub = n_steps * per;
   cfg.n_steps_cap = std::max(1, n_sub);
   cfg.eps_tol = ctx->krylov_tol;
+  cfg.workspace_limit = ctx->workspace_limit;
   CK(ctx, join_streams(us, s));
   if (!ctx->spec_engine || !ctx->spec_engine->compatible(cfg, vecs)) {
     ctx->spec_engine.reset(new Engine());
@@ -424,11 +430,12 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
   CKS(ctx, E.run(n_sub, false, nullptr, nullptr, s));
   std::vector<double> ov;
   CKS(ctx, E.fetch_overlaps(n_sub, ov, s));
-  int status = 0;
+  bool timed_out = false, non_finite = false;
   for (int v = 0; v < E.nvec(); ++v) {
     int st = 0;
     CKS(ctx, E.fetch(v, 0, nullptr, nullptr, nullptr, nullptr, nullptr, &st, s));
-    status |= st;
+    timed_out |= st == ED_ERR_TIMEOUT;
+    non_finite |= st != 0 && st != ED_ERR_TIMEOUT;
   }
   CK(ctx, cudaStreamSynchronize(s));
   CK(ctx, join_streams(s, us));
@@ -448,7 +455,9 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
         G_great[o + 1] = -re;
       }
     }
-  if (status != 0) return fail(ctx, ED_ERR_NUMERIC, "non-finite norm during spectral propagation");
+  if (timed_out)
+    return fail(ctx, ED_ERR_TIMEOUT, "a bounded device-side wait of the apply kernel gave up");
+  if (non_finite) return fail(ctx, ED_ERR_NUMERIC, "non-finite norm during spectral propagation");
   return ED_OK;
 }
 

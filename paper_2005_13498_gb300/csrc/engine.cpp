@@ -49,9 +49,26 @@ static std::atomic<int> g_forced_cfg{-1};
 void set_forced_apply_config(int cfg) { g_forced_cfg.store(cfg); }
 int forced_apply_config() { return g_forced_cfg.load(); }
 
+static std::atomic<int> g_withhold{-1};
+static std::atomic<uint32_t> g_wait_polls{0};
+void set_wait_fault(int withhold, uint32_t polls) {
+  g_withhold.store(withhold);
+  g_wait_polls.store(polls);
+}
+void init_batch_args(BatchArgs* a) {
+  std::memset(a, 0, sizeof(*a));
+  const uint32_t polls = g_wait_polls.load();
+  a->wait_limit = polls > 0 ? polls : kDefaultWaitLimit;
+  a->tma_withhold = g_withhold.load();
+}
+
 bool Engine::compatible(const EngineConfig& cfg, const std::vector<EngineVector>& vecs) const {
   const int forced = forced_apply_config();
   if (forced >= 0 && forced != shape_.cfg) return false;
+  BatchArgs now;
+  init_batch_args(&now);
+  if (now.wait_limit != args_.wait_limit || now.tma_withhold != args_.tma_withhold) return false;
+  if (cfg.workspace_limit > 0 && workspace_bytes_ > cfg.workspace_limit) return false;
   if (cfg.fp64 != cfg_.fp64 || cfg.m != cfg_.m || cfg.energy != cfg_.energy ||
       cfg.overlaps != cfg_.overlaps || cfg.n_steps_cap > cfg_.n_steps_cap ||
       cfg.eps_tol != cfg_.eps_tol)
@@ -211,9 +228,19 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     }
   }
 
-  // owned state buffers
-  int64_t owned = 0;
-  for (auto& v : vecs_) if (v.owned_x1) owned += v.D;
+  // owned state buffers, Krylov storage and scratch: checked against the
+  // context's workspace limit before anything is allocated
+  int64_t owned = 0, totD = 0;
+  for (auto& v : vecs_) {
+    if (v.owned_x1) owned += v.D;
+    totD += v.D;
+  }
+  const int64_t need = (owned + (int64_t)std::max(0, m - 1) * totD + totD) * (int64_t)esz;
+  workspace_bytes_ = need;
+  if (cfg.workspace_limit > 0 && need > cfg.workspace_limit)
+    return "device memory for the Krylov workspace (" + std::to_string(need) +
+           " bytes) exceeds the context's workspace limit (" +
+           std::to_string(cfg.workspace_limit) + " bytes)";
   ED_TRY(d_owned_x1_.alloc((size_t)owned * esz));
   {
     int64_t o = 0;
@@ -224,8 +251,6 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
       }
   }
   // Krylov storage and scratch
-  int64_t totD = 0;
-  for (auto& v : vecs_) totD += v.D;
   ED_TRY(d_V_.alloc((size_t)std::max(0, m - 1) * totD * esz));
   ED_TRY(d_w_.alloc((size_t)totD * esz));
 
@@ -292,7 +317,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
                          cudaMemcpyHostToDevice, stream));
   ED_TRY(cudaStreamSynchronize(stream));
 
-  std::memset(&args_, 0, sizeof(args_));
+  init_batch_args(&args_);
   args_.sec = static_cast<const SectorDev*>(d_sec_.p);
   args_.vec = static_cast<VecDev*>(d_vec_.p);
   args_.st = static_cast<LanczosState*>(d_st_.p);

@@ -38,6 +38,7 @@ struct EngineVector {
 };
 
 struct EngineConfig {
+  int64_t workspace_limit = 0;   // > 0: cap on the engine's device allocations (bytes)
   bool fp64 = false;
   int m = 1;
   bool energy = false;
@@ -68,6 +69,14 @@ struct ApplyTuneTarget {
 // configuration does not fit the precision or sector).
 void set_forced_apply_config(int cfg);
 int forced_apply_config();
+// Test hook of the bounded device-side waits (ed_set_wait_fault): the T_up
+// copy the TMA producer stops at (-1: none) and the poll limit of every
+// mbarrier wait (0: kDefaultWaitLimit); engines and plans set up afterwards
+// use them.
+void set_wait_fault(int withhold, uint32_t polls);
+// A BatchArgs with every field zero except the wait controls, which take the
+// current test-hook state (by default: no withheld copy, the default limit).
+void init_batch_args(BatchArgs* a);
 // Picks the apply configuration and returns its row-block map and (split
 // shapes) its column-block map.
 std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* shape,
@@ -109,6 +118,7 @@ class Engine {
   std::string capture(cudaStream_t s);
 
   EngineConfig cfg_;
+  int64_t workspace_bytes_ = 0;   // owned states + Krylov slots + scratch
   std::vector<EngineVector> vecs_;
   std::vector<SectorDev> sectors_;
   int n_groups_ = 0, Ns_ = 0;

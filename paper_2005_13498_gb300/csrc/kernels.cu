@@ -162,10 +162,9 @@ __device__ __forceinline__ const void* xptr(const VecDev& vd, int j, size_t esz)
 // of shared-memory slots (the configuration's stage count) with
 // cp.async.bulk; "full" mbarriers carry the byte count, "empty" mbarriers
 // collect one arrival per consumer warp.  Every wait is bounded: after
-// kTmaWaitLimit failed polls the thread records ED_ERR_TIMEOUT in the
+// BatchArgs::wait_limit failed polls the thread records ED_ERR_TIMEOUT in the
 // vector's status and a block-wide flag, and all later waits of the block
 // give up at once.
-constexpr uint32_t kTmaWaitLimit = 1u << 22;
 constexpr int kStatusTimeout = 4;    // ED_ERR_TIMEOUT
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -187,8 +186,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait for the phase of the given parity; false on timeout or when
 // another thread of the block has already timed out (err set).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err) {
-  for (uint32_t it = 0; it < kTmaWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err,
+                                          uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*err) return false;
   }
@@ -674,8 +674,14 @@ k_apply(BatchArgs a, int j) {
             const int e0 = __ldg(sd.up_off + urow[r]), e1 = __ldg(sd.up_off + urow[r] + 1);
             for (int e = e0; e < e1; ++e, ++idx) {
               const uint32_t q = idx % S;
+              // test hook: stop before this copy, as a stalled copy engine
+              // would (no copy of this block is left in flight afterwards)
+              if ((int)idx == a.tma_withhold) {
+                ok = false;
+                break;
+              }
               if (idx >= (uint32_t)S &&
-                  !mbar_wait(empty + q, ((idx / S) - 1u) & 1u, &tma_err)) {
+                  !mbar_wait(empty + q, ((idx / S) - 1u) & 1u, &tma_err, a.wait_limit)) {
                 ok = false;
                 break;
               }
@@ -692,7 +698,7 @@ k_apply(BatchArgs a, int j) {
           // wait (bounded, ignoring the flag) for the copies still in flight
           const uint32_t first = idx > (uint32_t)S ? idx - S : 0u;
           for (uint32_t k = first; k < idx; ++k)
-            for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
+            for (uint32_t it = 0; it < a.wait_limit; ++it)
               if (mbar_try_wait(full + k % S, (k / S) & 1u)) break;
         }
       }
@@ -828,7 +834,7 @@ k_apply(BatchArgs a, int j) {
             const uint32_t ent = nent;
             if (e + 1 < e1) nent = __ldg(sd.up_ent + e + 1);   // next entry under this one
             const uint32_t q = cidx % S;
-            const bool ready = mbar_wait(full + q, (cidx / S) & 1u, &tma_err);
+            const bool ready = mbar_wait(full + q, (cidx / S) & 1u, &tma_err, a.wait_limit);
             const char* slot = ring + (size_t)q * kSlotBytes;
             C v[2 * PP];
 #pragma unroll

@@ -85,6 +85,8 @@ def _load():
         "ed_apply_config_info": [I] + [ctypes.POINTER(ctypes.c_int)] * 6,
         "ed_set_apply_config": [I],
         "ed_set_krylov_tol": [P, D],
+        "ed_set_workspace_limit": [P, ctypes.c_int64],
+        "ed_set_wait_fault": [I, ctypes.c_int64],
         "ed_set_integrator": [P, I],
         "ed_get_apply_config": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "ed_destroy": [P],
@@ -300,6 +302,18 @@ def ed_set_krylov_tol(ctx, tol):
     """0: fixed Krylov dimension m (default); > 0: adaptive exit of
     Algorithm 6 with m as the maximum."""
     _check(lib.ed_set_krylov_tol(ctx, float(tol)), ctx)
+
+
+def ed_set_workspace_limit(ctx, nbytes):
+    """Cap (bytes) on the Krylov workspace of the context's propagations and
+    ground-state solves; 0 = no cap."""
+    _check(lib.ed_set_workspace_limit(ctx, int(nbytes)), ctx)
+
+
+def ed_set_wait_fault(withhold_copy=-1, wait_polls=0):
+    """Test hook of the bounded device-side waits (process-wide): the T_up
+    copy the TMA producer stops at (-1: none) and the poll limit (0: default)."""
+    _check(lib.ed_set_wait_fault(int(withhold_copy), int(wait_polls)))
 
 
 def ed_set_integrator(ctx, scheme):

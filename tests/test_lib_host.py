@@ -232,3 +232,46 @@ def test_spectral_function_host_transform_matches_oracle(ed):
     for bad in ((0.0, 0.1), (0.05, -1.0)):
         with pytest.raises(ed.EDError):
             ed.ed_spectral_function(G, bad[0], bad[1], nu)
+
+
+def test_device_verdict_refuses_foreign_devices(tmp_path):
+    """Every GPU entry point refuses to launch when the current device is not
+    the one the context's tables live on (ED_ERR_STATE) or when a caller's
+    device buffer lives on another device (ED_ERR_ARG): the decision, compiled
+    from csrc/device_guard.h and run on the host (one GPU cannot make the
+    devices differ)."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    csrc = os.path.join(ROOT, "paper_2005_13498_gb300", "csrc")
+    exe = str(tmp_path / "device_guard_check")
+    subprocess.run([gxx, "-std=c++17", "-O2", "-I", csrc,
+                    os.path.join(ROOT, "tests", "host", "device_guard_check.cpp"), "-o", exe],
+                   check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = [tuple(int(x) for x in ln.split()) for ln in out if ln.strip()]
+    ok, wrong_current, foreign = 0, 1, 2
+    want = {(0, 0, -1): ok, (0, 0, 0): ok, (1, 1, 1): ok, (1, 1, -1): ok,
+            (0, 1, -1): wrong_current, (1, 0, 0): wrong_current, (0, 1, 1): wrong_current,
+            (0, 0, 1): foreign, (1, 1, 0): foreign, (2, 2, 3): foreign}
+    assert len(got) == len(want)
+    for c0, c1, c2, v in got:
+        assert want[(c0, c1, c2)] == v, (c0, c1, c2, v)
+
+
+def test_new_control_calls_validate_arguments(ed):
+    ctx = ed.ed_build_basis(4, 2, 2)
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_set_workspace_limit(ctx, -1)
+    assert e.value.status == 1
+    ed.ed_set_workspace_limit(ctx, 0)
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_set_wait_fault(-2, 0)
+    assert e.value.status == 1
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_set_wait_fault(-1, -5)
+    assert e.value.status == 1
+    ed.ed_set_wait_fault(-1, 0)
+    ed.ed_destroy(ctx)
