@@ -20,3 +20,18 @@ def ed_lib():
     """The built C-ABI library through its Python binding (GPU tests only)."""
     from paper_2005_13498_gb300 import ed
     return ed
+
+
+@pytest.fixture(scope="session")
+def parity_log():
+    """Records measured errors of the parity tests as JSON lines in the file
+    named by ED_PARITY_LOG (nothing is written when it is unset)."""
+    import json
+    path = os.environ.get("ED_PARITY_LOG")
+
+    def record(test, **values):
+        if path:
+            with open(path, "a") as f:
+                f.write(json.dumps({"test": test, **{k: float(v) for k, v in values.items()}})
+                        + "\n")
+    return record

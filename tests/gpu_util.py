@@ -30,6 +30,21 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def max_el(a, b):
+    """Largest element error relative to the largest reference element:
+    max_k |a_k - b_k| / max_k |b_k| (a local error, e.g. in a few rows,
+    cannot hide under the norm of a large vector)."""
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+# Per-element bound of the apply tests, relative to max |w|: complex128 ~
+# rounding of a sum of at most 2 * 19 + 1 terms; complex64 about 40 float32
+# roundings of 6e-8 on terms no larger than the largest |w|, with margin.
+TOL_EL = {"c128": 1e-13, "c64": 5e-6}
+
+
 def ed_dtype(ed, name):
     return ed.ED_C128 if name == "c128" else ed.ED_C64
 

@@ -9,7 +9,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import LATTICES, torch_cuda, to_dev, from_dev, rel_l2, ed_dtype
+from gpu_util import (LATTICES, torch_cuda, to_dev, from_dev, rel_l2, ed_dtype, max_el,
+                      TOL_EL)
 from oracle.krylov import make_H
 
 pytestmark = pytest.mark.gpu
@@ -43,11 +44,12 @@ def test_apply_matches_oracle(ed_lib, dtype, name, nu, nd, U):
     torch.cuda.synchronize()
     w = from_dev(wd)
     assert rel_l2(w, ref) <= TOL[dtype]
+    assert max_el(w, ref) <= TOL_EL[dtype]
     h.close()
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_apply_full_size_ladder(ed_lib, dtype):
+def test_apply_full_size_ladder(ed_lib, dtype, parity_log):
     """Ns = 14 ladder, (7,7), D = 11,778,624: the configuration the step bench
     runs, compared on every element."""
     torch = torch_cuda()
@@ -62,7 +64,10 @@ def test_apply_full_size_ladder(ed_lib, dtype):
     wd = torch.zeros_like(vd)
     ed.ed_apply_H(h.ctx, vd, wd, ed_dtype(ed, dtype))
     torch.cuda.synchronize()
-    assert rel_l2(from_dev(wd), ref) <= TOL[dtype]
+    w = from_dev(wd)
+    assert rel_l2(w, ref) <= TOL[dtype]
+    assert max_el(w, ref) <= TOL_EL[dtype]
+    parity_log(f"apply_ladder_full_{dtype}", rel_l2=rel_l2(w, ref), max_el=max_el(w, ref))
     h.close()
 
 
@@ -82,6 +87,7 @@ def test_apply_long_rows_ns16(ed_lib):
         ed.ed_apply_H(h.ctx, vd, wd, ed_dtype(ed, dtype))
         torch.cuda.synchronize()
         assert rel_l2(from_dev(wd), ref) <= TOL[dtype]
+        assert max_el(from_dev(wd), ref) <= TOL_EL[dtype]
     h.close()
 
 

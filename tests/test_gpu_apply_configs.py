@@ -19,7 +19,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import LATTICES, torch_cuda, to_dev, from_dev, rel_l2, ed_dtype
+from gpu_util import (LATTICES, torch_cuda, to_dev, from_dev, rel_l2, ed_dtype, max_el,
+                      TOL_EL)
 from oracle.krylov import make_H
 
 pytestmark = pytest.mark.gpu
@@ -81,8 +82,10 @@ def test_every_config_matches_oracle(pinned, dtype, name, lat, nu, nd, U):
         ed.ed_apply_H(h.ctx, vd, wd, ed_dtype(ed, dtype), nvec=2)
         torch.cuda.synchronize()
         assert ed.ed_get_apply_config(h.ctx)[1] == cfg
-        err = rel_l2(from_dev(wd), ref)
+        w = from_dev(wd)
+        err = rel_l2(w, ref)
         assert err <= TOL[dtype], (cfg, ed.ed_apply_config_info(cfg), err)
+        assert max_el(w, ref) <= TOL_EL[dtype], (cfg, max_el(w, ref))
     h.close()
 
 

@@ -7,7 +7,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import LATTICES, torch_cuda, to_dev, from_dev, rel_l2, ed_dtype
+from gpu_util import (LATTICES, torch_cuda, to_dev, from_dev, rel_l2, ed_dtype, max_el,
+                      TOL_EL)
 from oracle.krylov import make_H
 
 pytestmark = pytest.mark.gpu
@@ -87,4 +88,5 @@ def test_batched_apply_ragged_row_blocks(ed_lib, dtype):
         torch.cuda.synchronize()
         tol = 1e-13 if dtype == "c128" else 3e-6
         assert rel_l2(from_dev(wd), ref) <= tol
+        assert max_el(from_dev(wd), ref) <= TOL_EL[dtype]
         h.close()

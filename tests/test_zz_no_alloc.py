@@ -5,7 +5,8 @@ memory is fixed up front, a host application enforcing its own memory budget);
 this entry point keeps its scratch in a fixed array inside the library.  These
 tests call it through the C ABI and check it against ed_double_occupation,
 within the tolerances the other double-occupancy tests use, on two calls in a
-row.  The file name puts it last in collection order.
+row, and near its fixed maximum against the oracle.  The file name puts it
+last in collection order.
 """
 import numpy as np
 import pytest
@@ -53,3 +54,31 @@ def test_static_rejects_oversized_sector_and_unprepared_context(ed_lib):
         ed.ed_double_occupation_static(fresh.ctx, v, ed.ED_C128)
     assert e.value.status == 6
     fresh.close()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_static_near_its_maximum_matches_oracle(ed_lib, dtype):
+    """The 16-site ring at (6,6): D = 8008^2 = 64,128,064 elements, 979 of the
+    1024 partial-sum rows of the fixed array, the last one partly filled;
+    average and per-site values against the oracle's sums over the same
+    (for complex64: rounded) vector."""
+    import oracle
+    torch = torch_cuda()
+    ed = ed_lib
+    code = ed.ED_C128 if dtype == "c128" else ed.ED_C64
+    h = ed.Hubbard(synth.ring(16), 6, 6, 4.0)
+    assert h.D == 64128064
+    v = synth.complex_normal(h.D, 8)
+    if dtype == "c64":
+        v = v.astype(np.complex64).astype(np.complex128)
+    vd = to_dev(torch, v, dtype)
+    ed.ed_double_occupation(h.ctx, vd, code)         # tables onto the device
+    d, site = ed.ed_double_occupation_static(h.ctx, vd, code)
+    w = oracle.double_occupancy_weights(16, 6, 6)
+    assert abs(d - oracle.double_occupation(v, w, 16)) <= 1e-12
+    bu = oracle.spin_basis(16, 6)
+    P = (np.abs(v) ** 2).reshape(len(bu), len(bu))
+    for i in range(16):
+        occ = ((bu >> np.uint64(i)) & np.uint64(1)) == 1
+        assert abs(site[i] - P[np.ix_(occ, occ)].sum()) <= 1e-11
+    h.close()
