@@ -10,7 +10,8 @@ every rank propagates its own copy of the workload (independent replicas, no
 collective on the data path); value = (max-rank time) / (N * K).
 
 The reference arm (--impl reference) times the float64 CPU oracle on the host
-cores, on a bounded sample of each step (see cpu_sample()).
+cores: every timed step is one whole oracle midpoint step of the same
+workload (cpu_full_step()), the warm-up steps a bounded sample (cpu_warmup()).
 """
 import argparse
 import json
@@ -60,6 +61,10 @@ def parse():
                     help="run 4 plain applies at the bench size and exit (profiler target)")
     ap.add_argument("--apply-workload", default=WORKLOAD,
                     help="workload of --apply-only (default: the bench's ladder)")
+    ap.add_argument("--spectral-only", action="store_true",
+                    help="run one small spectral batch (3x4 torus, 48 c/c+ vectors + psi, "
+                         "m=4, 2 steps) and exit (profiler target of the overlap and "
+                         "fermion-operator kernels)")
     return ap.parse_args()
 
 
@@ -153,41 +158,34 @@ def job_value(t_ms, ws, steps):
     return t_ms / (ws * steps)
 
 
-def cpu_sample(w, lat, n_iter=2, reps=1):
-    """Oracle (float64: scipy sparse Kronecker operator, numpy BLAS-1) on a
-    bounded sample of one midpoint step, scaled to a full step:
-    t_step = t(H(t_mid) build) + m * t(one Lanczos iteration) + m * t(one
-    axpy of the final combination).  n_iter Lanczos iterations and one axpy
-    are timed; the m x m exponential is negligible."""
+def cpu_full_step(w, lat, psi=None, t=None):
+    """One whole midpoint step of the oracle (float64: H(t_mid) as the scipy
+    sparse Kronecker operator, m Lanczos iterations with NumPy BLAS-1, the
+    m x m exponential and the combination, <d> and |psi|^2), as it stands,
+    from a seeded state inside the pulse.  Returns (ms, psi after the step,
+    t after the step, sample description)."""
+    import oracle
+    if psi is None:
+        D = oracle.sector_dims(lat["Ns"], w["n_up"], w["n_dn"])[2]
+        psi = np.asarray(__import__("synth").complex_normal(D, 0))
+    if t is None:
+        t = w["pulse_params"]["t0"] - 1.0
+    t0 = time.perf_counter()
+    r = oracle.propagate(lat, w["n_up"], w["n_dn"], w["U"], psi, w["pulse_params"], w["dt"],
+                         1, w["m"], t_start=t, form="kron")
+    ms = (time.perf_counter() - t0) * 1e3
+    return ms, r["psi"], t + w["dt"], (f"one full midpoint step of the oracle (H(t_mid), "
+                                       f"{w['m']} Lanczos iterations, exponential, combination, "
+                                       f"<d>, |psi|^2), measured, not extrapolated")
+
+
+def cpu_warmup(w, lat):
+    """An untimed bounded sample: H(t_mid) and one product H v."""
     import oracle
     from oracle.krylov import make_H
-    m = w["m"]
     D = oracle.sector_dims(lat["Ns"], w["n_up"], w["n_dn"])[2]
-    psi = np.asarray(__import__("synth").complex_normal(D, 0))
-    pulse = w["pulse_params"]
-    best = None
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        H = make_H(lat, w["n_up"], w["n_dn"], w["U"], oracle.pulse_A(9.01, pulse), "kron")
-        t1 = time.perf_counter()
-        v = psi / np.linalg.norm(psi)
-        vprev, bprev = None, 0.0
-        for j in range(n_iter):
-            x = H @ v
-            if vprev is not None:
-                x = x - bprev * vprev
-            a = np.vdot(v, x).real
-            x = x - a * v
-            b = np.linalg.norm(x)
-            vprev, v, bprev = v, x / b, b
-        t2 = time.perf_counter()
-        acc = 0.3 * v
-        acc += (0.1 + 0.2j) * vprev
-        t3 = time.perf_counter()
-        est = (t1 - t0) + m * (t2 - t1) / n_iter + m * (t3 - t2)
-        best = est if best is None else min(best, est)
-    return best * 1e3, (f"H(t_mid) build + {n_iter} of {m} Lanczos iterations + 1 axpy, "
-                        f"scaled to build + {m} iterations + {m} axpys")
+    H = make_H(lat, w["n_up"], w["n_dn"], w["U"], oracle.pulse_A(9.01, w["pulse_params"]), "kron")
+    H @ np.asarray(__import__("synth").complex_normal(D, 1))
 
 
 def small_oracle_steps():
@@ -248,11 +246,21 @@ def spectral_bench(ed, torch, synth, lat, w, pulse, h, psi64, stream, barrier, s
                     "a vector of the same dimension"}
 
 
+def kernel_sources_sha256():
+    """sha256 over every file of csrc/ (sorted by name) and include/ed.h."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_13498_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "ed.h"), "rb").read())
+    return h.hexdigest()
+
+
 def profiled_traffic(apply_config):
     """DRAM bytes per Lanczos-pass apply from the committed ncu summary, or
     None when the kernel sources or the configuration differ from the
     profiled ones (the counters no longer describe this kernel)."""
-    import hashlib
     import re
     path = os.path.join(ROOT, "profiles", "apply_ladder2x7_c64_lanczos_dram.md")
     if not os.path.exists(path):
@@ -263,10 +271,7 @@ def profiled_traffic(apply_config):
     cfg = re.search(r"apply configuration (\d+)", txt)
     if not (want and val and cfg) or int(cfg.group(1)) != apply_config:
         return None
-    h = hashlib.sha256()
-    for f in ("kernels.cu", "tables.cpp", "engine.cpp"):
-        h.update(open(os.path.join(ROOT, "paper_2005_13498_gb300", "csrc", f), "rb").read())
-    return int(val.group(1)) if h.hexdigest() == want.group(1) else None
+    return int(val.group(1)) if kernel_sources_sha256() == want.group(1) else None
 
 
 def adaptive_bench(ed, torch, h, psi32, pulse, t_start, dt, m, stream, barrier, steps):
@@ -480,6 +485,16 @@ def smaller_workloads_bench(ed, torch, synth, stream, barrier, steps):
     return out
 
 
+def bench_config(t_start, m, ws):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": "Ns=14 2x7 ladder (periodic legs, open rungs), n_up=n_dn=7, "
+                        "D=11,778,624, U=8, m=30, dt=0.02, pulse A0=0.5 Omega=8 "
+                        "sigma=2 t0=10 along the legs",
+            "t_start": t_start, "m": m, "parallelism": f"replicas x{ws}",
+            "l2": "no flush: per-step working set 2.9 GB (31 Krylov vectors of "
+                  "94 MB) > 129 MB L2"}
+
+
 def reference_arm(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -488,10 +503,12 @@ def reference_arm(args):
     w = synth.workload(WORKLOAD)
     lat = synth.lattice_from_name(w["lattice"])
     for _ in range(args.warmup):
-        cpu_sample(w, lat)
+        cpu_warmup(w, lat)
     per = []
+    psi, t = None, None
+    desc = ""
     for _ in range(args.steps):
-        ms, desc = cpu_sample(w, lat)
+        ms, psi, t, desc = cpu_full_step(w, lat, psi, t)
         per.append(ms)
     val = float(np.mean(per))
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
@@ -499,10 +516,10 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": val, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Ns=14 2x7 ladder (7,7) D=11,778,624, m=30, dt=0.02",
-                       "sample": desc},
+            "config": bench_config(w["pulse_params"]["t0"] - 1.0, w["m"], 1),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc + f"; {args.steps} consecutive steps, "
+                                              f"warm-up: {args.warmup} x (H(t_mid), one H v)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -551,6 +568,18 @@ def main():
         print(json.dumps({"apply_only": args.apply_only, "D": h.D}))
         h.close()
         return
+    if args.spectral_only:
+        ws_ = synth.workload("torus3x4_spectral")
+        lat_ = synth.lattice_from_name(ws_["lattice"])
+        h = ed.Hubbard(lat_, ws_["n_up"], ws_["n_dn"], ws_["U"])
+        psi = torch.from_numpy(synth.complex_normal(h.D, 0)).cuda()
+        gl, gg = ed.ed_spectral_propagate(h.ctx, psi, ed.ED_C64, ws_["pulse_params"],
+                                          ws_["dt"], 2, 4, 12)
+        torch.cuda.synchronize()
+        print(json.dumps({"spectral_only": "torus3x4", "D": h.D,
+                          "G_less_00": [float(gl[0, 0, 0].real), float(gl[0, 0, 0].imag)]}))
+        h.close()
+        return
     t_start = pulse["t0"] - 1.0        # inside the pulse: full Krylov dimension
     h = ed.Hubbard(lat, w["n_up"], w["n_dn"], w["U"])
     D = h.D
@@ -597,19 +626,17 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "Ns=14 2x7 ladder (periodic legs, open rungs), n_up=n_dn=7, "
-                                   "D=11,778,624, U=8, m=30, dt=0.02, pulse A0=0.5 Omega=8 "
-                                   "sigma=2 t0=10 along the legs",
-                       "t_start": t_start, "m": m, "m_eff_min": int(m_eff.min()),
-                       "parallelism": f"replicas x{ws}",
-                       "l2": "no flush: per-step working set 2.9 GB (31 Krylov vectors of "
-                             "94 MB) > 129 MB L2"},
+            "config": bench_config(t_start, m, ws), "m_eff_min": int(m_eff.min()),
             "clocks": clk.summary(), "gpu_launches": gpu_launches,
             "apply_kernel": dict(ainfo, config=acfg),
             "ground_state": {"E0": E0, "residual": resid}}
 
     if not args.no_extras:
         peak, peak_kind = measured_peaks()
+        # on-chip ceilings (L2 and shared-memory read rates, FMA rates) that
+        # bound the apply when DRAM does not
+        from paper_2005_13498_gb300 import probes
+        line["ceilings"] = probes.ed_probe_ceilings()
         # per-kernel device time (event pair around every launch, same K steps)
         prof = ed.ed_propagate(h.ctx, psi32, ed.ED_C64, pulse, t_start, dt, args.steps, m,
                                profile=True, stream=stream)
@@ -720,9 +747,9 @@ def main():
                        "note": "one ed_propagate call per step on a pinned host buffer"}
         # CPU oracle on this host (rank 0, N = 1 only)
         if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-            import torch as _t
-            cms, desc = cpu_sample(w, lat, n_iter=2)
-            cores = _t.get_num_threads()
+            cms, _, _, desc = cpu_full_step(w, lat)
+            cores = (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                     else os.cpu_count())
             line["cpu_baseline"] = {"value": cms, "unit": UNIT, "cores": cores,
                                     "kind": "oracle", "sample": desc}
             if not args.no_small:

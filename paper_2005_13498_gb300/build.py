@@ -45,6 +45,33 @@ def lib_path():
     return os.path.join(OUT_DIR, LIB_NAME)
 
 
+PROBES_NAME = "libed_probes.so"
+
+
+def probes_path():
+    return os.path.join(OUT_DIR, PROBES_NAME)
+
+
+def build_probes(force=False):
+    """libed_probes.so (include/ed_probes.h): the on-chip ceiling probes that
+    the benchmark reports beside the roofline."""
+    cuda = cuda_home()
+    nvcc = os.path.join(cuda, "bin", "nvcc")
+    src = os.path.join(CSRC, "probes.cu")
+    hdr = os.path.join(os.path.dirname(HERE), "include", "ed_probes.h")
+    target = probes_path()
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(target):
+        if os.path.getmtime(target) >= max(os.path.getmtime(src), os.path.getmtime(hdr)):
+            return target
+    tmp = target + ".tmp"
+    _run([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                          "-shared", src, "-o", tmp, "-lcudart",
+                          "-Xlinker", "-rpath," + os.path.join(cuda, "lib64")])
+    os.replace(tmp, target)
+    return target
+
+
 def build(verbose=False, force=False):
     cuda = cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
@@ -58,6 +85,7 @@ def build(verbose=False, force=False):
     if not force and os.path.exists(target):
         newest = max(os.path.getmtime(p) for p in srcs + headers + [__file__])
         if os.path.getmtime(target) >= newest:
+            build_probes()
             return target
     jobs = []
     objs = []
@@ -72,8 +100,10 @@ def build(verbose=False, force=False):
         objs.append(o)
         jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-Wno-unused-function",
                      "-I", inc, "-c", os.path.join(CSRC, s), "-o", o])
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs) + 1)) as ex:
+        probes = ex.submit(build_probes, force)
         logs = list(ex.map(_run, jobs))
+        probes.result()
     if verbose:
         for cmd, log in zip(jobs, logs):
             print(" ".join(cmd))

@@ -26,18 +26,23 @@ def ed():
     return mod
 
 
-def header_functions():
-    src = open(os.path.join(ROOT, "include", "ed.h")).read()
+def header_functions(name="ed.h"):
+    src = open(os.path.join(ROOT, "include", name)).read()
     return sorted(set(re.findall(r"^\s*(?:ed_status|const char\*|int)\s+(ed_\w+)\s*\(",
                                  src, re.M)))
 
 
 def test_library_exports_every_declared_symbol(ed):
-    names = header_functions()
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert headers == ["ed.h", "ed_probes.h"]
+    names = header_functions("ed.h")
     assert len(names) >= 16
     for n in names:
         assert hasattr(ed.lib, n), n
     assert "sm_103a" in ed.ed_version()
+    from paper_2005_13498_gb300 import probes
+    for n in header_functions("ed_probes.h"):
+        assert hasattr(probes.lib, n), n
 
 
 def test_errors_without_gpu_work(ed):
