@@ -338,17 +338,34 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
   cudaStream_t s = ctx->stream;
   const bool fp64 = dtype == ED_C128;
   const int Ns = ctx->Ns;
-  // sector list: 0 = N, then the N -+ 1 sectors that exist
+  // sector list: 0 = N, then the N -+ 1 sectors the phi vectors live in.  A
+  // down-spin phi of sector (n_up, n_dn -+ 1) is stored transposed, as a
+  // vector of the swapped sector (n_dn -+ 1, n_up): T_up and T_dn depend only
+  // on the particle number, so the Hamiltonian of the swapped sector is the
+  // same operator on the transposed matrix.  Its rows then have the length
+  // C(Ns, n_up) of the up-spin phi's rows, and at half filling the two
+  // operators of one kind share one sector (rows of an even length keep the
+  // 16-byte accesses of the apply for every vector of the batch).
   struct Target { int n_up, n_dn; };
-  const Target tg[4] = {{ctx->n_up - 1, ctx->n_dn}, {ctx->n_up, ctx->n_dn - 1},
-                        {ctx->n_up + 1, ctx->n_dn}, {ctx->n_up, ctx->n_dn + 1}};
+  const Target tg[4] = {{ctx->n_up - 1, ctx->n_dn}, {ctx->n_dn - 1, ctx->n_up},
+                        {ctx->n_up + 1, ctx->n_dn}, {ctx->n_dn + 1, ctx->n_up}};
+  auto exists = [&](const Target& t) {
+    return t.n_up >= 0 && t.n_up <= Ns && t.n_dn >= 0 && t.n_dn <= Ns;
+  };
+  // k aliases the first j < k with the same sector (or is itself the first)
+  int first_of[4];
+  for (int k = 0; k < 4; ++k) {
+    first_of[k] = k;
+    for (int j = 0; j < k; ++j)
+      if (tg[j].n_up == tg[k].n_up && tg[j].n_dn == tg[k].n_dn) { first_of[k] = j; break; }
+  }
   int sector_of[4];
   std::vector<SectorDev> secs = {ctx->sec.dev};
   std::vector<const SpinTable*> up_tabs = {&ctx->sec.up};
   if (ctx->spec_sectors.empty()) {
     for (int k = 0; k < 4; ++k) {
       std::unique_ptr<SectorGPU> S;
-      if (tg[k].n_up >= 0 && tg[k].n_up <= Ns && tg[k].n_dn >= 0 && tg[k].n_dn <= Ns) {
+      if (exists(tg[k]) && first_of[k] == k) {
         S.reset(new SectorGPU());
         CK(ctx, build_sector_gpu(*S, ctx->lat, tg[k].n_up, tg[k].n_dn));
       }
@@ -356,15 +373,18 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
     }
   }
   for (int k = 0; k < 4; ++k) {
-    if (ctx->spec_sectors[k]) {
+    if (!exists(tg[k])) {
+      sector_of[k] = -1;
+    } else if (first_of[k] != k) {
+      sector_of[k] = sector_of[first_of[k]];
+    } else {
       sector_of[k] = (int)secs.size();
       secs.push_back(ctx->spec_sectors[k]->dev);
       up_tabs.push_back(&ctx->spec_sectors[k]->up);
-    } else {
-      sector_of[k] = -1;
     }
   }
-  // vectors: psi, then for op (0: c, 1: c^+), spin, site
+  // vectors: psi, then for op (0: c, 1: c^+), spin, site; map mode 0 (row
+  // map) for the up spin, 2 (column map, vector stored transposed) for down
   struct Phi { int op, spin, site, vec; };
   std::vector<Phi> phis;
   std::vector<EngineVector> vecs = {{0, ctx->dim_up * ctx->dim_dn, nullptr, true}};
@@ -381,7 +401,7 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
         vecs.push_back({sector_of[k], (int64_t)sd.dim_up * sd.dim_dn, nullptr, true});
         std::vector<int32_t> mp = fermion_map(Ns, ctx->n_up, ctx->n_dn, site, spin, op == 1);
         moff.push_back((int64_t)maps.size());
-        mspin.push_back(spin);
+        mspin.push_back(spin == 0 ? 0 : 2);
         maps.insert(maps.end(), mp.begin(), mp.end());
       }
     }
@@ -421,9 +441,11 @@ ed_status ed_spectral_propagate_at(ed_ctx* ctx, const void* psi0, double t_ref,
   DevMem dmaps;
   CK(ctx, upload(dmaps, maps));
   for (const Phi& f : phis) {
+    // the target sector's shape (the stored shape transposed for spin 1)
     const SectorDev& sd = secs[vecs[f.vec].sector];
+    const int du = f.spin == 0 ? sd.dim_up : sd.dim_dn, dd = f.spin == 0 ? sd.dim_dn : sd.dim_up;
     CK(ctx, launch_fermion_op(fp64, E.vec_x1(0), E.vec_x1(f.vec), (int)ctx->dim_up,
-                              (int)ctx->dim_dn, sd.dim_up, sd.dim_dn, f.spin,
+                              (int)ctx->dim_dn, du, dd, f.spin == 0 ? 0 : 2,
                               static_cast<const int32_t*>(dmaps.p) + moff[f.vec], s));
   }
   CKS(ctx, E.begin(sub.coefs, {}, n_sub, sub.tau, s));

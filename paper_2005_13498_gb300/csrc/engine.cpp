@@ -41,8 +41,9 @@ size_t Engine::device_bytes() const {
   return d_sec_.bytes + d_vec_.bytes + d_st_.bytes + d_amap_.bytes + d_cmap_.bytes +
          d_emap_.bytes +
          d_partials_.bytes + d_counters_.bytes + d_coefs_.bytes + d_coefs_obs_.bytes +
-         d_V_.bytes + d_w_.bytes + d_out_.bytes + d_owned_x1_.bytes + d_maps_.bytes +
-         d_map_off_.bytes + d_map_spin_.bytes + d_ovl_.bytes;
+         d_V_.bytes + d_w_.bytes + d_w2_.bytes + d_out_.bytes + d_owned_x1_.bytes +
+         d_maps_.bytes +
+         d_map_off_.bytes + d_map_spin_.bytes + d_ovl_.bytes + d_psiT_.bytes;
 }
 
 static std::atomic<int> g_forced_cfg{-1};
@@ -235,7 +236,10 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     if (v.owned_x1) owned += v.D;
     totD += v.D;
   }
-  const int64_t need = (owned + (int64_t)std::max(0, m - 1) * totD + totD) * (int64_t)esz;
+  // (float32 engines count a second scratch vector, which the fused Lanczos
+  // passes of one-kernel apply configurations need)
+  const int64_t need =
+      (owned + (int64_t)std::max(0, m - 1) * totD + (cfg.fp64 ? 1 : 2) * totD) * (int64_t)esz;
   workspace_bytes_ = need;
   if (cfg.workspace_limit > 0 && need > cfg.workspace_limit)
     return "device memory for the Krylov workspace (" + std::to_string(need) +
@@ -281,7 +285,10 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     voff += v.D;
 
     v.ew_begin = (int)emap.size();
-    const int64_t ch = ew_chunk(v.D);
+    // one chunk size for the whole batch, from its total size: sized per
+    // vector, a batch of 49 small vectors got 35,000 blocks of 1024
+    // elements, each paying a block reduction
+    const int64_t ch = ew_chunk(totD);
     for (int64_t b = 0; b < v.D; b += ch) emap.push_back({i, 0, b, std::min(v.D, b + ch)});
     v.ew_end = (int)emap.size();
     double* base = static_cast<double*>(d_out_.p) + per_vec_out * i;
@@ -355,6 +362,20 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   std::string err = tune_apply(tt, stream, &shape_, &amap, &cmap);
   if (!err.empty()) return err;
   ED_TRY(prepare_apply(cfg.fp64, shape_));
+  // fused Lanczos passes (float32, one-kernel configurations): pass j forms
+  // x_j and beta_j itself, and the y_j it gathers alternate between w and w2
+  fused_ = !cfg.fp64 && !shape_.split && !shape_.tma;
+  if (fused_) {
+    ED_TRY(d_w2_.alloc((size_t)totD * esz));
+    int64_t off = 0;
+    for (int i = 0; i < nv; ++i) {
+      vd[i].w2 = static_cast<char*>(d_w2_.p) + (size_t)off * esz;
+      off += vd[i].D;
+    }
+  } else {
+    d_w2_.release();
+  }
+  args_.fused = fused_ ? 1 : 0;
   n_apply_ = (int)amap.size();
   for (int i = 0; i < nv; ++i) {
     vd[i].apply_begin = -1;
@@ -406,6 +427,16 @@ std::string Engine::set_overlap_maps(const std::vector<int32_t>& maps,
   oargs_.map_spin = static_cast<const int32_t*>(d_map_spin_.p);
   oargs_.psi_index = psi_index;
   oargs_.out = static_cast<double*>(d_ovl_.p);
+  // column maps of vectors stored transposed (mode 2) read psi transposed:
+  // one copy, refreshed before every overlap launch
+  need_psiT_ = std::find(spin.begin(), spin.end(), 2) != spin.end();
+  if (need_psiT_) {
+    const size_t esz = cfg_.fp64 ? 16 : 8;
+    ED_TRY(d_psiT_.alloc((size_t)vecs_[psi_index].D * esz));
+  } else {
+    d_psiT_.release();
+  }
+  oargs_.psiT = d_psiT_.p;
   have_overlaps_ = true;
   if (exec_) { cudaGraphExecDestroy(exec_); exec_ = nullptr; }
   if (graph_) { cudaGraphDestroy(graph_); graph_ = nullptr; }
@@ -480,7 +511,8 @@ std::string Engine::launch_step(cudaStream_t s, bool profile, cudaEvent_t* ev, i
     if (adaptive && j >= 3) ED_TRY(cudaStreamWaitEvent(s, ev_check_[j - 2], 0));
     STEP_LAUNCH(KK_APPLY, launch_apply(f, args_, n_apply_, shape_, j, s));
     if (j < cfg_.m) {
-      STEP_LAUNCH(KK_UPDATE, launch_update(f, args_, n_ew_, j, s));
+      // fused passes compute x_{j+1}'s norm in the apply: no update pass
+      if (!fused_) STEP_LAUNCH(KK_UPDATE, launch_update(f, args_, n_ew_, j, s));
       if (adaptive) {
         ED_TRY(cudaEventRecord(ev_fork_[j], s));
         ED_TRY(cudaStreamWaitEvent(side_, ev_fork_[j], 0));
@@ -493,9 +525,18 @@ std::string Engine::launch_step(cudaStream_t s, bool profile, cudaEvent_t* ev, i
   STEP_LAUNCH(KK_EXPM, launch_expm(args_, s));
   STEP_LAUNCH(KK_COMBINE, launch_combine(f, args_, n_ew_, s));
   if (cfg_.energy) STEP_LAUNCH(KK_ENERGY, launch_apply(f, args_, n_apply_, shape_, -1, s));
-  if (have_overlaps_) STEP_LAUNCH(KK_OVERLAP, launch_overlap(f, args_, oargs_, n_ew_, s));
+  if (have_overlaps_) {
+    if (need_psiT_) STEP_LAUNCH(KK_OVERLAP, launch_psiT(s));
+    STEP_LAUNCH(KK_OVERLAP, launch_overlap(f, args_, oargs_, n_ew_, s));
+  }
 #undef STEP_LAUNCH
   return "";
+}
+
+cudaError_t Engine::launch_psiT(cudaStream_t s) {
+  const SectorDev& sp = sectors_[vecs_[oargs_.psi_index].sector];
+  return launch_transpose(cfg_.fp64, vecs_[oargs_.psi_index].x1, d_psiT_.p, sp.dim_up,
+                          sp.dim_dn, s);
 }
 
 std::string Engine::capture(cudaStream_t s) {
@@ -519,7 +560,10 @@ std::string Engine::run(int n_steps, bool profile, double* kernel_ms, int64_t* l
   const bool f = cfg_.fp64;
   // observables at t_0 (also sets beta0 and the first scale)
   ED_TRY(launch_observe(f, args_, n_ew_, s));
-  if (have_overlaps_) ED_TRY(launch_overlap(f, args_, oargs_, n_ew_, s));
+  if (have_overlaps_) {
+    if (need_psiT_) ED_TRY(launch_psiT(s));
+    ED_TRY(launch_overlap(f, args_, oargs_, n_ew_, s));
+  }
   if (cfg_.energy) ED_TRY(launch_apply(f, args_, n_apply_, shape_, -1, s));
   if (!profile) {
     std::string err = capture(s);
@@ -527,7 +571,7 @@ std::string Engine::run(int n_steps, bool profile, double* kernel_ms, int64_t* l
     for (int n = 0; n < n_steps; ++n) ED_TRY(cudaGraphLaunch(exec_, s));
     return "";
   }
-  const int per_step = 2 * (2 * cfg_.m + 3);
+  const int per_step = 2 * (2 * cfg_.m + 6);   // event pairs per step, every launch kind
   std::vector<cudaEvent_t> ev((size_t)per_step * std::max(1, n_steps));
   std::vector<int> kind(ev.size(), -1);
   for (auto& e : ev) ED_TRY(cudaEventCreate(&e));

@@ -12,7 +12,8 @@
 //
 // The Lanczos recursion (Algorithm 6) is split into two passes per step j:
 //   apply :  w = s_j H x_j - beta_{j-1} s_{j-1} x_{j-1},  alpha_j = Re<v_j, w>
-//   update:  x_{j+1} = w - alpha_j s_j x_j,  beta_j = |x_{j+1}|,
+//   update:  x_{j+1} = w - h_jj s_j x_j,  beta_j = |x_{j+1}|,  with
+//            h_jj = <v_j, w> complex (alpha_j = Re h_jj enters T_m),
 //            s_{j+1} = 1 / beta_j   (normalisation is applied lazily)
 // Reductions are deterministic: per-block partial sums in float64, then the
 // last block of each vector sums the partials in block order.
@@ -186,11 +187,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait for the phase of the given parity; false on timeout or when
 // another thread of the block has already timed out (err set).
+// The flag is tested before every poll: once a wait of the block has given
+// up, a later slot's barrier may still be in the phase of a copy that was
+// never issued, and a poll for the other parity would report that phase as
+// complete (the parity names the previous phase).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err,
                                           uint32_t limit) {
   for (uint32_t it = 0; it < limit; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
     if (*err) return false;
+    if (mbar_try_wait(bar, parity)) return true;
   }
   *err = 1;
   return false;
@@ -375,7 +380,10 @@ struct TileIO {
 // rows u the padded entry list of u (uniform over the block) is walked four
 // entries at a time, each a coalesced load of the thread's column pairs of
 // the source row per column-pair group k < KA, all loads of a batch in
-// flight before they are used.  KA counts the groups of this chunk that hold
+// flight before they are used (padding entries load row u itself and carry
+// a zero coefficient: skipping their loads measured slower, the extra
+// instructions cost more than the L2 bytes they save).  KA counts the groups
+// of this chunk that hold
 // valid pairs; in the last of them the pair index is clamped to the last
 // pair of the row (those sums are never stored).
 //  * complex64: no group sums.  Each entry reads its signed coefficient
@@ -549,7 +557,8 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
 //  * Epilogue: the diagonal U * popcount(up & dn) (+ on-site energies) times
 //    the staged x joins the sums, w = s_j acc - beta_{j-1} s_{j-1} x_{j-1} is
 //    stored in pairs, and the partial of Re<x_j, w> is accumulated.
-template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS, int NT>
+template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS, int NT,
+          bool FUSED = false>
 __global__ void __launch_bounds__(TMAS ? NT + 32 : NT, MINB)
 k_apply(BatchArgs a, int j) {
   constexpr bool TMA = TMAS > 0;       // TMAS: ring stages of the TMA configurations
@@ -560,7 +569,7 @@ k_apply(BatchArgs a, int j) {
   constexpr uint32_t kSlotBytes = (uint32_t)(T * PP * 2 * sizeof(C));   // one chunk of a row
   static_assert(!(TMA && SPLIT), "the TMA ring serves the one-kernel T_up");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32 * 2];
+  __shared__ double red[32 * 4];
   __shared__ int flag;
   __shared__ int tma_err;
 
@@ -623,9 +632,24 @@ k_apply(BatchArgs a, int j) {
     }
   }
 
-  const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
+  // Fused Lanczos pass (float32 one-kernel configurations, BatchArgs::fused):
+  // pass j gathers from y_j = w_{j-1}, the unsubtracted output of pass j - 1
+  // (y_1 = x_1), and forms the Krylov vector x_j = y_j - h_{j-1} s_{j-1} x_{j-1}
+  // elementwise; H x_j = H y_j - h_{j-1} (y_j + beta_{j-2} s_{j-2} x_{j-2})
+  // because s_{j-1} H x_{j-1} = w_{j-1} + beta_{j-2} s_{j-2} x_{j-2}.  It
+  // stores x_j (Krylov slot) and w_j (the next y), and beta_j comes from
+  // |w_j - h_j s_j x_j|^2 = |w_j|^2 - |h_j|^2 (2 - s_j^2 |x_j|^2), reduced in
+  // the same pass: no separate update pass.  y alternates between w and w2.
+  static_assert(!FUSED || (sizeof(R) == 4 && !SPLIT && !TMAS),
+                "fused passes: float32 one-kernel configurations");
+  const bool fused = FUSED && j >= 1;
+  const C* x = static_cast<const C*>(
+      j < 1 ? vd.x1 : (fused && j >= 2) ? ((j & 1) ? vd.w2 : vd.w) : xptr(vd, j, sizeof(C)));
   const C* xp = (j >= 2) ? static_cast<const C*>(xptr(vd, j - 1, sizeof(C))) : nullptr;
-  C* w = static_cast<C*>(vd.w);
+  // fused: the next y, unless this is the last pass (x_j, x_{j-2} and the
+  // coefficients are taken in the epilogue, to keep them out of the registers
+  // live across the gathers)
+  C* w = static_cast<C*>(!fused ? vd.w : (j < st->m ? (((j + 1) & 1) ? vd.w2 : vd.w) : nullptr));
   const R s_in = (j >= 1) ? (R)st->inv_scale[j] : (R)1;
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
@@ -657,7 +681,7 @@ k_apply(BatchArgs a, int j) {
   }
   __syncthreads();
 
-  double dot_d = 0.0;
+  double dot_d = 0.0, dot_i = 0.0, nu_d = 0.0, ka_d = 0.0;
   uint32_t cidx = 0;     // T_up entries consumed so far (TMA ring position)
   if (TMA && tid >= T) {
     // ---- producer warp (TMA configurations): one elected lane issues the
@@ -886,6 +910,69 @@ k_apply(BatchArgs a, int j) {
         tup_chunk<R, NR, PP, 1, VEC, NT>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
     }
     // ---- epilogue: previous-vector loads first, then scale, subtract, store
+    R dot_acc = (R)0, dot_im = (R)0, nu_acc = (R)0, ka_acc = (R)0;
+    if constexpr (FUSED) {
+      // fused pass (see above): per column-pair group the loads of x_{j-1}
+      // and x_{j-2}, then x_j and w_j, both stored; coefficients h_{j-1}
+      // s_{j-1} (ap), s_j h_{j-1} (ch), beta_{j-2} s_{j-2} (bp2)
+      const bool fj = fused && j >= 2;
+      const C* xp2 = (fused && j >= 3) ? static_cast<const C*>(xptr(vd, j - 2, sizeof(C))) : nullptr;
+      C* xout = fj ? static_cast<C*>(const_cast<void*>(xptr(vd, j, sizeof(C)))) : nullptr;
+      const C ap = fj ? C{st->fco[0], st->fco[1]} : czero<C>();
+      const C ch = fj ? C{st->fco[2], st->fco[3]} : czero<C>();
+      const R bp2 = fj ? (R)st->fco[4] : (R)0;
+#pragma unroll
+      for (int k = 0; k < PP; ++k) {
+        const int p = pc + tid + k * T;
+        if (p >= npairs) continue;
+        const int d0 = 2 * p;
+        const bool has1 = d0 + 1 < dim_dn;
+        const uint32_t dw0 = __ldg(sd.dn_word + d0);
+        const uint32_t dw1 = has1 ? __ldg(sd.dn_word + d0 + 1) : 0u;
+        const R de0 = sd.dn_eps ? (R)__ldg(sd.dn_eps + d0) : (R)0;
+        const R de1 = (sd.dn_eps && has1) ? (R)__ldg(sd.dn_eps + d0 + 1) : (R)0;
+        // x_{j-1} and x_{j-2} of this pair group, every row's loads in flight
+        // before the arithmetic
+        C mm[NR][2], qq[NR][2];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          mm[r][0] = mm[r][1] = qq[r][0] = qq[r][1] = czero<C>();
+          if (r < nrows) {
+            if (xp) load_pair<C, VEC, true>(xp + (size_t)urow[r] * dim_dn, p, dim_dn, mm[r][0], mm[r][1]);
+            if (xp2) load_pair<C, VEC, true>(xp2 + (size_t)urow[r] * dim_dn, p, dim_dn, qq[r][0], qq[r][1]);
+          }
+        }
+        C ya[NR], yb[NR];
+        TIO::load(tile, d0, ya);          // y_j
+        TIO::load(tile, d0 + 1, yb);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r >= nrows) continue;
+          const C m0 = mm[r][0], m1 = mm[r][1], q0 = qq[r][0], q1 = qq[r][1];
+          const R g0 = U * (R)__popc(uw[r] & dw0) + eu[r] + de0;
+          const R g1 = U * (R)__popc(uw[r] & dw1) + eu[r] + de1;
+          C x0 = ya[r], x1 = yb[r];                  // x_j = y_j - ap x_{j-1}
+          x0.x -= ap.x * m0.x - ap.y * m0.y;
+          x0.y -= ap.x * m0.y + ap.y * m0.x;
+          x1.x -= ap.x * m1.x - ap.y * m1.y;
+          x1.y -= ap.x * m1.y + ap.y * m1.x;
+          // hp = y_j + bp2 x_{j-2};  w = s_j (H y_j) - ch hp - s_prev x_{j-1}
+          const C h0 = {ya[r].x + bp2 * q0.x, ya[r].y + bp2 * q0.y};
+          const C h1 = {yb[r].x + bp2 * q1.x, yb[r].y + bp2 * q1.y};
+          C o0, o1;
+          o0.x = s_in * (acc[r][2 * k].x + g0 * ya[r].x) - (ch.x * h0.x - ch.y * h0.y) - s_prev * m0.x;
+          o0.y = s_in * (acc[r][2 * k].y + g0 * ya[r].y) - (ch.x * h0.y + ch.y * h0.x) - s_prev * m0.y;
+          o1.x = s_in * (acc[r][2 * k + 1].x + g1 * yb[r].x) - (ch.x * h1.x - ch.y * h1.y) - s_prev * m1.x;
+          o1.y = s_in * (acc[r][2 * k + 1].y + g1 * yb[r].y) - (ch.x * h1.y + ch.y * h1.x) - s_prev * m1.y;
+          if (xout) store_pair<C, VEC, true>(xout + (size_t)urow[r] * dim_dn, p, dim_dn, x0, x1);
+          if (w) store_pair<C, VEC, true>(w + (size_t)urow[r] * dim_dn, p, dim_dn, o0, o1);
+          dot_acc += x0.x * o0.x + x0.y * o0.y + x1.x * o1.x + x1.y * o1.y;
+          dot_im += x0.x * o0.y - x0.y * o0.x + x1.x * o1.y - x1.y * o1.x;
+          nu_acc += o0.x * o0.x + o0.y * o0.y + o1.x * o1.x + o1.y * o1.y;
+          ka_acc += x0.x * x0.x + x0.y * x0.y + x1.x * x1.x + x1.y * x1.y;
+        }
+      }
+    } else {
     C pv[NR][2 * PP];
 #pragma unroll
     for (int r = 0; r < NR; ++r)
@@ -897,7 +984,6 @@ k_apply(BatchArgs a, int j) {
                                   pv[r][2 * k + 1]);
         else { pv[r][2 * k] = czero<C>(); pv[r][2 * k + 1] = czero<C>(); }
       }
-    R dot_acc = (R)0;
 #pragma unroll
     for (int k = 0; k < PP; ++k) {
       const int p = pc + tid + k * T;
@@ -929,23 +1015,66 @@ k_apply(BatchArgs a, int j) {
             o1.y = s_in * a1.y - s_prev * pv[r][2 * k + 1].y;
             store_pair<C, VEC, true>(w + (size_t)urow[r] * dim_dn, p, dim_dn, o0, o1);
             dot_acc += xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
+            // Im h_jj: float32 only (in float64 it is rounding, and the
+            // float64 apply is bound by its FP64 operations)
+            if constexpr (sizeof(R) == 4)
+              dot_im += xa[r].x * o0.y - xa[r].y * o0.x + xb[r].x * o1.y - xb[r].y * o1.x;
           }
         }
       }
     }
+    }
     dot_d += (double)dot_acc;
+    dot_i += (double)dot_im;
+    nu_d += (double)nu_acc;
+    ka_d += (double)ka_acc;
   }
   if constexpr (TMA) {
     if (tma_err && tid == 0) st->status = kStatusTimeout;
   }
   if (j == 0) return;
-  double v[1] = {dot_d};
-  if (reduce_last_block<1>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
-                           a.partials, a.counters + ab.vec, red, &flag)) {
+  constexpr int KR = FUSED ? 4 : 2;   // <x_j, w> (re, im), and fused: |w|^2, |x_j|^2
+  double v[KR];
+  v[0] = dot_d;
+  v[1] = dot_i;
+  if constexpr (FUSED) {
+    v[2] = nu_d;
+    v[3] = ka_d;
+  }
+  if (reduce_last_block<KR>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
+                            a.partials, a.counters + ab.vec, red, &flag)) {
     if (tid == 0) {
       if (j >= 1) {
-        st->alpha[j] = v[0] * st->inv_scale[j];
-        if (!isfinite(v[0])) { st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1; }
+        // h_jj = <v_j, w> of Algorithm 6: the real part is alpha_j (H is
+        // Hermitian); the update subtracts the whole complex h_jj v_j
+        const double sj = st->inv_scale[j];
+        st->alpha[j] = v[0] * sj;
+        st->alpha_im[j] = v[1] * sj;
+        if (!isfinite(v[0]) || !isfinite(v[1])) {
+          st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1;
+        } else if (FUSED && j < st->m) {
+          // beta_j of the update this pass replaces (see k_update)
+          const double h2 = st->alpha[j] * st->alpha[j] + st->alpha_im[j] * st->alpha_im[j];
+          const double b2 = v[KR - 2] - h2 * (2.0 - sj * sj * v[KR - 1]);
+          const double beta = sqrt(fmax(b2, 0.0));
+          const double sc = fmax(st->scale, fabs(st->alpha[j]));
+          st->beta[j] = beta;
+          st->sc_at[j] = sc;
+          if (!isfinite(beta)) {
+            st->status = 7; st->stopped = 1; st->m_eff = j;
+          } else if (beta <= a.break_tol * sc) {
+            st->stopped = 1; st->m_eff = j;
+          } else {
+            st->inv_scale[j + 1] = 1.0 / beta;
+            st->scale = fmax(sc, beta);
+            // the next pass's coefficients: h_j s_j, s_{j+1} h_j, beta_{j-1} s_{j-1}
+            st->fco[0] = (float)(st->alpha[j] * sj);
+            st->fco[1] = (float)(st->alpha_im[j] * sj);
+            st->fco[2] = (float)(st->alpha[j] * st->inv_scale[j + 1]);
+            st->fco[3] = (float)(st->alpha_im[j] * st->inv_scale[j + 1]);
+            st->fco[4] = j >= 2 ? (float)(st->beta[j - 1] * st->inv_scale[j - 1]) : 0.f;
+          }
+        }
       } else {
         if (vd.out_energy) vd.out_energy[st->step] = v[0] / a.Ns;
       }
@@ -1215,7 +1344,8 @@ k_apply_up(BatchArgs a, int j) {
 }
 
 // ------------------------------------------------------------------ update
-// x_{j+1} = w - alpha_j s_j x_j ;  beta_j = |x_{j+1}| ;  breakdown test.
+// x_{j+1} = w - h_jj s_j x_j (h_jj = alpha_j + i alpha_im_j) ;  beta_j =
+// |x_{j+1}| ;  breakdown test.
 // PAIR: complex64 vectors of even length are processed two elements per
 // 16-byte access (chunk boundaries are multiples of 256 elements).
 template <typename R, bool PAIR>
@@ -1227,7 +1357,13 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
   const VecDev vd = a.vec[eb.vec];
   LanczosState* st = a.st + eb.vec;
   if (lanczos_done(st, j)) return;
+  // h_jj s_j with h_jj = <v_j, w> complex (Algorithm 6 subtracts h_jj v_j):
+  // its imaginary part is of the order of the rounding of H v_j, but for a
+  // state near an eigenvector (beta_j small) dropping it leaves a component
+  // i Im(h_jj) v_j in x_{j+1} that, scaled by 1/beta_j, makes the propagated
+  // norm drift by ~tau Im(h_jj) per step in float32
   const R as = (R)(st->alpha[j] * st->inv_scale[j]);
+  const R ai = (R)(st->alpha_im[j] * st->inv_scale[j]);
   double nrm_d = 0.0;
   const void* pw = vd.w;
   const void* px = xptr(vd, j, sizeof(C));
@@ -1238,7 +1374,7 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
     const float4* x = static_cast<const float4*>(px);
     float4* xn = static_cast<float4*>(const_cast<void*>(pxn));
     const int64_t b2 = eb.begin >> 1, e2 = eb.end >> 1;
-    const float af = (float)as;
+    const float af = (float)as, ag = (float)ai;
     const int bd = blockDim.x;
     // four pairs per thread and iteration: eight 16-byte loads in flight.
     // w and x_j are not read again before the combine at the end of the
@@ -1257,10 +1393,11 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
       for (int q = 0; q < 4; ++q) {
         const int64_t i = i0 + (int64_t)q * bd;
         float4 o;
-        o.x = wv[q].x - af * xv[q].x;
-        o.y = wv[q].y - af * xv[q].y;
-        o.z = wv[q].z - af * xv[q].z;
-        o.w = wv[q].w - af * xv[q].w;
+        // w - (af + i ag) x for the two elements (x, y) and (z, w)
+        o.x = wv[q].x - af * xv[q].x + ag * xv[q].y;
+        o.y = wv[q].y - af * xv[q].y - ag * xv[q].x;
+        o.z = wv[q].z - af * xv[q].z + ag * xv[q].w;
+        o.w = wv[q].w - af * xv[q].w - ag * xv[q].z;
         if (i < e2) xn[i] = o;
         nrm += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
       }
@@ -1276,8 +1413,8 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
     for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
       const C wv = __ldcs(w + i), xv = __ldcs(x + i);
       C o;
-      o.x = wv.x - as * xv.x;
-      o.y = wv.y - as * xv.y;
+      o.x = wv.x - as * xv.x + ai * xv.y;
+      o.y = wv.y - as * xv.y - ai * xv.x;
       xn[i] = o;
       nrm += o.x * o.x + o.y * o.y;
       if (++cnt == 8) { nrm_d += (double)nrm; nrm = (R)0; cnt = 0; }
@@ -1524,6 +1661,31 @@ __device__ __forceinline__ C combine_one(const C* cf, C cf_lo, int n, const C* V
   return p;
 }
 
+// Eight 16-byte streaming loads (evict-first) issued together: four pairs
+// each of two Krylov vectors (element offsets o[q] from bases a and b).
+__device__ __forceinline__ void ld8_stream(const float4* a, const float4* b,
+                                           const int64_t (&o)[4], float4 (&va)[4],
+                                           float4 (&vb)[4]) {
+  asm volatile(
+      "ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%32];\n\t"
+      "ld.global.cs.v4.f32 {%4, %5, %6, %7}, [%33];\n\t"
+      "ld.global.cs.v4.f32 {%8, %9, %10, %11}, [%34];\n\t"
+      "ld.global.cs.v4.f32 {%12, %13, %14, %15}, [%35];\n\t"
+      "ld.global.cs.v4.f32 {%16, %17, %18, %19}, [%36];\n\t"
+      "ld.global.cs.v4.f32 {%20, %21, %22, %23}, [%37];\n\t"
+      "ld.global.cs.v4.f32 {%24, %25, %26, %27}, [%38];\n\t"
+      "ld.global.cs.v4.f32 {%28, %29, %30, %31}, [%39];"
+      : "=f"(va[0].x), "=f"(va[0].y), "=f"(va[0].z), "=f"(va[0].w), "=f"(va[1].x),
+        "=f"(va[1].y), "=f"(va[1].z), "=f"(va[1].w), "=f"(va[2].x), "=f"(va[2].y),
+        "=f"(va[2].z), "=f"(va[2].w), "=f"(va[3].x), "=f"(va[3].y), "=f"(va[3].z),
+        "=f"(va[3].w), "=f"(vb[0].x), "=f"(vb[0].y), "=f"(vb[0].z), "=f"(vb[0].w),
+        "=f"(vb[1].x), "=f"(vb[1].y), "=f"(vb[1].z), "=f"(vb[1].w), "=f"(vb[2].x),
+        "=f"(vb[2].y), "=f"(vb[2].z), "=f"(vb[2].w), "=f"(vb[3].x), "=f"(vb[3].y),
+        "=f"(vb[3].z), "=f"(vb[3].w)
+      : "l"(a + o[0]), "l"(a + o[1]), "l"(a + o[2]), "l"(a + o[3]), "l"(b + o[0]),
+        "l"(b + o[1]), "l"(b + o[2]), "l"(b + o[3]));
+}
+
 template <typename R, bool COMBINE>
 __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
   using C = typename C2T<R>::T;
@@ -1587,8 +1749,42 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
           p[q].z = lo.x * xv[q].z - lo.y * xv[q].w;
           p[q].w = lo.x * xv[q].w + lo.y * xv[q].z;
         }
-#pragma unroll 2
-        for (int jj = 1; jj < n; ++jj) {
+        // JV Krylov vectors per round, all JV x Q loads issued before their
+        // products, by volatile loads at in-range indices (out-of-range
+        // lanes read element e2 - 1 and drop it).  Left to the compiler, the
+        // loads of one vector waited for the previous vector's products,
+        // about one vector's loads were in flight per thread, and the kernel
+        // ran 2.3x slower.  Accumulation order j = 1, 2, ... as in combine_one.
+        constexpr int JV = 4;
+        int64_t ldi[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) ldi[q] = ok[q] ? idx[q] : e2 - 1;
+        int jj = 1;
+        for (; jj + JV <= n; jj += JV) {
+          float4 v[JV][Q];
+#pragma unroll
+          for (int u = 0; u < JV; u += 2) {
+            const float4* Vj = V4 + (size_t)(jj + u - 1) * D2;
+            ld8_stream(Vj, Vj + D2, ldi, v[u], v[u + 1]);
+          }
+#pragma unroll
+          for (int u = 0; u < JV; ++u)
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+              if (!ok[q]) v[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < JV; ++u) {
+            const float2 c = *reinterpret_cast<const float2*>(&cf[jj + u]);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+              p[q].x += c.x * v[u][q].x - c.y * v[u][q].y;
+              p[q].y += c.x * v[u][q].y + c.y * v[u][q].x;
+              p[q].z += c.x * v[u][q].z - c.y * v[u][q].w;
+              p[q].w += c.x * v[u][q].w + c.y * v[u][q].z;
+            }
+          }
+        }
+        for (; jj < n; ++jj) {
           const float4* Vj = V4 + (size_t)(jj - 1) * D2;
           const float2 c = *reinterpret_cast<const float2*>(&cf[jj]);
           float4 v[Q];
@@ -1619,9 +1815,10 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         if (!ok[q]) continue;
-        const int64_t e = 2 * idx[q];
-        const int u = (int)(e / dim_dn);
-        const int d = (int)(e - (int64_t)u * dim_dn);
+        // sector indices fit 32 bits (D <= C(16,8)^2 < 2^28): 32-bit division
+        const uint32_t e = 2u * (uint32_t)idx[q];
+        const int u = (int)(e / (uint32_t)dim_dn);
+        const int d = (int)(e - (uint32_t)u * (uint32_t)dim_dn);
         const uint32_t uwd = __ldg(sd.up_word + u);
         const R q0 = p[q].x * p[q].x + p[q].y * p[q].y, q1 = p[q].z * p[q].z + p[q].w * p[q].w;
         nl += q0 + q1;
@@ -1639,8 +1836,8 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
         p = combine_one<R, C>(cf, cf_lo, n, V, vd.D, i, p);
         x1[i] = p;
       }
-      const int u = (int)(i / dim_dn);
-      const int d = (int)(i - (int64_t)u * dim_dn);
+      const int u = (int)((uint32_t)i / (uint32_t)dim_dn);
+      const int d = (int)((uint32_t)i - (uint32_t)u * (uint32_t)dim_dn);
       const R q = p.x * p.x + p.y * p.y;
       nl += q;
       wl += (R)__popc(__ldg(sd.up_word + u) & __ldg(sd.dn_word + d)) * q;
@@ -1669,6 +1866,27 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
 }
 
 // -------------------------------------------------------- fermion operator
+// Element (u, d) of the target sector dim_up_dst x dim_dn_dst, at storage
+// index t: row-major (t = u dim_dn + d) for spin 0 and 1, column-major
+// (t = d dim_up + u, the vector stored transposed) for spin mode 2.
+// (Sector indices fit 32 bits, D <= C(16,8)^2 < 2^28: 32-bit division, which
+// costs a fraction of a 64-bit one.)
+__device__ __forceinline__ void target_ud(int64_t t, int dim_up, int dim_dn, int spin, int& u,
+                                          int& d) {
+  const uint32_t t32 = (uint32_t)t;
+  if (spin == 2) {
+    d = (int)(t32 / (uint32_t)dim_up);
+    u = (int)(t32 - (uint32_t)d * (uint32_t)dim_up);
+  } else {
+    u = (int)(t32 / (uint32_t)dim_dn);
+    d = (int)(t32 - (uint32_t)u * (uint32_t)dim_dn);
+  }
+}
+
+// out = op psi through the map of the operator's spin: spin 0 a row map
+// (up spin), 1 a column map (down spin), 2 a column map with out stored
+// transposed (dim_dn_dst x dim_up_dst: as a vector of the sector with the two
+// spins' particle numbers swapped, whose Hamiltonian is the same).
 template <typename R>
 __global__ void k_fermion_op(const typename C2T<R>::T* in,
                              typename C2T<R>::T* out, int dim_dn_src,
@@ -1678,8 +1896,8 @@ __global__ void k_fermion_op(const typename C2T<R>::T* in,
   const int64_t n = (int64_t)dim_up_dst * dim_dn_dst;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int u = (int)(t / dim_dn_dst);
-    const int d = (int)(t - (int64_t)u * dim_dn_dst);
+    int u, d;
+    target_ud(t, dim_up_dst, dim_dn_dst, spin, u, d);
     const int32_t m = __ldg(map + (spin == 0 ? u : d));
     C o = czero<C>();
     if (m != 0x7FFFFFFF) {
@@ -1710,16 +1928,25 @@ __global__ void __launch_bounds__(256) k_overlap(BatchArgs a, OverlapArgs o) {
   const int32_t* map = o.maps + moff;
   const C* phi = static_cast<const C*>(vd.x1);
   const C* psi = static_cast<const C*>(vp.x1);
-  const int dim_dn = sd.dim_dn, dim_dn_src = sp.dim_dn;
+  // spin mode 2: phi is stored transposed (a vector of the sector with the
+  // spins' particle numbers swapped), so its storage shape is sd's and the
+  // target sector of the map is sd with rows and columns exchanged
+  const int dim_up_t = spin == 2 ? sd.dim_dn : sd.dim_up;
+  const int dim_dn_t = spin == 2 ? sd.dim_up : sd.dim_dn;
+  const int dim_dn_src = sp.dim_dn, dim_up_src = sp.dim_up;
+  // mode 2 reads psi transposed: row src of psi^T is column src of psi, so
+  // consecutive t (consecutive u) read consecutive elements
+  const C* psiT = static_cast<const C*>(o.psiT);
   double ar = 0.0, ai = 0.0;
   for (int64_t t = eb.begin + threadIdx.x; t < eb.end; t += blockDim.x) {
-    const int u = (int)(t / dim_dn);
-    const int d = (int)(t - (int64_t)u * dim_dn);
+    int u, d;
+    target_ud(t, dim_up_t, dim_dn_t, spin, u, d);
     const int32_t m = __ldg(map + (spin == 0 ? u : d));
     if (m == 0x7FFFFFFF) continue;
     const int src = m & 0x7FFFFFFF;
-    const C p = spin == 0 ? psi[(int64_t)src * dim_dn_src + d]
-                          : psi[(int64_t)u * dim_dn_src + src];
+    const C p = spin == 0   ? psi[(int64_t)src * dim_dn_src + d]
+                : spin == 2 ? psiT[(int64_t)src * dim_up_src + u]
+                            : psi[(int64_t)u * dim_dn_src + src];
     const C f = phi[t];
     // conj(s p) f, s = +-1
     double re = (double)p.x * f.x + (double)p.y * f.y;
@@ -1737,6 +1964,27 @@ __global__ void __launch_bounds__(256) k_overlap(BatchArgs a, OverlapArgs o) {
       out[0] = v[0];
       out[1] = v[1];
     }
+  }
+}
+
+// Tiled transpose of a rows x cols complex matrix through shared memory
+// (32 x 32 tiles, one padding column against bank conflicts): reads and
+// writes are both row-contiguous.
+template <typename C>
+__global__ void __launch_bounds__(256) k_transpose(const C* in, C* out, int rows, int cols) {
+  __shared__ C tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+#pragma unroll
+  for (int k = 0; k < 32; k += 8) {
+    const int r = r0 + ty + k, c = c0 + tx;
+    if (r < rows && c < cols) tile[ty + k][tx] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 32; k += 8) {
+    const int c = c0 + ty + k, r = r0 + tx;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = tile[tx][ty + k];
   }
 }
 
@@ -1878,8 +2126,8 @@ k_docc_sites(const typename C2T<R>::T* psi, SectorDev sd, int Ns, double* partia
 #pragma unroll
   for (int i = 0; i <= kMaxSites; ++i) v[i] = 0.0;
   for (int64_t t = i0 + threadIdx.x; t < i1; t += blockDim.x) {
-    const int u = (int)(t / sd.dim_dn);
-    const int d = (int)(t - (int64_t)u * sd.dim_dn);
+    const int u = (int)((uint32_t)t / (uint32_t)sd.dim_dn);
+    const int d = (int)((uint32_t)t - (uint32_t)u * (uint32_t)sd.dim_dn);
     const auto p = psi[t];
     const double q = (double)p.x * p.x + (double)p.y * p.y;
     const uint32_t both = sd.up_word[u] & sd.dn_word[d];
@@ -2045,6 +2293,13 @@ static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShap
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if constexpr (sizeof(R) == 4 && !SPLIT && !TMA) {
+    if (a.fused && j >= 1) {   // fused Lanczos passes
+      if (sh.vec) k_apply<R, NR, PP, V, MINB, false, 0, NT, true><<<nblk, threads, sh.smem, s>>>(a, j);
+      else k_apply<R, NR, PP, false, MINB, false, 0, NT, true><<<nblk, threads, sh.smem, s>>>(a, j);
+      return cudaGetLastError();
+    }
+  }
   if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
   else k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
@@ -2061,6 +2316,14 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
+  if constexpr (sizeof(R) == 4 && !SPLIT && !TMA) {
+    e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, false, 0, NT, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, false, 0, NT, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+  }
   if constexpr (SPLIT && CB == 0) {
     const int smc = (int)sh.smem_c;
     e = cudaFuncSetAttribute(k_apply_tup<R, PPC, false, MINBC>,
@@ -2177,6 +2440,18 @@ cudaError_t launch_overlap(bool fp64, const BatchArgs& a, const OverlapArgs& o, 
                            cudaStream_t s) {
   if (fp64) k_overlap<double><<<nblk, 256, 0, s>>>(a, o);
   else k_overlap<float><<<nblk, 256, 0, s>>>(a, o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(bool fp64, const void* in, void* out, int rows, int cols,
+                             cudaStream_t s) {
+  const dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  if (fp64)
+    k_transpose<double2><<<grid, 256, 0, s>>>(static_cast<const double2*>(in),
+                                              static_cast<double2*>(out), rows, cols);
+  else
+    k_transpose<float2><<<grid, 256, 0, s>>>(static_cast<const float2*>(in),
+                                             static_cast<float2*>(out), rows, cols);
   return cudaGetLastError();
 }
 

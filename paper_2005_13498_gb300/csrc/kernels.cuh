@@ -104,7 +104,9 @@ cudaError_t launch_observe(bool fp64, const BatchArgs& a, int n_ew_blocks,
                            cudaStream_t s);
 
 // Fermion operator: out[t] = sign * in[src(t)] through a row map (spin 0) or a
-// column map (spin 1).  map entries: src | (neg << 31); 0x7FFFFFFF = no source.
+// column map (spin 1); spin 2: a column map with out stored transposed
+// (dim_dn_dst x dim_up_dst).  map entries: src | (neg << 31); 0x7FFFFFFF = no
+// source.
 cudaError_t launch_fermion_op(bool fp64, const void* in, void* out,
                               int dim_up_src, int dim_dn_src,
                               int dim_up_dst, int dim_dn_dst, int spin,
@@ -114,13 +116,18 @@ cudaError_t launch_fermion_op(bool fp64, const void* in, void* out,
 // map_off[b] >= 0, psi = vec[psi_index].x1; result added to out[(step)*nb*2..]
 struct OverlapArgs {
   const int32_t* maps;      // concatenated maps
+  const void* psiT;         // psi transposed (dim_dn x dim_up), for map mode 2
   const int64_t* map_off;   // [nvec] offset into maps, -1 = no overlap
-  const int32_t* map_spin;  // [nvec] 0 row map, 1 column map
+  const int32_t* map_spin;  // [nvec] 0 row map, 1 column map, 2 column map with the
+                            // vector stored transposed (see k_fermion_op)
   int psi_index;            // vector holding psi(t_n)
   double* out;              // [n_steps+1][nvec][2] (re, im)
 };
 cudaError_t launch_overlap(bool fp64, const BatchArgs& a, const OverlapArgs& o,
                            int n_ew_blocks, cudaStream_t s);
+// out[c * rows + r] = in[r * cols + c] for a rows x cols complex matrix.
+cudaError_t launch_transpose(bool fp64, const void* in, void* out, int rows, int cols,
+                             cudaStream_t s);
 
 // ---- ground-state helpers (float64 only) ---------------------------------
 // partial[blk][i] = sum over block chunk of conj(V_i) w, i < k  (k <= 256)
