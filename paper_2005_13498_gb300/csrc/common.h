@@ -66,10 +66,6 @@ struct SectorDev {
 struct LanczosState {
   double alpha[kMaxKrylov + 2];
   double alpha_im[kMaxKrylov + 2];  // Im <v_j, w>: subtracted with alpha, not in T_m
-  // fused passes: the float32 coefficients of the next pass, written by the
-  // last block of the previous one: h_{j-1} s_{j-1} (re, im), s_j h_{j-1}
-  // (re, im), beta_{j-2} s_{j-2}
-  float fco[6];
   double beta[kMaxKrylov + 2];
   double inv_scale[kMaxKrylov + 2];
   double comb_re[kMaxKrylov + 2];   // combine coefficients: psi = sum comb_j x_j
@@ -104,7 +100,6 @@ struct VecDev {
   void* x1;            // the state psi (x_1)
   void* V;             // (m-1) * D slots for x_2 .. x_m
   void* w;             // scratch vector of D elements
-  void* w2;            // second scratch vector (fused Lanczos passes), or null
   int apply_begin, apply_end;   // range of apply blocks of this vector
   int ew_begin, ew_end;         // range of elementwise blocks
   double* out_docc;    // device [n_steps+1] or null
@@ -161,9 +156,6 @@ struct BatchArgs {
   // consumers' wait for that copy run out
   uint32_t wait_limit;
   int tma_withhold;
-  // 1: fused Lanczos passes (k_apply, float32 one-kernel configurations):
-  // pass j also forms x_j and beta_j, and no update pass runs
-  int fused;
 };
 
 // Default poll limit of the bounded mbarrier waits.

@@ -41,8 +41,7 @@ size_t Engine::device_bytes() const {
   return d_sec_.bytes + d_vec_.bytes + d_st_.bytes + d_amap_.bytes + d_cmap_.bytes +
          d_emap_.bytes +
          d_partials_.bytes + d_counters_.bytes + d_coefs_.bytes + d_coefs_obs_.bytes +
-         d_V_.bytes + d_w_.bytes + d_w2_.bytes + d_out_.bytes + d_owned_x1_.bytes +
-         d_maps_.bytes +
+         d_V_.bytes + d_w_.bytes + d_out_.bytes + d_owned_x1_.bytes + d_maps_.bytes +
          d_map_off_.bytes + d_map_spin_.bytes + d_ovl_.bytes + d_psiT_.bytes;
 }
 
@@ -236,10 +235,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     if (v.owned_x1) owned += v.D;
     totD += v.D;
   }
-  // (float32 engines count a second scratch vector, which the fused Lanczos
-  // passes of one-kernel apply configurations need)
-  const int64_t need =
-      (owned + (int64_t)std::max(0, m - 1) * totD + (cfg.fp64 ? 1 : 2) * totD) * (int64_t)esz;
+  const int64_t need = (owned + (int64_t)std::max(0, m - 1) * totD + totD) * (int64_t)esz;
   workspace_bytes_ = need;
   if (cfg.workspace_limit > 0 && need > cfg.workspace_limit)
     return "device memory for the Krylov workspace (" + std::to_string(need) +
@@ -362,20 +358,6 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   std::string err = tune_apply(tt, stream, &shape_, &amap, &cmap);
   if (!err.empty()) return err;
   ED_TRY(prepare_apply(cfg.fp64, shape_));
-  // fused Lanczos passes (float32, one-kernel configurations): pass j forms
-  // x_j and beta_j itself, and the y_j it gathers alternate between w and w2
-  fused_ = !cfg.fp64 && !shape_.split && !shape_.tma;
-  if (fused_) {
-    ED_TRY(d_w2_.alloc((size_t)totD * esz));
-    int64_t off = 0;
-    for (int i = 0; i < nv; ++i) {
-      vd[i].w2 = static_cast<char*>(d_w2_.p) + (size_t)off * esz;
-      off += vd[i].D;
-    }
-  } else {
-    d_w2_.release();
-  }
-  args_.fused = fused_ ? 1 : 0;
   n_apply_ = (int)amap.size();
   for (int i = 0; i < nv; ++i) {
     vd[i].apply_begin = -1;
@@ -511,8 +493,7 @@ std::string Engine::launch_step(cudaStream_t s, bool profile, cudaEvent_t* ev, i
     if (adaptive && j >= 3) ED_TRY(cudaStreamWaitEvent(s, ev_check_[j - 2], 0));
     STEP_LAUNCH(KK_APPLY, launch_apply(f, args_, n_apply_, shape_, j, s));
     if (j < cfg_.m) {
-      // fused passes compute x_{j+1}'s norm in the apply: no update pass
-      if (!fused_) STEP_LAUNCH(KK_UPDATE, launch_update(f, args_, n_ew_, j, s));
+      STEP_LAUNCH(KK_UPDATE, launch_update(f, args_, n_ew_, j, s));
       if (adaptive) {
         ED_TRY(cudaEventRecord(ev_fork_[j], s));
         ED_TRY(cudaStreamWaitEvent(side_, ev_fork_[j], 0));

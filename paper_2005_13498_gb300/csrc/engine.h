@@ -93,7 +93,6 @@ class Engine {
                     const std::vector<const SpinTable*>& up_tabs = {});
   bool compatible(const EngineConfig& cfg, const std::vector<EngineVector>& vecs) const;
   int apply_config() const { return shape_.cfg; }
-  bool fused() const { return fused_; }
   // Upload per-step coefficients ([n_steps][n_groups] complex double; energy
   // coefficients [n_steps+1][n_groups] or empty) and reset the Lanczos state.
   std::string begin(const std::vector<double>& coefs, const std::vector<double>& coefs_obs,
@@ -136,8 +135,7 @@ class Engine {
   OverlapArgs oargs_{};
   bool have_overlaps_ = false;
   DevMem d_sec_, d_vec_, d_st_, d_amap_, d_cmap_, d_emap_, d_partials_, d_counters_;
-  DevMem d_coefs_, d_coefs_obs_, d_V_, d_w_, d_w2_, d_out_, d_owned_x1_;
-  bool fused_ = false;   // fused Lanczos passes (no update kernel)
+  DevMem d_coefs_, d_coefs_obs_, d_V_, d_w_, d_out_, d_owned_x1_;
   DevMem d_maps_, d_map_off_, d_map_spin_, d_ovl_, d_psiT_;
   bool need_psiT_ = false;
   cudaGraph_t graph_ = nullptr;

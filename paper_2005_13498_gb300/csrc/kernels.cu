@@ -557,8 +557,7 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
 //  * Epilogue: the diagonal U * popcount(up & dn) (+ on-site energies) times
 //    the staged x joins the sums, w = s_j acc - beta_{j-1} s_{j-1} x_{j-1} is
 //    stored in pairs, and the partial of Re<x_j, w> is accumulated.
-template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS, int NT,
-          bool FUSED = false>
+template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS, int NT>
 __global__ void __launch_bounds__(TMAS ? NT + 32 : NT, MINB)
 k_apply(BatchArgs a, int j) {
   constexpr bool TMA = TMAS > 0;       // TMAS: ring stages of the TMA configurations
@@ -569,7 +568,7 @@ k_apply(BatchArgs a, int j) {
   constexpr uint32_t kSlotBytes = (uint32_t)(T * PP * 2 * sizeof(C));   // one chunk of a row
   static_assert(!(TMA && SPLIT), "the TMA ring serves the one-kernel T_up");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32 * 4];
+  __shared__ double red[32 * 2];
   __shared__ int flag;
   __shared__ int tma_err;
 
@@ -632,24 +631,9 @@ k_apply(BatchArgs a, int j) {
     }
   }
 
-  // Fused Lanczos pass (float32 one-kernel configurations, BatchArgs::fused):
-  // pass j gathers from y_j = w_{j-1}, the unsubtracted output of pass j - 1
-  // (y_1 = x_1), and forms the Krylov vector x_j = y_j - h_{j-1} s_{j-1} x_{j-1}
-  // elementwise; H x_j = H y_j - h_{j-1} (y_j + beta_{j-2} s_{j-2} x_{j-2})
-  // because s_{j-1} H x_{j-1} = w_{j-1} + beta_{j-2} s_{j-2} x_{j-2}.  It
-  // stores x_j (Krylov slot) and w_j (the next y), and beta_j comes from
-  // |w_j - h_j s_j x_j|^2 = |w_j|^2 - |h_j|^2 (2 - s_j^2 |x_j|^2), reduced in
-  // the same pass: no separate update pass.  y alternates between w and w2.
-  static_assert(!FUSED || (sizeof(R) == 4 && !SPLIT && !TMAS),
-                "fused passes: float32 one-kernel configurations");
-  const bool fused = FUSED && j >= 1;
-  const C* x = static_cast<const C*>(
-      j < 1 ? vd.x1 : (fused && j >= 2) ? ((j & 1) ? vd.w2 : vd.w) : xptr(vd, j, sizeof(C)));
+  const C* x = static_cast<const C*>(j >= 1 ? xptr(vd, j, sizeof(C)) : vd.x1);
   const C* xp = (j >= 2) ? static_cast<const C*>(xptr(vd, j - 1, sizeof(C))) : nullptr;
-  // fused: the next y, unless this is the last pass (x_j, x_{j-2} and the
-  // coefficients are taken in the epilogue, to keep them out of the registers
-  // live across the gathers)
-  C* w = static_cast<C*>(!fused ? vd.w : (j < st->m ? (((j + 1) & 1) ? vd.w2 : vd.w) : nullptr));
+  C* w = static_cast<C*>(vd.w);
   const R s_in = (j >= 1) ? (R)st->inv_scale[j] : (R)1;
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
@@ -681,7 +665,7 @@ k_apply(BatchArgs a, int j) {
   }
   __syncthreads();
 
-  double dot_d = 0.0, dot_i = 0.0, nu_d = 0.0, ka_d = 0.0;
+  double dot_d = 0.0, dot_i = 0.0;
   uint32_t cidx = 0;     // T_up entries consumed so far (TMA ring position)
   if (TMA && tid >= T) {
     // ---- producer warp (TMA configurations): one elected lane issues the
@@ -910,69 +894,8 @@ k_apply(BatchArgs a, int j) {
         tup_chunk<R, NR, PP, 1, VEC, NT>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
     }
     // ---- epilogue: previous-vector loads first, then scale, subtract, store
-    R dot_acc = (R)0, dot_im = (R)0, nu_acc = (R)0, ka_acc = (R)0;
-    if constexpr (FUSED) {
-      // fused pass (see above): per column-pair group the loads of x_{j-1}
-      // and x_{j-2}, then x_j and w_j, both stored; coefficients h_{j-1}
-      // s_{j-1} (ap), s_j h_{j-1} (ch), beta_{j-2} s_{j-2} (bp2)
-      const bool fj = fused && j >= 2;
-      const C* xp2 = (fused && j >= 3) ? static_cast<const C*>(xptr(vd, j - 2, sizeof(C))) : nullptr;
-      C* xout = fj ? static_cast<C*>(const_cast<void*>(xptr(vd, j, sizeof(C)))) : nullptr;
-      const C ap = fj ? C{st->fco[0], st->fco[1]} : czero<C>();
-      const C ch = fj ? C{st->fco[2], st->fco[3]} : czero<C>();
-      const R bp2 = fj ? (R)st->fco[4] : (R)0;
-#pragma unroll
-      for (int k = 0; k < PP; ++k) {
-        const int p = pc + tid + k * T;
-        if (p >= npairs) continue;
-        const int d0 = 2 * p;
-        const bool has1 = d0 + 1 < dim_dn;
-        const uint32_t dw0 = __ldg(sd.dn_word + d0);
-        const uint32_t dw1 = has1 ? __ldg(sd.dn_word + d0 + 1) : 0u;
-        const R de0 = sd.dn_eps ? (R)__ldg(sd.dn_eps + d0) : (R)0;
-        const R de1 = (sd.dn_eps && has1) ? (R)__ldg(sd.dn_eps + d0 + 1) : (R)0;
-        // x_{j-1} and x_{j-2} of this pair group, every row's loads in flight
-        // before the arithmetic
-        C mm[NR][2], qq[NR][2];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          mm[r][0] = mm[r][1] = qq[r][0] = qq[r][1] = czero<C>();
-          if (r < nrows) {
-            if (xp) load_pair<C, VEC, true>(xp + (size_t)urow[r] * dim_dn, p, dim_dn, mm[r][0], mm[r][1]);
-            if (xp2) load_pair<C, VEC, true>(xp2 + (size_t)urow[r] * dim_dn, p, dim_dn, qq[r][0], qq[r][1]);
-          }
-        }
-        C ya[NR], yb[NR];
-        TIO::load(tile, d0, ya);          // y_j
-        TIO::load(tile, d0 + 1, yb);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          if (r >= nrows) continue;
-          const C m0 = mm[r][0], m1 = mm[r][1], q0 = qq[r][0], q1 = qq[r][1];
-          const R g0 = U * (R)__popc(uw[r] & dw0) + eu[r] + de0;
-          const R g1 = U * (R)__popc(uw[r] & dw1) + eu[r] + de1;
-          C x0 = ya[r], x1 = yb[r];                  // x_j = y_j - ap x_{j-1}
-          x0.x -= ap.x * m0.x - ap.y * m0.y;
-          x0.y -= ap.x * m0.y + ap.y * m0.x;
-          x1.x -= ap.x * m1.x - ap.y * m1.y;
-          x1.y -= ap.x * m1.y + ap.y * m1.x;
-          // hp = y_j + bp2 x_{j-2};  w = s_j (H y_j) - ch hp - s_prev x_{j-1}
-          const C h0 = {ya[r].x + bp2 * q0.x, ya[r].y + bp2 * q0.y};
-          const C h1 = {yb[r].x + bp2 * q1.x, yb[r].y + bp2 * q1.y};
-          C o0, o1;
-          o0.x = s_in * (acc[r][2 * k].x + g0 * ya[r].x) - (ch.x * h0.x - ch.y * h0.y) - s_prev * m0.x;
-          o0.y = s_in * (acc[r][2 * k].y + g0 * ya[r].y) - (ch.x * h0.y + ch.y * h0.x) - s_prev * m0.y;
-          o1.x = s_in * (acc[r][2 * k + 1].x + g1 * yb[r].x) - (ch.x * h1.x - ch.y * h1.y) - s_prev * m1.x;
-          o1.y = s_in * (acc[r][2 * k + 1].y + g1 * yb[r].y) - (ch.x * h1.y + ch.y * h1.x) - s_prev * m1.y;
-          if (xout) store_pair<C, VEC, true>(xout + (size_t)urow[r] * dim_dn, p, dim_dn, x0, x1);
-          if (w) store_pair<C, VEC, true>(w + (size_t)urow[r] * dim_dn, p, dim_dn, o0, o1);
-          dot_acc += x0.x * o0.x + x0.y * o0.y + x1.x * o1.x + x1.y * o1.y;
-          dot_im += x0.x * o0.y - x0.y * o0.x + x1.x * o1.y - x1.y * o1.x;
-          nu_acc += o0.x * o0.x + o0.y * o0.y + o1.x * o1.x + o1.y * o1.y;
-          ka_acc += x0.x * x0.x + x0.y * x0.y + x1.x * x1.x + x1.y * x1.y;
-        }
-      }
-    } else {
+    R dot_acc = (R)0, dot_im = (R)0;
+    {
     C pv[NR][2 * PP];
 #pragma unroll
     for (int r = 0; r < NR; ++r)
@@ -1026,21 +949,13 @@ k_apply(BatchArgs a, int j) {
     }
     dot_d += (double)dot_acc;
     dot_i += (double)dot_im;
-    nu_d += (double)nu_acc;
-    ka_d += (double)ka_acc;
   }
   if constexpr (TMA) {
     if (tma_err && tid == 0) st->status = kStatusTimeout;
   }
   if (j == 0) return;
-  constexpr int KR = FUSED ? 4 : 2;   // <x_j, w> (re, im), and fused: |w|^2, |x_j|^2
-  double v[KR];
-  v[0] = dot_d;
-  v[1] = dot_i;
-  if constexpr (FUSED) {
-    v[2] = nu_d;
-    v[3] = ka_d;
-  }
+  constexpr int KR = 2;   // <x_j, w>: real and imaginary part
+  double v[KR] = {dot_d, dot_i};
   if (reduce_last_block<KR>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
                             a.partials, a.counters + ab.vec, red, &flag)) {
     if (tid == 0) {
@@ -1052,28 +967,6 @@ k_apply(BatchArgs a, int j) {
         st->alpha_im[j] = v[1] * sj;
         if (!isfinite(v[0]) || !isfinite(v[1])) {
           st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1;
-        } else if (FUSED && j < st->m) {
-          // beta_j of the update this pass replaces (see k_update)
-          const double h2 = st->alpha[j] * st->alpha[j] + st->alpha_im[j] * st->alpha_im[j];
-          const double b2 = v[KR - 2] - h2 * (2.0 - sj * sj * v[KR - 1]);
-          const double beta = sqrt(fmax(b2, 0.0));
-          const double sc = fmax(st->scale, fabs(st->alpha[j]));
-          st->beta[j] = beta;
-          st->sc_at[j] = sc;
-          if (!isfinite(beta)) {
-            st->status = 7; st->stopped = 1; st->m_eff = j;
-          } else if (beta <= a.break_tol * sc) {
-            st->stopped = 1; st->m_eff = j;
-          } else {
-            st->inv_scale[j + 1] = 1.0 / beta;
-            st->scale = fmax(sc, beta);
-            // the next pass's coefficients: h_j s_j, s_{j+1} h_j, beta_{j-1} s_{j-1}
-            st->fco[0] = (float)(st->alpha[j] * sj);
-            st->fco[1] = (float)(st->alpha_im[j] * sj);
-            st->fco[2] = (float)(st->alpha[j] * st->inv_scale[j + 1]);
-            st->fco[3] = (float)(st->alpha_im[j] * st->inv_scale[j + 1]);
-            st->fco[4] = j >= 2 ? (float)(st->beta[j - 1] * st->inv_scale[j - 1]) : 0.f;
-          }
         }
       } else {
         if (vd.out_energy) vd.out_energy[st->step] = v[0] / a.Ns;
@@ -2293,13 +2186,6 @@ static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShap
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if constexpr (sizeof(R) == 4 && !SPLIT && !TMA) {
-    if (a.fused && j >= 1) {   // fused Lanczos passes
-      if (sh.vec) k_apply<R, NR, PP, V, MINB, false, 0, NT, true><<<nblk, threads, sh.smem, s>>>(a, j);
-      else k_apply<R, NR, PP, false, MINB, false, 0, NT, true><<<nblk, threads, sh.smem, s>>>(a, j);
-      return cudaGetLastError();
-    }
-  }
   if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
   else k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
@@ -2316,14 +2202,6 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
-  if constexpr (sizeof(R) == 4 && !SPLIT && !TMA) {
-    e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, false, 0, NT, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, false, 0, NT, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-  }
   if constexpr (SPLIT && CB == 0) {
     const int smc = (int)sh.smem_c;
     e = cudaFuncSetAttribute(k_apply_tup<R, PPC, false, MINBC>,
