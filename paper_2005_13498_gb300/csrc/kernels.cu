@@ -61,16 +61,25 @@ __device__ __forceinline__ void cax(C& s, R g, const C& v) {
     s.y += g * v.y;
   }
 }
-// acc += c s (complex)
+// acc += c s (complex), each component a chain of two fused multiply-adds
+// into acc: no product is rounded on its own (two FMAs per component, where
+// acc + (a b - c d) takes a multiply, an FMA and an add)
 template <typename C>
-__device__ __forceinline__ void cmac(C& acc, const C& c, const C& s) {
+__device__ __forceinline__ void cmac(C& acc, const C c, const C s) {
   if constexpr (sizeof(C) == 8) {
     acc = ffma2(make_float2(c.x, c.x), s, acc);
     acc = ffma2(make_float2(-c.y, c.y), make_float2(s.y, s.x), acc);
   } else {
-    acc.x += c.x * s.x - c.y * s.y;
-    acc.y += c.x * s.y + c.y * s.x;
+    acc.x = __fma_rn(-c.y, s.y, __fma_rn(c.x, s.x, acc.x));
+    acc.y = __fma_rn(c.y, s.x, __fma_rn(c.x, s.y, acc.y));
   }
+}
+// the same for the two complex64 values of a 16-byte word
+__device__ __forceinline__ void cmac4(float4& acc, const float2 c, const float4 s) {
+  float2 a = make_float2(acc.x, acc.y), b = make_float2(acc.z, acc.w);
+  cmac(a, c, make_float2(s.x, s.y));
+  cmac(b, c, make_float2(s.z, s.w));
+  acc = make_float4(a.x, a.y, b.x, b.y);
 }
 
 template <typename R> __device__ __forceinline__ typename C2T<R>::T
@@ -1535,22 +1544,19 @@ __global__ void __launch_bounds__(32) k_conv_check(BatchArgs a, int j) {
 // sum_k w_d[k] |psi_k|^2 (Sec. 3.5), then the per-step bookkeeping.
 // In float32 the dominant coefficient c_1 is split hi + lo and its product is
 // added last, which keeps the rounding of c_1 out of |psi| (the norm would
-// otherwise drift by ~1e-7 per step).
+// otherwise drift by ~1e-7 per step).  Every product is accumulated by a
+// chain of fused multiply-adds into p (cmac): when c_1 x was rounded on its
+// own first, as in p + (a b - c d), the rounding errors of the many equal
+// amplitudes of a symmetric state added up coherently and |psi|^2 drifted
+// by 1-5e-8 per step, with a sign that depends on tau.
 template <typename R, typename C>
 __device__ __forceinline__ C combine_one(const C* cf, C cf_lo, int n, const C* V,
                                          int64_t D, int64_t i, C x) {
-  C p;
-  p.x = cf_lo.x * x.x - cf_lo.y * x.y;
-  p.y = cf_lo.x * x.y + cf_lo.y * x.x;
+  C p = czero<C>();
+  cmac(p, cf_lo, x);
 #pragma unroll 4
-  for (int jj = 1; jj < n; ++jj) {
-    const C v = V[(size_t)(jj - 1) * D + i];
-    const C c = cf[jj];
-    p.x += c.x * v.x - c.y * v.y;
-    p.y += c.x * v.y + c.y * v.x;
-  }
-  p.x += cf[0].x * x.x - cf[0].y * x.y;
-  p.y += cf[0].x * x.y + cf[0].y * x.x;
+  for (int jj = 1; jj < n; ++jj) cmac(p, cf[jj], V[(size_t)(jj - 1) * D + i]);
+  cmac(p, cf[0], x);
   return p;
 }
 
@@ -1637,10 +1643,8 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
         const float2 lo = *reinterpret_cast<const float2*>(&cf_lo);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          p[q].x = lo.x * xv[q].x - lo.y * xv[q].y;
-          p[q].y = lo.x * xv[q].y + lo.y * xv[q].x;
-          p[q].z = lo.x * xv[q].z - lo.y * xv[q].w;
-          p[q].w = lo.x * xv[q].w + lo.y * xv[q].z;
+          p[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          cmac4(p[q], lo, xv[q]);
         }
         // JV Krylov vectors per round, all JV x Q loads issued before their
         // products, by volatile loads at in-range indices (out-of-range
@@ -1669,12 +1673,7 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
           for (int u = 0; u < JV; ++u) {
             const float2 c = *reinterpret_cast<const float2*>(&cf[jj + u]);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-              p[q].x += c.x * v[u][q].x - c.y * v[u][q].y;
-              p[q].y += c.x * v[u][q].y + c.y * v[u][q].x;
-              p[q].z += c.x * v[u][q].z - c.y * v[u][q].w;
-              p[q].w += c.x * v[u][q].w + c.y * v[u][q].z;
-            }
+            for (int q = 0; q < Q; ++q) cmac4(p[q], c, v[u][q]);
           }
         }
         for (; jj < n; ++jj) {
@@ -1685,20 +1684,12 @@ __global__ void __launch_bounds__(256) k_combine(BatchArgs a) {
           for (int q = 0; q < Q; ++q)
             v[q] = ok[q] ? __ldcs(Vj + idx[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            p[q].x += c.x * v[q].x - c.y * v[q].y;
-            p[q].y += c.x * v[q].y + c.y * v[q].x;
-            p[q].z += c.x * v[q].z - c.y * v[q].w;
-            p[q].w += c.x * v[q].w + c.y * v[q].z;
-          }
+          for (int q = 0; q < Q; ++q) cmac4(p[q], c, v[q]);
         }
         const float2 c0 = *reinterpret_cast<const float2*>(&cf[0]);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          p[q].x += c0.x * xv[q].x - c0.y * xv[q].y;
-          p[q].y += c0.x * xv[q].y + c0.y * xv[q].x;
-          p[q].z += c0.x * xv[q].z - c0.y * xv[q].w;
-          p[q].w += c0.x * xv[q].w + c0.y * xv[q].z;
+          cmac4(p[q], c0, xv[q]);
           if (ok[q]) x4[idx[q]] = p[q];
         }
       } else {
