@@ -77,7 +77,9 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms; each sample
+    keeps the host time it arrived at, so that summary() can keep the
+    samples of one timed window."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -92,7 +94,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -102,7 +104,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -112,10 +114,18 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, max clock and active reasons of the samples that
+        arrived between host times t0 and t1 (plus one sampling interval);
+        all samples if that window holds none."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if t0 is not None and t1 is not None:
+            win = [x for x in lines if t0 <= x[0] <= t1 + 0.1]
+            lines = win or lines
+        window = "timed region" if lines is not self.lines else "whole sampler run"
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -130,7 +140,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def dist_env():
@@ -565,7 +575,8 @@ def main():
         for _ in range(4):
             ed.ed_apply_H(h.ctx, v, wv, code)
         torch.cuda.synchronize()
-        print(json.dumps({"apply_only": args.apply_only, "D": h.D}))
+        print(json.dumps({"apply_only": args.apply_only, "D": h.D,
+                          "config": ed.ed_get_apply_config(h.ctx)[1]}))
         h.close()
         return
     if args.spectral_only:
@@ -601,17 +612,19 @@ def main():
         torch.cuda.synchronize()
 
     # ---------------------------------------------------------------- headline
-    ed.ed_propagate(h.ctx, psi32, ed.ED_C64, pulse, t_start - args.warmup * dt, dt,
-                    args.warmup, m, stream=stream)
-    barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev) as clk:
+    with ClockSampler(dev) as clk:      # running before the timed region starts
+        ed.ed_propagate(h.ctx, psi32, ed.ED_C64, pulse, t_start - args.warmup * dt, dt,
+                        args.warmup, m, stream=stream)
         barrier()
+        time.sleep(0.3)
+        h0 = time.time()
         e0.record(stream)
         out = ed.ed_propagate(h.ctx, psi32, ed.ED_C64, pulse, t_start, dt, args.steps, m,
                               stream=stream)
         e1.record(stream)
         barrier()
+        h1 = time.time()
     t_ms = job_time_ms(e0.elapsed_time(e1), ws, device="cuda")
     value = job_value(t_ms, ws, args.steps)
     ms_step = t_ms / args.steps
@@ -627,7 +640,7 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
             "config": bench_config(t_start, m, ws), "m_eff_min": int(m_eff.min()),
-            "clocks": clk.summary(), "gpu_launches": gpu_launches,
+            "clocks": clk.summary(h0, h1), "gpu_launches": gpu_launches,
             "apply_kernel": dict(ainfo, config=acfg),
             "ground_state": {"E0": E0, "residual": resid}}
 
@@ -695,7 +708,8 @@ def main():
         a1.record(stream)
         barrier()
         hv64 = a0.elapsed_time(a1) / 10
-        line["hv_c128"] = {"GBs": 2 * D * 16 / (hv64 * 1e-3) / 1e9, "ms": hv64}
+        line["hv_c128"] = {"GBs": 2 * D * 16 / (hv64 * 1e-3) / 1e9, "ms": hv64,
+                           "config": ed.ed_get_apply_config(h.ctx)[1]}
         # float64 propagator on the same workload
         ed.ed_propagate(h.ctx, psi64, ed.ED_C128, pulse, t_start - dt, dt, 1, m, stream=stream)
         barrier()
@@ -707,7 +721,8 @@ def main():
         barrier()
         fp64_ms = f0.elapsed_time(f1) / args.fp64_steps
         line["fp64"] = {"ms_per_step": fp64_ms, "steps": args.fp64_steps,
-                        "speedup_c64_over_c128": fp64_ms / ms_step}
+                        "speedup_c64_over_c128": fp64_ms / ms_step,
+                        "apply_config": ed.ed_get_apply_config(h.ctx)[0]}
         # spectral batch (Ns=14 ladder): c and c^+ on every site and spin of
         # the state, 56 vectors of 3003x3432 / 3432x3003 plus psi, m=20,
         # complex64, one batched launch per kernel; against 56 sequential

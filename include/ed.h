@@ -322,14 +322,20 @@ ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme);
  * one chunk of columns at a time, for vectors larger than the L2), and
  * whether an extra producer warp stages the T_up source-row chunks in shared
  * memory with TMA bulk copies (tma = 1; used only for even dim_dn and
- * 16-byte aligned vectors).
+ * 16-byte aligned vectors), and whether a thread block takes one row u of
+ * rows_per_cta vectors of one sector instead of rows_per_cta rows of one
+ * vector (multi_vector = 1: for batches such as the c / c+ propagations of
+ * Sec. 3.7, where the T_dn tables and the entry list of u then serve those
+ * vectors together; the autotuner does not pick these entries, which
+ * measured slower than one-vector blocks on the batches, so they run only
+ * when pinned with ed_set_apply_config).
  * ed_apply_config_count returns the number of entries; ed_apply_config_info
  * describes entry `config` (ED_ERR_ARG if out of range; any output pointer
  * may be NULL).                                                              */
 int ed_apply_config_count(void);
 ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
                                int* pairs_per_thread, int* ctas_per_sm,
-                               int* split, int* tma);
+                               int* split, int* tma, int* multi_vector);
 
 /* Process-wide choice of the H v configuration for every propagation,
  * ed_apply_H plan and ground-state solve set up after the call (contexts

@@ -397,9 +397,10 @@ ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme) {
 int ed_apply_config_count(void) { return apply_config_count(); }
 
 ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
-                               int* pairs_per_thread, int* ctas_per_sm, int* split, int* tma) {
-  int f, nr, pp, mb, sp, tm;
-  if (!apply_config_info(config, &f, &nr, &pp, &mb, &sp, &tm))
+                               int* pairs_per_thread, int* ctas_per_sm, int* split, int* tma,
+                               int* multi_vector) {
+  int f, nr, pp, mb, sp, tm, mv;
+  if (!apply_config_info(config, &f, &nr, &pp, &mb, &sp, &tm, &mv))
     return fail(nullptr, ED_ERR_ARG, "no apply configuration " + std::to_string(config));
   if (fp64) *fp64 = f;
   if (rows_per_cta) *rows_per_cta = nr;
@@ -407,6 +408,7 @@ ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,
   if (ctas_per_sm) *ctas_per_sm = mb;
   if (split) *split = sp;
   if (tma) *tma = tm;
+  if (multi_vector) *multi_vector = mv;
   return ED_OK;
 }
 
@@ -496,19 +498,16 @@ ed_status ed_apply_H(ed_ctx* ctx, const void* v, void* w, ed_dtype dtype, int nv
     tt.dim_up.assign(nvec, (int)ctx->dim_up);
     tt.dim_dn.assign(nvec, (int)ctx->dim_dn);
     tt.up.assign(nvec, &ctx->sec.up);
+    tt.sector.assign(nvec, 0);
     tt.args = P.args;
     std::vector<ApplyBlock> amap, cmap;
     CKS(ctx, tune_apply(tt, s, &P.shape, &amap, &cmap));
     CK(ctx, prepare_apply(fp64, P.shape));
-    for (int b = 0; b < (int)amap.size(); ++b) {
-      VecDev& vv = vd[amap[b].vec];
-      if (b == 0 || amap[b - 1].vec != amap[b].vec) vv.apply_begin = b;
-      vv.apply_end = b + 1;
-    }
+    assign_apply_ranges(amap, P.shape.mv, vd.data(), nvec);
     CK(ctx, upload(P.vec, vd));
     CK(ctx, upload(P.amap, amap));
     CK(ctx, upload(P.cmap, cmap));
-    CK(ctx, P.partials.alloc(sizeof(double) * 4 * amap.size()));
+    CK(ctx, P.partials.alloc(sizeof(double) * apply_partials_per_block(P.shape) * amap.size()));
     P.args.vec = static_cast<VecDev*>(P.vec.p);
     P.args.apply_map = static_cast<const ApplyBlock*>(P.amap.p);
     P.args.col_map = static_cast<const ApplyBlock*>(P.cmap.p);

@@ -139,16 +139,16 @@ std::string gs_apply_setup(GsApply& G, ed_ctx* ctx, const double2* x, double2* w
   tt.dim_up = {(int)ctx->dim_up};
   tt.dim_dn = {(int)ctx->dim_dn};
   tt.up = {&ctx->sec.up};
+  tt.sector = {0};
   tt.args = G.args;
   std::vector<ApplyBlock> amap, cmap;
   std::string err = tune_apply(tt, s, &G.shape, &amap, &cmap);
   if (!err.empty()) return err;
-  vd[0].apply_begin = 0;
-  vd[0].apply_end = (int)amap.size();
+  assign_apply_ranges(amap, G.shape.mv, vd.data(), 1);
   ED_TRY(upload(G.vec, vd));
   ED_TRY(upload(G.amap, amap));
   ED_TRY(upload(G.cmap, cmap));
-  ED_TRY(G.partials.alloc(sizeof(double) * 4 * amap.size()));
+  ED_TRY(G.partials.alloc(sizeof(double) * apply_partials_per_block(G.shape) * amap.size()));
   G.args.vec = static_cast<VecDev*>(G.vec.p);
   G.args.apply_map = static_cast<const ApplyBlock*>(G.amap.p);
   G.args.col_map = static_cast<const ApplyBlock*>(G.cmap.p);

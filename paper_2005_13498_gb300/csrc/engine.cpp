@@ -92,6 +92,13 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
     cands.erase(std::remove_if(cands.begin(), cands.end(),
                                [](const LaunchShape& c) { return c.tma; }),
                 cands.end());
+  // multi-vector configurations run only when pinned: on both spectral
+  // batches they measured slower than one-vector blocks (the vectors that
+  // share a block multiply the working set of the T_up row gathers)
+  if (forced_apply_config() < 0)
+    cands.erase(std::remove_if(cands.begin(), cands.end(),
+                               [](const LaunchShape& c) { return c.mv; }),
+                cands.end());
   if (cands.empty()) return "apply kernel: rows too long for shared memory";
   for (auto& c : cands) c.vec = t.vec_ok;
   // row orders of the vectors' up spaces (reverse Cuthill-McKee), computed once
@@ -103,6 +110,21 @@ std::string tune_apply(const ApplyTuneTarget& t, cudaStream_t s, LaunchShape* sh
   auto build = [&](const LaunchShape& sh) {
     map->clear();
     cmap->clear();
+    if (sh.mv) {   // the vectors of each sector, in batch order, nr at a time
+      std::vector<int> done(t.dim_up.size(), 0);
+      for (size_t i = 0; i < t.dim_up.size(); ++i) {
+        if (done[i]) continue;
+        std::vector<int> ids;
+        for (size_t k = i; k < t.dim_up.size(); ++k)
+          if (!done[k] && (k < t.sector.size() ? t.sector[k] : (int)k) ==
+                              (i < t.sector.size() ? t.sector[i] : (int)i)) {
+            ids.push_back((int)k);
+            done[k] = 1;
+          }
+        append_mv_blocks(*map, ids, t.dim_up[i], sh.nr, order_of(i));
+      }
+      return;
+    }
     for (size_t i = 0; i < t.dim_up.size(); ++i) {
       append_apply_blocks(*map, (int)i, t.dim_up[i], sh.nr, order_of(i));
       if (sh.split && sh.cb > 0) append_col_blocks(*cmap, (int)i, t.dim_dn[i], t.fp64, sh.cb);
@@ -352,6 +374,7 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
     tt.dim_dn.push_back(sectors_[vecs_[i].sector].dim_dn);
     tt.up.push_back((size_t)vecs_[i].sector < up_tabs.size() ? up_tabs[vecs_[i].sector]
                                                                : nullptr);
+    tt.sector.push_back(vecs_[i].sector);
   }
   tt.args = args_;
   std::vector<ApplyBlock> cmap;
@@ -359,21 +382,15 @@ std::string Engine::setup(const EngineConfig& cfg, const std::vector<SectorDev>&
   if (!err.empty()) return err;
   ED_TRY(prepare_apply(cfg.fp64, shape_));
   n_apply_ = (int)amap.size();
-  for (int i = 0; i < nv; ++i) {
-    vd[i].apply_begin = -1;
-    vd[i].apply_end = -1;
-  }
-  for (int b = 0; b < n_apply_; ++b) {
-    VecDev& v = vd[amap[b].vec];
-    if (v.apply_begin < 0) v.apply_begin = b;
-    v.apply_end = b + 1;
-  }
+  assign_apply_ranges(amap, shape_.mv, vd.data(), nv);
   ED_TRY(d_amap_.alloc(sizeof(ApplyBlock) * amap.size()));
   ED_TRY(d_cmap_.alloc(sizeof(ApplyBlock) * std::max<size_t>(1, cmap.size())));
   if (!cmap.empty())
     ED_TRY(cudaMemcpyAsync(d_cmap_.p, cmap.data(), sizeof(ApplyBlock) * cmap.size(),
                            cudaMemcpyHostToDevice, stream));
-  ED_TRY(d_partials_.alloc(sizeof(double) * 4 * std::max(n_apply_, n_ew_)));
+  ED_TRY(d_partials_.alloc(sizeof(double) *
+                           std::max(apply_partials_per_block(shape_) * n_apply_,
+                                    (size_t)4 * n_ew_)));
   ED_TRY(cudaMemcpyAsync(d_vec_.p, vd.data(), sizeof(VecDev) * nv, cudaMemcpyHostToDevice,
                          stream));
   ED_TRY(cudaMemcpyAsync(d_amap_.p, amap.data(), sizeof(ApplyBlock) * amap.size(),

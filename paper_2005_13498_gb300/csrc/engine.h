@@ -61,6 +61,7 @@ struct ApplyTuneTarget {
   std::vector<int> dim_up;      // per vector
   std::vector<int> dim_dn;      // per vector
   std::vector<const SpinTable*> up;   // per vector: up-spin table (CTA order), or empty
+  std::vector<int> sector;      // per vector: sector index (equal = same tables)
   BatchArgs args{};             // vec / sec / coefs valid; the block maps are set here
 };
 // Process-wide choice of the apply configuration: -1 lets the autotuner pick

@@ -403,7 +403,8 @@ struct TileIO {
 //  * complex128 (FP64-pipe bound): signed sums per bond group, multiplied
 //    by c_g once per group.
 template <int NR, int PP, int KA, bool VEC, int NT>
-__device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2* x,
+__device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd,
+                                              const float2* const (&xr)[NR],
                                               const float4* coefQ, const int (&urow)[NR],
                                               int nrows, int pc,
                                               int npairs, int dim_dn, float2 (&acc)[NR][2 * PP]) {
@@ -434,7 +435,7 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2*
       float2 v[4][2 * KA];
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq) {
-        const float2* src = x + rows[qq];
+        const float2* src = xr[r] + rows[qq];
 #pragma unroll
         for (int k = 0; k < KA; ++k) {
           if constexpr (VEC) {
@@ -464,8 +465,11 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd, const float2*
   }
 }
 
+// complex128: row r gathers from xr[r] (one vector, or one per row in
+// multi-vector blocks)
 template <int NR, int PP, int KA, int NT>
-__device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double2* x,
+__device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd,
+                                               const double2* const (&xr)[NR],
                                                const double2* coefS, const int (&urow)[NR],
                                                int nrows, int pc,
                                                int npairs, int dim_dn,
@@ -501,7 +505,7 @@ __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd, const double
       for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
         for (int k = 0; k < KA; ++k)
-          load_pair<C, false>(x + rows[qq], pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
+          load_pair<C, false>(xr[r] + rows[qq], pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq) {
         const uint32_t g = (ents[qq] >> kEntGroupShift) & 0xFFu;
@@ -531,10 +535,49 @@ __device__ __forceinline__ void tup_chunk(const SectorDev& sd, const typename C2
                                           const int (&urow)[NR], int nrows, int pc, int npairs,
                                           int dim_dn,
                                           typename C2T<R>::T (&acc)[NR][2 * PP]) {
+  const typename C2T<R>::T* xr[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) xr[r] = x;
   if constexpr (sizeof(R) == 4)
-    tup_chunk_c64<NR, PP, KA, VEC, NT>(sd, x, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
+    tup_chunk_c64<NR, PP, KA, VEC, NT>(sd, xr, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
   else
-    tup_chunk_c128<NR, PP, KA, NT>(sd, x, coefS, urow, nrows, pc, npairs, dim_dn, acc);
+    tup_chunk_c128<NR, PP, KA, NT>(sd, xr, coefS, urow, nrows, pc, npairs, dim_dn, acc);
+}
+
+// The same for multi-vector blocks: row r of the block is row u of the
+// vector at xr[r].  The rows walk u's entry list one after the other (the
+// list, its source offsets and coefficient slots are L1 hits after the
+// first row), which keeps the accumulators of one row live at a time.
+template <typename R, int NR, int PP, int KA, bool VEC, int NT>
+__device__ __forceinline__ void tup_chunk_mv(const SectorDev& sd,
+                                             const typename C2T<R>::T* const (&xr)[NR],
+                                             const typename C2T<R>::T* coefS, const float4* coefQ,
+                                             int u, int nrows, int pc, int npairs, int dim_dn,
+                                             typename C2T<R>::T (&acc)[NR][2 * PP]) {
+  int urow[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) urow[r] = u;
+  if constexpr (sizeof(R) == 4)
+    tup_chunk_c64<NR, PP, KA, VEC, NT>(sd, xr, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
+  else
+    tup_chunk_c128<NR, PP, KA, NT>(sd, xr, coefS, urow, nrows, pc, npairs, dim_dn, acc);
+}
+
+// The reduced <x_j, w> of one vector: j >= 1, h_jj = <v_j, w> of Algorithm 6,
+// whose real part is alpha_j (H is Hermitian; the update subtracts the whole
+// complex h_jj v_j); j == -1, the energy <x_1, H x_1> / Ns at this step.
+__device__ __forceinline__ void apply_dot_result(LanczosState* st, double* out_energy, int j,
+                                                 double re, double im, int Ns) {
+  if (j >= 1) {
+    const double sj = st->inv_scale[j];
+    st->alpha[j] = re * sj;
+    st->alpha_im[j] = im * sj;
+    if (!isfinite(re) || !isfinite(im)) {
+      st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1;
+    }
+  } else {
+    if (out_energy) out_energy[st->step] = re / Ns;
+  }
 }
 
 // Shared-memory bytes in front of the TMA ring / end of the apply's dynamic
@@ -566,7 +609,7 @@ __host__ __device__ inline size_t apply_coef_end(int max_dim_dn, int nr, int n_g
 //  * Epilogue: the diagonal U * popcount(up & dn) (+ on-site energies) times
 //    the staged x joins the sums, w = s_j acc - beta_{j-1} s_{j-1} x_{j-1} is
 //    stored in pairs, and the partial of Re<x_j, w> is accumulated.
-template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS, int NT>
+template <typename R, int NR, int PP, bool VEC, int MINB, bool SPLIT, int TMAS, int NT, bool MV>
 __global__ void __launch_bounds__(TMAS ? NT + 32 : NT, MINB)
 k_apply(BatchArgs a, int j) {
   constexpr bool TMA = TMAS > 0;       // TMAS: ring stages of the TMA configurations
@@ -576,22 +619,42 @@ k_apply(BatchArgs a, int j) {
   constexpr int T = NT;                      // consumer threads (all threads without TMA)
   constexpr uint32_t kSlotBytes = (uint32_t)(T * PP * 2 * sizeof(C));   // one chunk of a row
   static_assert(!(TMA && SPLIT), "the TMA ring serves the one-kernel T_up");
+  static_assert(!MV || (!TMA && !SPLIT), "multi-vector blocks use the one-kernel gathers");
+  static_assert((NT / 32 + (TMA ? 1 : 0)) * (MV ? 2 * NR : 2) <= 64, "reduction scratch");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32 * 2];
+  __shared__ double red[64];
   __shared__ int flag;
   __shared__ int tma_err;
 
+  // One vector: the block's rows ab.row[0 .. nrows) of vector ab.vec.
+  // Multi-vector (MV): row ab.row0 of the vectors ab.row[0 .. nrows), all of
+  // one sector; every block of such a subgroup lists the same vectors, and
+  // ab.vec, the first of them, holds the subgroup's block range and
+  // reduction counter.
   const ApplyBlock ab = a.apply_map[blockIdx.x];
   const VecDev vd = a.vec[ab.vec];
   LanczosState* st = a.st + ab.vec;
-  if (j >= 1 && lanczos_done(st, j)) return;   // uniform over the vector's blocks
+  const int nrows = ab.nrows;
+  bool rdone[NR];   // MV: rows whose vector has finished this step's Lanczos
+  if constexpr (MV) {
+    bool all = true;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      rdone[r] = r >= nrows || (j >= 1 && lanczos_done(a.st + ab.row[r], j));
+      all = all && rdone[r];
+    }
+    if (all) return;   // uniform over the subgroup's blocks
+  } else {
+    if (j >= 1 && lanczos_done(st, j)) return;   // uniform over the vector's blocks
+#pragma unroll
+    for (int r = 0; r < NR; ++r) rdone[r] = false;
+  }
   const SectorDev sd = a.sec[vd.sector];
   const int dim_dn = sd.dim_dn;
   const int npairs = (dim_dn + 1) >> 1;
-  const int nrows = ab.nrows;
   int urow[NR];   // the block's rows (padding slots repeat the first row)
 #pragma unroll
-  for (int r = 0; r < NR; ++r) urow[r] = r < nrows ? ab.row[r] : ab.row[0];
+  for (int r = 0; r < NR; ++r) urow[r] = MV ? ab.row0 : (r < nrows ? ab.row[r] : ab.row[0]);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
 
@@ -646,6 +709,26 @@ k_apply(BatchArgs a, int j) {
   const R s_in = (j >= 1) ? (R)st->inv_scale[j] : (R)1;
   const R s_prev = (j >= 2) ? (R)(st->beta[j - 1] * st->inv_scale[j - 1]) : (R)0;
   const R U = (R)a.U;
+  // per-row vectors (one vector: all rows alike)
+  const C* xr[NR];
+  const C* xpr[NR];
+  C* wr[NR];
+  R sinr[NR], sprevr[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if constexpr (MV) {
+      const int vi = ab.row[r < nrows ? r : 0];
+      const VecDev& vr = a.vec[vi];
+      const LanczosState* sr = a.st + vi;
+      xr[r] = static_cast<const C*>(j >= 1 ? xptr(vr, j, sizeof(C)) : vr.x1);
+      xpr[r] = (j >= 2) ? static_cast<const C*>(xptr(vr, j - 1, sizeof(C))) : nullptr;
+      wr[r] = static_cast<C*>(vr.w);
+      sinr[r] = (j >= 1) ? (R)sr->inv_scale[j] : (R)1;
+      sprevr[r] = (j >= 2) ? (R)(sr->beta[j - 1] * sr->inv_scale[j - 1]) : (R)0;
+    } else {
+      xr[r] = x; xpr[r] = xp; wr[r] = w; sinr[r] = s_in; sprevr[r] = s_prev;
+    }
+  }
 
   // ---- stage the NR rows column by column, one column per thread and
   // iteration (consecutive lanes write consecutive tile columns: no bank
@@ -660,7 +743,7 @@ k_apply(BatchArgs a, int j) {
       C v[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r)
-        v[r] = (r < nrows && d < dim_dn) ? __ldcg(x + (size_t)urow[r] * dim_dn + d) : czero<C>();
+        v[r] = (r < nrows && d < dim_dn) ? __ldcg(xr[r] + (size_t)urow[r] * dim_dn + d) : czero<C>();
       TIO::store(tile, d, v);
     }
   }
@@ -675,6 +758,9 @@ k_apply(BatchArgs a, int j) {
   __syncthreads();
 
   double dot_d = 0.0, dot_i = 0.0;
+  double dd_r[NR], di_r[NR];   // MV: per vector
+#pragma unroll
+  for (int r = 0; r < NR; ++r) { dd_r[r] = 0.0; di_r[r] = 0.0; }
   uint32_t cidx = 0;     // T_up entries consumed so far (TMA ring position)
   if (TMA && tid >= T) {
     // ---- producer warp (TMA configurations): one elected lane issues the
@@ -896,7 +982,14 @@ k_apply(BatchArgs a, int j) {
     }
     // ---- T_up: the padded entry lists of the rows (uniform over the block);
     // versioned on how many column-pair groups of this chunk hold valid pairs
-    if constexpr (!SPLIT && !TMA) {
+    if constexpr (MV) {
+      if (PP > 1 && pc + (PP - 1) * T < npairs)
+        tup_chunk_mv<R, NR, PP, PP, VEC, NT>(sd, xr, coefS, coefQ, urow[0], nrows, pc, npairs,
+                                              dim_dn, acc);
+      else
+        tup_chunk_mv<R, NR, PP, 1, VEC, NT>(sd, xr, coefS, coefQ, urow[0], nrows, pc, npairs,
+                                             dim_dn, acc);
+    } else if constexpr (!SPLIT && !TMA) {
       if (PP > 1 && pc + (PP - 1) * T < npairs)
         tup_chunk<R, NR, PP, PP, VEC, NT>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
       else
@@ -904,6 +997,9 @@ k_apply(BatchArgs a, int j) {
     }
     // ---- epilogue: previous-vector loads first, then scale, subtract, store
     R dot_acc = (R)0, dot_im = (R)0;
+    R dacc_r[NR], dim_r[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) { dacc_r[r] = (R)0; dim_r[r] = (R)0; }
     {
     C pv[NR][2 * PP];
 #pragma unroll
@@ -911,8 +1007,8 @@ k_apply(BatchArgs a, int j) {
 #pragma unroll
       for (int k = 0; k < PP; ++k) {
         const int p = pc + tid + k * T;
-        if (xp && r < nrows && p < npairs)
-          load_pair<C, VEC, true>(xp + (size_t)urow[r] * dim_dn, p, dim_dn, pv[r][2 * k],
+        if (xpr[r] && r < nrows && p < npairs)
+          load_pair<C, VEC, true>(xpr[r] + (size_t)urow[r] * dim_dn, p, dim_dn, pv[r][2 * k],
                                   pv[r][2 * k + 1]);
         else { pv[r][2 * k] = czero<C>(); pv[r][2 * k + 1] = czero<C>(); }
       }
@@ -941,16 +1037,21 @@ k_apply(BatchArgs a, int j) {
             a1.x += g1 * xb[r].x;
             a1.y += g1 * xb[r].y;
             C o0, o1;
-            o0.x = s_in * a0.x - s_prev * pv[r][2 * k].x;
-            o0.y = s_in * a0.y - s_prev * pv[r][2 * k].y;
-            o1.x = s_in * a1.x - s_prev * pv[r][2 * k + 1].x;
-            o1.y = s_in * a1.y - s_prev * pv[r][2 * k + 1].y;
-            store_pair<C, VEC, true>(w + (size_t)urow[r] * dim_dn, p, dim_dn, o0, o1);
-            dot_acc += xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
+            o0.x = sinr[r] * a0.x - sprevr[r] * pv[r][2 * k].x;
+            o0.y = sinr[r] * a0.y - sprevr[r] * pv[r][2 * k].y;
+            o1.x = sinr[r] * a1.x - sprevr[r] * pv[r][2 * k + 1].x;
+            o1.y = sinr[r] * a1.y - sprevr[r] * pv[r][2 * k + 1].y;
+            if (!rdone[r]) store_pair<C, VEC, true>(wr[r] + (size_t)urow[r] * dim_dn, p, dim_dn, o0, o1);
+            const R dre = xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
+            if constexpr (MV) dacc_r[r] += dre;
+            else dot_acc += dre;
             // Im h_jj: float32 only (in float64 it is rounding, and the
             // float64 apply is bound by its FP64 operations)
-            if constexpr (sizeof(R) == 4)
-              dot_im += xa[r].x * o0.y - xa[r].y * o0.x + xb[r].x * o1.y - xb[r].y * o1.x;
+            if constexpr (sizeof(R) == 4) {
+              const R dim = xa[r].x * o0.y - xa[r].y * o0.x + xb[r].x * o1.y - xb[r].y * o1.x;
+              if constexpr (MV) dim_r[r] += dim;
+              else dot_im += dim;
+            }
           }
         }
       }
@@ -958,28 +1059,33 @@ k_apply(BatchArgs a, int j) {
     }
     dot_d += (double)dot_acc;
     dot_i += (double)dot_im;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) { dd_r[r] += (double)dacc_r[r]; di_r[r] += (double)dim_r[r]; }
   }
   if constexpr (TMA) {
     if (tma_err && tid == 0) st->status = kStatusTimeout;
   }
   if (j == 0) return;
-  constexpr int KR = 2;   // <x_j, w>: real and imaginary part
-  double v[KR] = {dot_d, dot_i};
-  if (reduce_last_block<KR>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
-                            a.partials, a.counters + ab.vec, red, &flag)) {
-    if (tid == 0) {
-      if (j >= 1) {
-        // h_jj = <v_j, w> of Algorithm 6: the real part is alpha_j (H is
-        // Hermitian); the update subtracts the whole complex h_jj v_j
-        const double sj = st->inv_scale[j];
-        st->alpha[j] = v[0] * sj;
-        st->alpha_im[j] = v[1] * sj;
-        if (!isfinite(v[0]) || !isfinite(v[1])) {
-          st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1;
-        }
-      } else {
-        if (vd.out_energy) vd.out_energy[st->step] = v[0] / a.Ns;
-      }
+  if constexpr (MV) {
+    constexpr int KR = 2 * NR;   // <x_j, w> of each vector of the subgroup
+    double v[KR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) { v[2 * r] = dd_r[r]; v[2 * r + 1] = di_r[r]; }
+    if (reduce_last_block<KR>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
+                              a.partials, a.counters + ab.vec, red, &flag)) {
+      if (tid == 0)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (!rdone[r])
+            apply_dot_result(a.st + ab.row[r], a.vec[ab.row[r]].out_energy, j, v[2 * r],
+                             v[2 * r + 1], a.Ns);
+    }
+  } else {
+    constexpr int KR = 2;   // <x_j, w>: real and imaginary part
+    double v[KR] = {dot_d, dot_i};
+    if (reduce_last_block<KR>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
+                              a.partials, a.counters + ab.vec, red, &flag)) {
+      if (tid == 0) apply_dot_result(st, vd.out_energy, j, v[0], v[1], a.Ns);
     }
   }
 }
@@ -2058,7 +2164,7 @@ static int grid_for(int64_t n, int threads) {
 // register budget) of the row kernel; for the split apply also the pairs per
 // thread and occupancy of the column pass.  The autotuner times the feasible
 // ones.
-struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc, cb, tc; int tma; int nt; };
+struct ApplyCfg { bool fp64; int nr, pp, minb; bool split; int ppc, minbc, cb, tc; int tma; int nt; bool mv; };
 // tma: 0, or the ring stages of a configuration whose T_up row chunks are
 // staged by TMA
 static const ApplyCfg kApplyCfgs[] = {
@@ -2081,11 +2187,16 @@ static const ApplyCfg kApplyCfgs[] = {
     // the same with a 512-thread row pass (twice the warps per SM on long rows),
     // and with two rows in one 1024-thread CTA per SM
     {false, 1, 1, 2, true, 2, 3, 0, 256, 0, 512}, {false, 2, 1, 1, true, 2, 3, 0, 256, 0, 1024},
+    // multi-vector blocks (batches with several vectors in one sector): one
+    // row of nr vectors per CTA (the per-vector pointers and sums need more
+    // registers than configuration 1's three CTAs per SM allow)
+    {false, 2, 2, 2, false, 0, 0, 0, 0, 0, 256, true}, {true, 2, 1, 2, false, 0, 0, 0, 0, 0, 256, true},
 };
 static const int kNumApplyCfgs = (int)(sizeof(kApplyCfgs) / sizeof(kApplyCfgs[0]));
 
 int apply_config_count() { return kNumApplyCfgs; }
-bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split, int* tma) {
+bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split, int* tma,
+                       int* mv) {
   if (i < 0 || i >= kNumApplyCfgs) return false;
   const ApplyCfg& c = kApplyCfgs[i];
   *fp64 = c.fp64;
@@ -2094,6 +2205,7 @@ bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split
   *minb = c.minb;
   *split = c.split;
   *tma = c.tma > 0;
+  *mv = c.mv;
   return true;
 }
 
@@ -2112,6 +2224,7 @@ std::vector<LaunchShape> apply_candidates(int max_dim_up, int max_dim_dn, bool f
     sh.cb = c.cb;
     sh.tc = c.tc;
     sh.tma = c.tma > 0;
+    sh.mv = c.mv;
     sh.smem = apply_coef_end(max_dim_dn, c.nr, n_groups, fp64);
     if (c.tma)   // 128-byte aligned ring of row chunks + full/empty mbarriers
       sh.smem = ((sh.smem + 127) & ~(size_t)127) +
@@ -2161,7 +2274,7 @@ LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups)
 }
 
 template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC,
-          int TMA, int NT>
+          int TMA, int NT, bool MV>
 static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShape& sh,
                                   int j, cudaStream_t s) {
   constexpr bool V = sizeof(R) == 4;
@@ -2177,20 +2290,20 @@ static cudaError_t launch_apply_t(const BatchArgs& a, int nblk, const LaunchShap
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
-  else k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT><<<nblk, threads, sh.smem, s>>>(a, j);
+  if (sh.vec) k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT, MV><<<nblk, threads, sh.smem, s>>>(a, j);
+  else k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT, MV><<<nblk, threads, sh.smem, s>>>(a, j);
   return cudaGetLastError();
 }
 
 template <typename R, int NR, int PP, int MINB, bool SPLIT, int PPC, int MINBC, int CB, int TC,
-          int TMA, int NT>
+          int TMA, int NT, bool MV>
 static cudaError_t prepare_apply_t(const LaunchShape& sh) {
   constexpr bool V = sizeof(R) == 4;
   const int sm = (int)sh.smem;
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT>,
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NR, PP, false, MINB, SPLIT, TMA, NT, MV>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT>,
+  e = cudaFuncSetAttribute(k_apply<R, NR, PP, V, MINB, SPLIT, TMA, NT, MV>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
   if constexpr (SPLIT && CB == 0) {
@@ -2213,34 +2326,36 @@ static cudaError_t prepare_apply_t(const LaunchShape& sh) {
 
 // One switch over the configuration table for both prepare and launch.
 #define ED_APPLY_CONFIGS(X)                                \
-  X(0, float, 4, 2, 2, false, 1, 1, 32, 256, 0, 256)        \
-  X(1, float, 2, 2, 3, false, 1, 1, 32, 256, 0, 256)        \
-  X(2, float, 2, 1, 4, false, 1, 1, 32, 256, 0, 256)        \
-  X(3, float, 1, 2, 2, false, 1, 1, 32, 256, 0, 256)        \
-  X(4, double, 2, 1, 2, false, 1, 1, 32, 256, 0, 256)       \
-  X(5, double, 1, 1, 4, false, 1, 1, 32, 256, 0, 256)       \
-  X(6, double, 1, 1, 2, false, 1, 1, 32, 256, 0, 256)       \
-  X(7, float, 4, 2, 2, true, 1, 2, 32, 256, 0, 256)         \
-  X(8, float, 2, 2, 3, true, 1, 2, 32, 256, 0, 256)         \
-  X(9, float, 2, 1, 4, true, 1, 2, 32, 256, 0, 256)         \
-  X(10, float, 4, 2, 2, true, 2, 2, 32, 256, 0, 256)        \
-  X(11, double, 2, 1, 2, true, 1, 2, 32, 256, 0, 256)       \
-  X(12, double, 1, 1, 4, true, 1, 2, 32, 256, 0, 256)       \
-  X(13, float, 1, 2, 2, true, 1, 1, 16, 512, 0, 256)        \
-  X(14, double, 1, 1, 1, true, 1, 1, 16, 512, 0, 256)       \
-  X(15, float, 2, 2, 2, false, 1, 1, 32, 256, 6, 256)        \
-  X(16, float, 1, 2, 2, false, 1, 1, 32, 256, 8, 256)        \
-  X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6, 256)      \
-  X(18, float, 1, 2, 2, true, 1, 4, 0, 256, 0, 256)         \
-  X(19, float, 1, 2, 2, true, 2, 3, 0, 256, 0, 256)       \
-  X(20, float, 1, 1, 2, true, 2, 3, 0, 256, 0, 512)       \
-  X(21, float, 2, 1, 1, true, 2, 3, 0, 256, 0, 1024)
+  X(0, float, 4, 2, 2, false, 1, 1, 32, 256, 0, 256, false)  \
+  X(1, float, 2, 2, 3, false, 1, 1, 32, 256, 0, 256, false)  \
+  X(2, float, 2, 1, 4, false, 1, 1, 32, 256, 0, 256, false)  \
+  X(3, float, 1, 2, 2, false, 1, 1, 32, 256, 0, 256, false)  \
+  X(4, double, 2, 1, 2, false, 1, 1, 32, 256, 0, 256, false) \
+  X(5, double, 1, 1, 4, false, 1, 1, 32, 256, 0, 256, false) \
+  X(6, double, 1, 1, 2, false, 1, 1, 32, 256, 0, 256, false) \
+  X(7, float, 4, 2, 2, true, 1, 2, 32, 256, 0, 256, false)   \
+  X(8, float, 2, 2, 3, true, 1, 2, 32, 256, 0, 256, false)   \
+  X(9, float, 2, 1, 4, true, 1, 2, 32, 256, 0, 256, false)   \
+  X(10, float, 4, 2, 2, true, 2, 2, 32, 256, 0, 256, false)  \
+  X(11, double, 2, 1, 2, true, 1, 2, 32, 256, 0, 256, false) \
+  X(12, double, 1, 1, 4, true, 1, 2, 32, 256, 0, 256, false) \
+  X(13, float, 1, 2, 2, true, 1, 1, 16, 512, 0, 256, false)  \
+  X(14, double, 1, 1, 1, true, 1, 1, 16, 512, 0, 256, false) \
+  X(15, float, 2, 2, 2, false, 1, 1, 32, 256, 6, 256, false) \
+  X(16, float, 1, 2, 2, false, 1, 1, 32, 256, 8, 256, false) \
+  X(17, double, 1, 1, 2, false, 1, 1, 32, 256, 6, 256, false) \
+  X(18, float, 1, 2, 2, true, 1, 4, 0, 256, 0, 256, false)   \
+  X(19, float, 1, 2, 2, true, 2, 3, 0, 256, 0, 256, false)   \
+  X(20, float, 1, 1, 2, true, 2, 3, 0, 256, 0, 512, false)   \
+  X(21, float, 2, 1, 1, true, 2, 3, 0, 256, 0, 1024, false) \
+  X(22, float, 2, 2, 2, false, 1, 1, 32, 256, 0, 256, true)  \
+  X(23, double, 2, 1, 2, false, 1, 1, 32, 256, 0, 256, true)
 
 cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
   (void)fp64;
   if (sh.nr < 1 || sh.smem > 227 * 1024 || sh.smem_c > 227 * 1024) return cudaErrorInvalidValue;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT) \
-  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT>(sh);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT, MV) \
+  case i: return prepare_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT, MV>(sh);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;
@@ -2251,8 +2366,8 @@ cudaError_t prepare_apply(bool fp64, const LaunchShape& sh) {
 cudaError_t launch_apply(bool fp64, const BatchArgs& a, int nblk, const LaunchShape& sh,
                          int j, cudaStream_t s) {
   (void)fp64;
-#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT) \
-  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT>(a, nblk, sh, j, s);
+#define X(i, R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT, MV) \
+  case i: return launch_apply_t<R, NR, PP, MB, SP, PPC, MBC, CB, TC, TM, NT, MV>(a, nblk, sh, j, s);
   switch (sh.cfg) {
     ED_APPLY_CONFIGS(X)
     default: return cudaErrorInvalidValue;

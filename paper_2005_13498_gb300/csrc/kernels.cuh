@@ -1,6 +1,7 @@
 // Kernel launchers (host-callable), implemented in kernels.cu.
 #pragma once
 
+#include <algorithm>
 #include <vector>
 
 #include "common.h"
@@ -24,6 +25,7 @@ struct LaunchShape {
   int tc = 256;        // column-pass threads per CTA
   int ppc = 1;         // T_up pass: column pairs per thread (chunk = 256 ppc pairs)
   bool tma = false;    // T_up row chunks staged by TMA (one extra producer warp)
+  bool mv = false;     // multi-vector blocks: one row of nr vectors of one sector
 };
 
 // Feasible apply configurations for sectors of at most max_dim_up rows of
@@ -77,10 +79,53 @@ inline void append_apply_blocks(std::vector<ApplyBlock>& map, int vec, int dim_u
   }
 }
 
+// Multi-vector apply blocks: for every sector, its vectors (vec_ids, in
+// batch order) in subgroups of at most nr, and for each subgroup one block
+// per row u in the given order (natural when order is null): row0 = u,
+// nrows = vectors in the subgroup, row[r] = their batch indices, vec = the
+// first of them.
+inline void append_mv_blocks(std::vector<ApplyBlock>& map, const std::vector<int>& vec_ids,
+                             int dim_up, int nr, const std::vector<int>* order = nullptr) {
+  for (size_t g = 0; g < vec_ids.size(); g += nr) {
+    const int k = (int)std::min<size_t>(nr, vec_ids.size() - g);
+    for (int i = 0; i < dim_up; ++i) {
+      ApplyBlock b{vec_ids[g], order ? (*order)[i] : i, k, 0, {0, 0, 0, 0}};
+      for (int r = 0; r < k; ++r) b.row[r] = vec_ids[g + r];
+      map.push_back(b);
+    }
+  }
+}
+
+// Block range [apply_begin, apply_end) of every vector: its own blocks, or
+// in multi-vector maps the blocks of its subgroup (contiguous in the map).
+inline void assign_apply_ranges(const std::vector<ApplyBlock>& map, bool mv,
+                                VecDev* vd, int nvec) {
+  for (int i = 0; i < nvec; ++i) { vd[i].apply_begin = -1; vd[i].apply_end = -1; }
+  for (int b = 0; b < (int)map.size(); ++b) {
+    VecDev& v = vd[map[b].vec];
+    if (v.apply_begin < 0) v.apply_begin = b;
+    v.apply_end = b + 1;
+  }
+  if (mv)
+    for (const ApplyBlock& b : map)
+      for (int r = 0; r < b.nrows; ++r) {
+        vd[b.row[r]].apply_begin = vd[b.vec].apply_begin;
+        vd[b.row[r]].apply_end = vd[b.vec].apply_end;
+      }
+}
+
+// Doubles of reduction scratch per apply block (Re and Im of <x_j, w> per
+// vector of the block).
+inline size_t apply_partials_per_block(const LaunchShape& sh) {
+  return sh.mv ? std::max(4, 2 * sh.nr) : 4;
+}
+
 // The configuration table: its size, and the precision, rows per CTA, pairs
-// per thread, CTAs per SM and split flag of entry i (false if out of range).
+// per thread, CTAs per SM, split, TMA and multi-vector flags of entry i
+// (false if out of range).
 int apply_config_count();
-bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split, int* tma);
+bool apply_config_info(int i, int* fp64, int* nr, int* pp, int* minb, int* split, int* tma,
+                       int* mv);
 // The default configuration (first candidate).
 LaunchShape apply_shape(int max_dim_up, int max_dim_dn, bool fp64, int n_groups);
 // Raise the dynamic shared-memory limit of the apply kernel for this shape

@@ -82,7 +82,7 @@ def _load():
                                      P, P, P],
         "ed_spectral_function": [P, I, I, D, D, P, I, P],
         "ed_device_bytes": [P, ctypes.POINTER(ctypes.c_int64)],
-        "ed_apply_config_info": [I] + [ctypes.POINTER(ctypes.c_int)] * 6,
+        "ed_apply_config_info": [I] + [ctypes.POINTER(ctypes.c_int)] * 7,
         "ed_set_apply_config": [I],
         "ed_set_krylov_tol": [P, D],
         "ed_set_workspace_limit": [P, ctypes.c_int64],
@@ -329,10 +329,10 @@ def ed_apply_config_count():
 
 
 def ed_apply_config_info(config):
-    """dict(fp64, rows_per_cta, pairs_per_thread, ctas_per_sm, split, tma)."""
-    v = [ctypes.c_int() for _ in range(6)]
+    """dict(fp64, rows_per_cta, pairs_per_thread, ctas_per_sm, split, tma, mv)."""
+    v = [ctypes.c_int() for _ in range(7)]
     _check(lib.ed_apply_config_info(config, *[ctypes.byref(x) for x in v]))
-    keys = ["fp64", "rows_per_cta", "pairs_per_thread", "ctas_per_sm", "split", "tma"]
+    keys = ["fp64", "rows_per_cta", "pairs_per_thread", "ctas_per_sm", "split", "tma", "mv"]
     return {k: x.value for k, x in zip(keys, v)}
 
 

@@ -36,13 +36,15 @@ def torus_case():
     return lat, pulse, psi0
 
 
-def test_torus_adaptive_c128_matches_oracle(ed_lib):
+def test_torus_adaptive_c128_matches_oracle(ed_lib, parity_log):
     torch = torch_cuda()
     lat, pulse, psi0 = torus_case()
     ref = oracle.propagate(lat, 6, 5, 8.0, psi0, pulse, 0.02, 10, 24, eps_tol=1e-8,
                            with_energy=True)
     psi, out = run(ed_lib, torch, lat, 6, 5, 8.0, psi0, pulse, 0.02, 10, 24, "c128", 1e-8,
                    energy=True)
+    parity_log("torus_adaptive_c128", state_rel_l2=rel_l2(psi, ref["psi"]),
+               docc_max_err=np.abs(out["docc"] - ref["docc"]).max())
     assert list(out["m_eff"]) == list(ref["m_eff"])
     assert max(ref["m_eff"]) < 24          # the exit is really taken
     assert rel_l2(psi, ref["psi"]) <= 1e-10
@@ -50,11 +52,14 @@ def test_torus_adaptive_c128_matches_oracle(ed_lib):
     assert np.abs(out["energy"] - ref["energy"]).max() <= 1e-10
 
 
-def test_torus_adaptive_c64_close_to_oracle(ed_lib):
+def test_torus_adaptive_c64_close_to_oracle(ed_lib, parity_log):
     torch = torch_cuda()
     lat, pulse, psi0 = torus_case()
     ref = oracle.propagate(lat, 6, 5, 8.0, psi0, pulse, 0.02, 10, 24, eps_tol=1e-6)
     psi, out = run(ed_lib, torch, lat, 6, 5, 8.0, psi0, pulse, 0.02, 10, 24, "c64", 1e-6)
+    parity_log("torus_adaptive_c64", state_rel_l2=rel_l2(psi, ref["psi"]),
+               docc_max_err=np.abs(out["docc"] - ref["docc"]).max(),
+               norm_drift=np.abs(out["norm2"] - out["norm2"][0]).max())
     assert np.abs(np.array(out["m_eff"]) - np.array(ref["m_eff"])).max() <= 1
     assert np.abs(out["docc"] - ref["docc"]).max() <= 1e-5
     assert np.abs(out["norm2"] - out["norm2"][0]).max() <= 1e-6

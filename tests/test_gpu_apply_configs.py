@@ -3,8 +3,9 @@ with ed_set_apply_config: the one-kernel variants, the split variants (a
 T_up pass, either column blocks staged in shared memory or row gathers one
 chunk of columns at a time, then a row pass for the diagonal and T_dn, with
 256, 512 or 1024 threads) and the variants whose T_up row chunks a producer
-warp stages by TMA, with all their rows-per-block, pairs-per-thread and
-occupancy settings.  The 924 x 792 sector gives the row-gather pass a
+warp stages by TMA, and the multi-vector variants (one row of several
+vectors of one sector per thread block), with all their rows-per-block,
+pairs-per-thread and occupancy settings.  The 924 x 792 sector gives the row-gather pass a
 ragged second chunk (256-pair chunks) and a partly valid second column-pair
 group (512-pair chunks).
 
@@ -122,3 +123,33 @@ def test_split_propagation_with_energy_matches_oracle(pinned, dtype):
             assert rel_l2(psi, ref["psi"]) <= 1e-4
             assert np.abs(out["docc"] - ref["docc"]).max() <= 1e-5
             assert np.abs(out["energy"] - ref["energy"]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_multi_vector_configs_with_partial_subgroups(pinned, dtype):
+    """Three vectors of one sector under each multi-vector configuration:
+    with two or four vectors per thread block the last subgroup is partly
+    filled (and with four, all three vectors share one, leaving a slot
+    empty).  Element by element against the oracle."""
+    torch = torch_cuda()
+    ed = pinned
+    lat, nu, nd, U = LATTICES["torus3x4"], 6, 5, 8.0
+    A = np.array([0.29, 0.13, 0.0])
+    h = ed.Hubbard(lat, nu, nd, U)
+    ed.ed_set_field(h.ctx, A)
+    v = synth.random_state(h.dim_up, h.dim_dn, seed=9, nvec=3).reshape(3, -1)
+    H = make_H(lat, nu, nd, U, A)
+    ref = np.stack([H @ v[k] for k in range(3)])
+    vd = to_dev(torch, v, dtype)
+    mv = [c for c in configs(ed, dtype) if ed.ed_apply_config_info(c)["mv"]]
+    assert mv
+    for cfg in mv:
+        ed.ed_set_apply_config(cfg)
+        wd = torch.full_like(vd, float("nan"))
+        ed.ed_apply_H(h.ctx, vd, wd, ed_dtype(ed, dtype), nvec=3)
+        torch.cuda.synchronize()
+        assert ed.ed_get_apply_config(h.ctx)[1] == cfg
+        w = from_dev(wd)
+        assert rel_l2(w, ref) <= TOL[dtype], cfg
+        assert max_el(w, ref) <= TOL_EL[dtype], (cfg, max_el(w, ref))
+    h.close()

@@ -43,13 +43,16 @@ def torus_reference():
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_torus_cfet4_matches_oracle(ed_lib, dtype):
+def test_torus_cfet4_matches_oracle(ed_lib, dtype, parity_log):
     torch = torch_cuda()
     lat, pulse, psi0 = torus_case()
     ref = torus_reference()
     psi, out = run(ed_lib, torch, lat, 6, 5, 8.0, psi0, pulse, 0.05, 8, 20, dtype,
                    energy=True)
     assert len(out["docc"]) == 9 and len(out["m_eff"]) == 8
+    parity_log(f"torus_cfet4_{dtype}", state_rel_l2=rel_l2(psi, ref["psi"]),
+               docc_max_err=np.abs(out["docc"] - ref["docc"]).max(),
+               energy_max_err=np.abs(out["energy"] - ref["energy"]).max())
     if dtype == "c128":
         assert rel_l2(psi, ref["psi"]) <= 1e-10
         assert np.abs(out["docc"] - ref["docc"]).max() <= 1e-10

@@ -23,13 +23,15 @@ def test_ground_state_dimer_closed_form(ed_lib, U, E0):
 @pytest.mark.parametrize("name,nu,nd,U", [("ring8", 4, 4, 8.0), ("ring6", 3, 3, 4.0),
                                           ("chain6_eps", 3, 2, 2.0),
                                           ("torus3x4", 6, 6, 8.0)])
-def test_ground_state_matches_oracle(ed_lib, name, nu, nd, U):
+def test_ground_state_matches_oracle(ed_lib, name, nu, nd, U, parity_log):
     torch = torch_cuda()
     lat = LATTICES[name]
     E0, psi_ref, gap = oracle.ground_state(lat, nu, nd, U)
     h = ed_lib.Hubbard(lat, nu, nd, U)
     psi = torch.zeros(h.D, dtype=torch.complex128, device="cuda")
     E, res = ed_lib.ed_ground_state(h.ctx, psi, tol=1e-11, max_iter=3000)
+    parity_log(f"ground_state_{name}", E0_rel_err=abs(E - E0) / max(1.0, abs(E0)),
+               residual=res)
     assert abs(E - E0) <= 1e-10 * max(1.0, abs(E0))
     assert res <= 1e-10 * max(1.0, abs(E0))
     p = from_dev(psi)
@@ -101,6 +103,59 @@ def test_fermion_ops_match_oracle(ed_lib):
     src.close()
 
 
+def _mv_configs(ed, fp64):
+    return [c for c in range(ed.ed_apply_config_count())
+            if ed.ed_apply_config_info(c)["mv"] and ed.ed_apply_config_info(c)["fp64"] == fp64]
+
+
+@pytest.fixture
+def pinned(ed_lib):
+    yield ed_lib
+    ed_lib.ed_set_apply_config(-1)
+
+
+def test_spectral_dimer_multi_vector_breakdown(pinned):
+    """The dimer batch (Krylov breakdown in every vector, at different j)
+    with each complex128 multi-vector configuration: the vectors of a
+    sector share thread blocks, and a vector that has stopped leaves the
+    others' alpha_j untouched."""
+    ed = pinned
+    torch_cuda()
+    U, t = 5.0, 1.0
+    lat = synth.dimer(t)
+    E0, psi0, _ = oracle.ground_state(lat, 1, 1, U)
+    ref = oracle.spectral_batch(lat, 1, 1, U, psi0, None, 0.05, 12, 8)
+    for cfg in _mv_configs(ed, 1):
+        ed.ed_set_apply_config(cfg)
+        h = ed.Hubbard(lat, 1, 1, U)
+        Gl, Gg = ed.ed_spectral_propagate(h.ctx, psi0, ed.ED_C128, None, 0.05, 12, 8, 2)
+        h.close()
+        assert np.abs(Gl - ref["G_less"]).max() <= 1e-11, cfg
+        assert np.abs(Gg - ref["G_greater"]).max() <= 1e-11, cfg
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_spectral_batch_multi_vector_configs(pinned, dtype):
+    """Ring 6 at half filling under a pulse, every multi-vector configuration
+    of the precision pinned: six vectors per sector (spin-down ones stored
+    transposed into the spin-up shape), all 24 traces against the oracle."""
+    ed = pinned
+    torch_cuda()
+    lat = LATTICES["ring6"]
+    E0, psi0, _ = oracle.ground_state(lat, 3, 3, 6.0)
+    pulse = {"A0": 0.8, "omega": 6.0, "sigma": 0.5, "t0": 0.4, "dir": (1.0, 0, 0)}
+    ref = oracle.spectral_batch(lat, 3, 3, 6.0, psi0, pulse, 0.04, 25, 12)
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    for cfg in _mv_configs(ed, 1 if dtype == "c128" else 0):
+        ed.ed_set_apply_config(cfg)
+        h = ed.Hubbard(lat, 3, 3, 6.0)
+        Gl, Gg = ed.ed_spectral_propagate(h.ctx, psi0, ed_dtype(ed, dtype), pulse,
+                                          0.04, 25, 12, 6)
+        h.close()
+        assert np.abs(Gl - ref["G_less"]).max() <= tol, cfg
+        assert np.abs(Gg - ref["G_greater"]).max() <= tol, cfg
+
+
 def test_spectral_dimer_closed_form(ed_lib):
     torch_cuda()
     U, t = 5.0, 1.0
@@ -124,7 +179,7 @@ def test_spectral_dimer_closed_form(ed_lib):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_spectral_batch_matches_oracle(ed_lib, dtype):
+def test_spectral_batch_matches_oracle(ed_lib, dtype, parity_log):
     """Ring 6 at half filling under a pulse: all 24 Green's-function traces."""
     torch_cuda()
     lat = LATTICES["ring6"]
@@ -135,6 +190,8 @@ def test_spectral_batch_matches_oracle(ed_lib, dtype):
     Gl, Gg = ed_lib.ed_spectral_propagate(h.ctx, psi0, ed_dtype(ed_lib, dtype), pulse,
                                           0.04, 25, 12, 6)
     tol = 1e-10 if dtype == "c128" else 1e-5
+    parity_log(f"ring6_spectral_{dtype}", G_less_max_err=np.abs(Gl - ref["G_less"]).max(),
+               G_greater_max_err=np.abs(Gg - ref["G_greater"]).max())
     assert np.abs(Gl - ref["G_less"]).max() <= tol
     assert np.abs(Gg - ref["G_greater"]).max() <= tol
     h.close()
@@ -163,7 +220,7 @@ def test_spectral_torus_sum_rules(ed_lib):
     h.close()
 
 
-def test_spectral_torus_one_site_matches_oracle(ed_lib):
+def test_spectral_torus_one_site_matches_oracle(ed_lib, parity_log):
     """3x4 torus (6,6) batch in complex64: the traces of site 5 (all four
     operators) over 3 steps against the oracle's float64 propagation of the
     same four vectors and psi."""
@@ -175,6 +232,9 @@ def test_spectral_torus_one_site_matches_oracle(ed_lib):
     ref = oracle.spectral_batch(lat, 6, 6, 8.0, psi0, pulse, 0.02, 3, 20, sites=[5])
     h = ed_lib.Hubbard(lat, 6, 6, 8.0)
     Gl, Gg = ed_lib.ed_spectral_propagate(h.ctx, psi0, ed_lib.ED_C64, pulse, 0.02, 3, 20, 12)
+    parity_log("torus_spectral_site5_c64",
+               G_less_max_err=np.abs(Gl[:, 5] - ref["G_less"][:, 5]).max(),
+               G_greater_max_err=np.abs(Gg[:, 5] - ref["G_greater"][:, 5]).max())
     for s in (0, 1):
         assert np.abs(Gl[:, 5, s] - ref["G_less"][:, 5, s]).max() <= 1e-5
         assert np.abs(Gg[:, 5, s] - ref["G_greater"][:, 5, s]).max() <= 1e-5

@@ -33,7 +33,7 @@ def sample_indices(rng, k):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_apply_ns16_half_filling_sampled(ed_lib, dtype):
+def test_apply_ns16_half_filling_sampled(ed_lib, dtype, parity_log):
     torch = torch_cuda()
     ed = ed_lib
     A = (0.31, 0.17, 0.0)
@@ -72,6 +72,7 @@ def test_apply_ns16_half_filling_sampled(ed_lib, dtype):
         o += nu + nd + 1
     scale = np.abs(ref).max()
     tol = 1e-13 if dtype == "c128" else 3e-6
+    parity_log(f"apply_ns16_sampled_{dtype}", max_el=np.abs(got - ref).max() / scale)
     assert np.abs(got - ref).max() <= tol * scale
     h.close()
 
@@ -83,7 +84,7 @@ def slater_amplitudes(u_up, u_dn, occ_targets_up, occ_targets_dn, occ0_up, occ0_
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_free_fermion_propagation_ns16_is_slater(ed_lib, dtype):
+def test_free_fermion_propagation_ns16_is_slater(ed_lib, dtype, parity_log):
     torch = torch_cuda()
     ed = ed_lib
     pulse = {"A0": 0.9, "omega": 5.0, "sigma": 0.6, "t0": 0.1, "dir": (1.0, 0.7, 0.0)}
@@ -114,6 +115,7 @@ def test_free_fermion_propagation_ns16_is_slater(ed_lib, dtype):
     ref = slater_amplitudes(u1, u1, [occ(words[u]) for u in us], [occ(words[d]) for d in ds],
                             occ(words[u0]), occ(words[d0]))
     tol = 1e-10 if dtype == "c128" else 2e-5
+    parity_log(f"ns16_slater_{dtype}", amplitude_max_err=np.abs(got - ref).max())
     assert np.abs(ref[-200:]).max() > 1e-3        # the sample sees real amplitudes
     assert np.abs(got - ref).max() <= tol
     h.close()

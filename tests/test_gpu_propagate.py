@@ -35,7 +35,7 @@ def run_gpu(ed, torch, lat, nu, nd, U, psi0, pulse, dt, n, m, dtype, energy=Fals
     return psi, out
 
 
-def test_ring8_full_trajectory_c128(ed_lib):
+def test_ring8_full_trajectory_c128(ed_lib, parity_log):
     """Ns=8 ring, (4,4), U=8, 500 steps dt=0.02, m=12, pulse A0=0.5 Omega=8
     sigma=2 t0=5: the whole trajectory against the oracle."""
     torch = torch_cuda()
@@ -46,6 +46,10 @@ def test_ring8_full_trajectory_c128(ed_lib):
                            with_energy=True)
     psi, out = run_gpu(ed_lib, torch, lat, 4, 4, 8.0, psi0, w["pulse_params"], 0.02,
                        500, 12, "c128", energy=True)
+    parity_log("ring8_500_c128", state_rel_l2=rel_l2(psi, ref["psi"]),
+               docc_max_err=np.abs(out["docc"] - ref["docc"]).max(),
+               norm2_max_err=np.abs(out["norm2"] - ref["norm2"]).max(),
+               energy_max_err=np.abs(out["energy"] - ref["energy"]).max())
     assert rel_l2(psi, ref["psi"]) <= 1e-10
     assert np.abs(out["docc"] - ref["docc"]).max() <= 1e-10
     assert np.abs(out["norm2"] - ref["norm2"]).max() <= 1e-10
@@ -54,7 +58,7 @@ def test_ring8_full_trajectory_c128(ed_lib):
     assert np.ptp(ref["docc"]) > 1e-3  # the pulse really excites the system
 
 
-def test_ring8_trajectory_c64(ed_lib):
+def test_ring8_trajectory_c64(ed_lib, parity_log):
     torch = torch_cuda()
     w = synth.workload("ring8")
     lat = LATTICES["ring8"]
@@ -62,13 +66,16 @@ def test_ring8_trajectory_c64(ed_lib):
     ref = oracle.propagate(lat, 4, 4, 8.0, psi0, w["pulse_params"], 0.02, 500, 12)
     psi, out = run_gpu(ed_lib, torch, lat, 4, 4, 8.0, psi0, w["pulse_params"], 0.02,
                        500, 12, "c64")
+    parity_log("ring8_500_c64", state_rel_l2=rel_l2(psi, ref["psi"]),
+               docc_max_err=np.abs(out["docc"] - ref["docc"]).max(),
+               norm_drift=np.abs(out["norm2"] - out["norm2"][0]).max())
     assert np.abs(out["docc"] - ref["docc"]).max() <= 1e-5
     assert np.abs(out["norm2"] - out["norm2"][0]).max() <= 1e-6
     assert rel_l2(psi, ref["psi"]) <= 1e-4
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_torus_prefix(ed_lib, dtype):
+def test_torus_prefix(ed_lib, dtype, parity_log):
     """Ns=12 3x4 torus, (6,6), m=20, dt=0.02: first 12 steps (D = 853,776)."""
     torch = torch_cuda()
     w = synth.workload("torus3x4")
@@ -78,6 +85,9 @@ def test_torus_prefix(ed_lib, dtype):
     pulse = dict(w["pulse_params"], t0=0.1)
     ref = oracle.propagate(lat, 6, 6, 8.0, psi0, pulse, 0.02, 12, 20)
     psi, out = run_gpu(ed_lib, torch, lat, 6, 6, 8.0, psi0, pulse, 0.02, 12, 20, dtype)
+    parity_log(f"torus_prefix12_{dtype}", state_rel_l2=rel_l2(psi, ref["psi"]),
+               docc_max_err=np.abs(out["docc"] - ref["docc"]).max(),
+               norm_drift=np.abs(out["norm2"] - out["norm2"][0]).max())
     if dtype == "c128":
         assert rel_l2(psi, ref["psi"]) <= 1e-10
         assert np.abs(out["docc"] - ref["docc"]).max() <= 1e-10
@@ -87,7 +97,7 @@ def test_torus_prefix(ed_lib, dtype):
         assert rel_l2(psi, ref["psi"]) <= 1e-5
 
 
-def test_ladder_full_size_one_step(ed_lib):
+def test_ladder_full_size_one_step(ed_lib, parity_log):
     """Ns=14 ladder, (7,7), m=30: one full midpoint step at t=10 (pulse
     maximum region) in both dtypes against the oracle, every element."""
     torch = torch_cuda()
@@ -103,6 +113,8 @@ def test_ladder_full_size_one_step(ed_lib):
         out = ed_lib.ed_propagate(h.ctx, xd, ed_dtype(ed_lib, dtype), w["pulse_params"],
                                   t_start, 0.02, 1, 30)
         torch.cuda.synchronize()
+        parity_log(f"ladder_one_step_{dtype}", state_rel_l2=rel_l2(from_dev(xd), ref["psi"]),
+                   docc_err=abs(out["docc"][1] - ref["docc"][1]))
         assert rel_l2(from_dev(xd), ref["psi"]) <= tol, dtype
         assert abs(out["docc"][1] - ref["docc"][1]) <= (1e-10 if dtype == "c128" else 1e-6)
         h.close()

@@ -188,8 +188,11 @@ def test_apply_config_table_and_switch(ed):
         i = ed.ed_apply_config_info(c)
         assert i["fp64"] in (0, 1) and i["split"] in (0, 1) and i["tma"] in (0, 1)
         assert i["rows_per_cta"] >= 1 and i["pairs_per_thread"] >= 1 and i["ctas_per_sm"] >= 1
+        assert i["mv"] in (0, 1) and not (i["mv"] and (i["split"] or i["tma"]))
         seen.add((i["fp64"], i["split"]))
-    assert seen == {(0, 0), (0, 1), (1, 0), (1, 1)}
+        if i["mv"]:
+            seen.add(("mv", i["fp64"]))
+    assert seen == {(0, 0), (0, 1), (1, 0), (1, 1), ("mv", 0), ("mv", 1)}
     for bad in (-2, n):
         with pytest.raises(ed.EDError) as e:
             ed.ed_set_apply_config(bad)
