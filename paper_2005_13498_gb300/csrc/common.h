@@ -65,7 +65,6 @@ struct SectorDev {
 // Lanczos vector of Algorithm 6.  x_1 is the propagated state itself.
 struct LanczosState {
   double alpha[kMaxKrylov + 2];
-  double alpha_im[kMaxKrylov + 2];  // Im <v_j, w>: subtracted with alpha, not in T_m
   double beta[kMaxKrylov + 2];
   double inv_scale[kMaxKrylov + 2];
   double comb_re[kMaxKrylov + 2];   // combine coefficients: psi = sum comb_j x_j

@@ -563,16 +563,14 @@ __device__ __forceinline__ void tup_chunk_mv(const SectorDev& sd,
     tup_chunk_c128<NR, PP, KA, NT>(sd, xr, coefS, urow, nrows, pc, npairs, dim_dn, acc);
 }
 
-// The reduced <x_j, w> of one vector: j >= 1, h_jj = <v_j, w> of Algorithm 6,
-// whose real part is alpha_j (H is Hermitian; the update subtracts the whole
-// complex h_jj v_j); j == -1, the energy <x_1, H x_1> / Ns at this step.
+// The reduced Re<x_j, w> of one vector: j >= 1, alpha_j = Re h_jj of
+// Algorithm 6 (H is Hermitian: the imaginary part of <v_j, w> is rounding);
+// j == -1, the energy <x_1, H x_1> / Ns at this step.
 __device__ __forceinline__ void apply_dot_result(LanczosState* st, double* out_energy, int j,
-                                                 double re, double im, int Ns) {
+                                                 double re, int Ns) {
   if (j >= 1) {
-    const double sj = st->inv_scale[j];
-    st->alpha[j] = re * sj;
-    st->alpha_im[j] = im * sj;
-    if (!isfinite(re) || !isfinite(im)) {
+    st->alpha[j] = re * st->inv_scale[j];
+    if (!isfinite(re)) {
       st->status = 7; st->stopped = 1; st->m_eff = j > 1 ? j - 1 : 1;
     }
   } else {
@@ -620,7 +618,7 @@ k_apply(BatchArgs a, int j) {
   constexpr uint32_t kSlotBytes = (uint32_t)(T * PP * 2 * sizeof(C));   // one chunk of a row
   static_assert(!(TMA && SPLIT), "the TMA ring serves the one-kernel T_up");
   static_assert(!MV || (!TMA && !SPLIT), "multi-vector blocks use the one-kernel gathers");
-  static_assert((NT / 32 + (TMA ? 1 : 0)) * (MV ? 2 * NR : 2) <= 64, "reduction scratch");
+  static_assert((NT / 32 + (TMA ? 1 : 0)) * (MV ? NR : 1) <= 64, "reduction scratch");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
   __shared__ int flag;
@@ -757,10 +755,10 @@ k_apply(BatchArgs a, int j) {
   }
   __syncthreads();
 
-  double dot_d = 0.0, dot_i = 0.0;
-  double dd_r[NR], di_r[NR];   // MV: per vector
+  double dot_d = 0.0;
+  double dd_r[NR];   // MV: per vector
 #pragma unroll
-  for (int r = 0; r < NR; ++r) { dd_r[r] = 0.0; di_r[r] = 0.0; }
+  for (int r = 0; r < NR; ++r) dd_r[r] = 0.0;
   uint32_t cidx = 0;     // T_up entries consumed so far (TMA ring position)
   if (TMA && tid >= T) {
     // ---- producer warp (TMA configurations): one elected lane issues the
@@ -996,10 +994,10 @@ k_apply(BatchArgs a, int j) {
         tup_chunk<R, NR, PP, 1, VEC, NT>(sd, x, coefS, coefQ, urow, nrows, pc, npairs, dim_dn, acc);
     }
     // ---- epilogue: previous-vector loads first, then scale, subtract, store
-    R dot_acc = (R)0, dot_im = (R)0;
-    R dacc_r[NR], dim_r[NR];
+    R dot_acc = (R)0;
+    R dacc_r[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) { dacc_r[r] = (R)0; dim_r[r] = (R)0; }
+    for (int r = 0; r < NR; ++r) dacc_r[r] = (R)0;
     {
     C pv[NR][2 * PP];
 #pragma unroll
@@ -1045,47 +1043,37 @@ k_apply(BatchArgs a, int j) {
             const R dre = xa[r].x * o0.x + xa[r].y * o0.y + xb[r].x * o1.x + xb[r].y * o1.y;
             if constexpr (MV) dacc_r[r] += dre;
             else dot_acc += dre;
-            // Im h_jj: float32 only (in float64 it is rounding, and the
-            // float64 apply is bound by its FP64 operations)
-            if constexpr (sizeof(R) == 4) {
-              const R dim = xa[r].x * o0.y - xa[r].y * o0.x + xb[r].x * o1.y - xb[r].y * o1.x;
-              if constexpr (MV) dim_r[r] += dim;
-              else dot_im += dim;
-            }
           }
         }
       }
     }
     }
     dot_d += (double)dot_acc;
-    dot_i += (double)dot_im;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) { dd_r[r] += (double)dacc_r[r]; di_r[r] += (double)dim_r[r]; }
+    for (int r = 0; r < NR; ++r) dd_r[r] += (double)dacc_r[r];
   }
   if constexpr (TMA) {
     if (tma_err && tid == 0) st->status = kStatusTimeout;
   }
   if (j == 0) return;
   if constexpr (MV) {
-    constexpr int KR = 2 * NR;   // <x_j, w> of each vector of the subgroup
+    constexpr int KR = NR;   // Re<x_j, w> of each vector of the subgroup
     double v[KR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) { v[2 * r] = dd_r[r]; v[2 * r + 1] = di_r[r]; }
+    for (int r = 0; r < NR; ++r) v[r] = dd_r[r];
     if (reduce_last_block<KR>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
                               a.partials, a.counters + ab.vec, red, &flag)) {
       if (tid == 0)
 #pragma unroll
         for (int r = 0; r < NR; ++r)
           if (!rdone[r])
-            apply_dot_result(a.st + ab.row[r], a.vec[ab.row[r]].out_energy, j, v[2 * r],
-                             v[2 * r + 1], a.Ns);
+            apply_dot_result(a.st + ab.row[r], a.vec[ab.row[r]].out_energy, j, v[r], a.Ns);
     }
   } else {
-    constexpr int KR = 2;   // <x_j, w>: real and imaginary part
-    double v[KR] = {dot_d, dot_i};
-    if (reduce_last_block<KR>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
-                              a.partials, a.counters + ab.vec, red, &flag)) {
-      if (tid == 0) apply_dot_result(st, vd.out_energy, j, v[0], v[1], a.Ns);
+    double v[1] = {dot_d};   // Re<x_j, w>
+    if (reduce_last_block<1>(v, blockIdx.x, vd.apply_begin, vd.apply_end,
+                             a.partials, a.counters + ab.vec, red, &flag)) {
+      if (tid == 0) apply_dot_result(st, vd.out_energy, j, v[0], a.Ns);
     }
   }
 }
@@ -1352,8 +1340,7 @@ k_apply_up(BatchArgs a, int j) {
 }
 
 // ------------------------------------------------------------------ update
-// x_{j+1} = w - h_jj s_j x_j (h_jj = alpha_j + i alpha_im_j) ;  beta_j =
-// |x_{j+1}| ;  breakdown test.
+// x_{j+1} = w - alpha_j s_j x_j ;  beta_j = |x_{j+1}| ;  breakdown test.
 // PAIR: complex64 vectors of even length are processed two elements per
 // 16-byte access (chunk boundaries are multiples of 256 elements).
 template <typename R, bool PAIR>
@@ -1365,13 +1352,7 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
   const VecDev vd = a.vec[eb.vec];
   LanczosState* st = a.st + eb.vec;
   if (lanczos_done(st, j)) return;
-  // h_jj s_j with h_jj = <v_j, w> complex (Algorithm 6 subtracts h_jj v_j):
-  // its imaginary part is of the order of the rounding of H v_j, but for a
-  // state near an eigenvector (beta_j small) dropping it leaves a component
-  // i Im(h_jj) v_j in x_{j+1} that, scaled by 1/beta_j, makes the propagated
-  // norm drift by ~tau Im(h_jj) per step in float32
   const R as = (R)(st->alpha[j] * st->inv_scale[j]);
-  const R ai = (R)(st->alpha_im[j] * st->inv_scale[j]);
   double nrm_d = 0.0;
   const void* pw = vd.w;
   const void* px = xptr(vd, j, sizeof(C));
@@ -1382,7 +1363,7 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
     const float4* x = static_cast<const float4*>(px);
     float4* xn = static_cast<float4*>(const_cast<void*>(pxn));
     const int64_t b2 = eb.begin >> 1, e2 = eb.end >> 1;
-    const float af = (float)as, ag = (float)ai;
+    const float af = (float)as;
     const int bd = blockDim.x;
     // four pairs per thread and iteration: eight 16-byte loads in flight.
     // w and x_j are not read again before the combine at the end of the
@@ -1401,11 +1382,10 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
       for (int q = 0; q < 4; ++q) {
         const int64_t i = i0 + (int64_t)q * bd;
         float4 o;
-        // w - (af + i ag) x for the two elements (x, y) and (z, w)
-        o.x = wv[q].x - af * xv[q].x + ag * xv[q].y;
-        o.y = wv[q].y - af * xv[q].y - ag * xv[q].x;
-        o.z = wv[q].z - af * xv[q].z + ag * xv[q].w;
-        o.w = wv[q].w - af * xv[q].w - ag * xv[q].z;
+        o.x = wv[q].x - af * xv[q].x;
+        o.y = wv[q].y - af * xv[q].y;
+        o.z = wv[q].z - af * xv[q].z;
+        o.w = wv[q].w - af * xv[q].w;
         if (i < e2) xn[i] = o;
         nrm += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
       }
@@ -1421,8 +1401,8 @@ __global__ void __launch_bounds__(256) k_update(BatchArgs a, int j) {
     for (int64_t i = eb.begin + threadIdx.x; i < eb.end; i += blockDim.x) {
       const C wv = __ldcs(w + i), xv = __ldcs(x + i);
       C o;
-      o.x = wv.x - as * xv.x + ai * xv.y;
-      o.y = wv.y - as * xv.y - ai * xv.x;
+      o.x = wv.x - as * xv.x;
+      o.y = wv.y - as * xv.y;
       xn[i] = o;
       nrm += o.x * o.x + o.y * o.y;
       if (++cnt == 8) { nrm_d += (double)nrm; nrm = (R)0; cnt = 0; }

@@ -225,7 +225,7 @@ extern "C" int ed_probe_ceilings(ed_ceilings* out) {
     rc = time_ms(t, [&] { k_ffma2<<<grid, kThreads>>>(iters, 0.999f, 0.001f, fsink); }, &ms);
     if (rc) { cudaFree(sink); return rc; }
     out->fp32x2_fma_tflops = 4.0 * 8 * iters * (double)grid * kThreads / (ms * 1e-3) / 1e12;
-    const int diters = 64;
+    const int diters = 1024;   // long enough that launch and tail do not count
     rc = time_ms(t, [&] { k_dfma<<<grid, kThreads>>>(diters, 0.999, 0.001, dsink); }, &ms);
     if (rc) { cudaFree(sink); return rc; }
     out->fp64_fma_tflops = 2.0 * 8 * diters * (double)grid * kThreads / (ms * 1e-3) / 1e12;
