@@ -311,6 +311,38 @@ ed_status ed_set_krylov_tol(ed_ctx* ctx, double tol);
  * the step's two Krylov steps.  ED_ERR_ARG for an unknown scheme.            */
 ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme);
 
+/* The hopping coefficients a propagation of this context uses (host
+ * computation, no GPU work): for every Krylov sub-step s of n_steps time
+ * steps from t_start (n_sub = n_steps sub-steps for ED_MIDPOINT, at the
+ * midpoints t_start + (n + 1/2) dt of Eq. (32); n_sub = 2 n_steps for
+ * ED_CFET4, in the order they act) and every bond b,
+ * coef[2 (s n_bonds + b)] + i coef[.. + 1] is the matrix element of the hop
+ * p_b -> q_b, -t_b exp(-i A(t) . d_b) with the Peierls phase of Eqs. (1)
+ * and (3) (for CFET4 the combination of its two field times that the
+ * sub-step applies).  The reverse hop carries the conjugate.  *n_sub and
+ * *tau (both nullable) receive the number of sub-steps and the sub-step
+ * length the Krylov exponential uses with them (dt, or dt / 2 for CFET4).
+ * coef is a host buffer of 2 n_sub n_bonds doubles, or NULL to query n_sub
+ * only.  pulse may be NULL (A = 0).  ED_ERR_STATE before ed_set_lattice;
+ * ED_ERR_ARG for n_steps < 1, a non-finite t_start or dt, or invalid pulse
+ * parameters.                                                               */
+ed_status ed_step_coefficients(ed_ctx* ctx, const ed_pulse* pulse, double t_start,
+                               double dt, int n_steps, double* coef, int* n_sub,
+                               double* tau);
+
+/* The small exponential of Algorithm 6 on the current GPU: for each of
+ * `batch` real symmetric tridiagonal matrices T_b of order n (1 <= n <= 64;
+ * diagonal alpha[b n .. b n + n), off-diagonal beta[b (n-1) ..]),
+ * y[b n + i] = (exp(-i tau T_b) e_1)_i as (re, im) pairs, computed by the
+ * float64 device routine the propagation's exponential kernel runs (shifted
+ * Taylor series with sub-steps).  Host buffers (alpha: batch n doubles, beta:
+ * batch (n - 1), may be NULL for n = 1; y: 2 batch n doubles); the call
+ * copies them to and from the device and returns when y is written.
+ * ED_ERR_ARG for sizes out of range, NULL buffers or non-finite inputs;
+ * ED_ERR_CUDA if the device work fails.                                     */
+ed_status ed_tridiag_expm(int batch, int n, const double* alpha, const double* beta,
+                          double tau, double* y);
+
 /* Kernel configurations of H v (the matrix-vector product inside Lanczos,
  * Eq. (18) applied as T_up (x) 1 + 1 (x) T_dn + diagonal, Sec. 3.2).  Each
  * entry of the library's table fixes the precision, the rows of Psi one

@@ -394,6 +394,56 @@ ed_status ed_set_integrator(ed_ctx* ctx, ed_integrator scheme) {
   return ED_OK;
 }
 
+ed_status ed_step_coefficients(ed_ctx* ctx, const ed_pulse* pulse, double t_start, double dt,
+                               int n_steps, double* coef, int* n_sub_out, double* tau) {
+  if (!ctx) return fail(nullptr, ED_ERR_ARG, "ctx is NULL");
+  if (!ctx->lattice_set) return fail(ctx, ED_ERR_STATE, "ed_set_lattice has not been called");
+  if (n_steps < 1 || !std::isfinite(t_start) || !std::isfinite(dt))
+    return fail(ctx, ED_ERR_ARG, "n_steps >= 1 and finite t_start, dt required");
+  if (ed_status e = check_pulse(ctx, pulse)) return e;
+  const SubSteps sub = integrator_substeps(ctx, pulse, t_start, dt, n_steps);
+  const int ng = 2 * ctx->lat.n_classes, nb = ctx->lat.n_bonds;
+  const int n_sub = n_steps * sub.per_step;
+  if (n_sub_out) *n_sub_out = n_sub;
+  if (tau) *tau = sub.tau;
+  if (!coef) return ED_OK;
+  for (int s = 0; s < n_sub; ++s)
+    for (int b = 0; b < nb; ++b) {
+      // group 2 c: the hop p -> q of bond class c
+      const size_t g = ((size_t)s * ng + 2 * (size_t)ctx->lat.bond_class[b]) * 2;
+      coef[2 * ((size_t)s * nb + b)] = sub.coefs[g];
+      coef[2 * ((size_t)s * nb + b) + 1] = sub.coefs[g + 1];
+    }
+  return ED_OK;
+}
+
+ed_status ed_tridiag_expm(int batch, int n, const double* alpha, const double* beta,
+                          double tau, double* y) {
+  if (batch < 1 || n < 1 || n > kMaxKrylov)
+    return fail(nullptr, ED_ERR_ARG, "batch >= 1 and 1 <= n <= 64 required");
+  if (!alpha || !y || (n > 1 && !beta)) return fail(nullptr, ED_ERR_ARG, "NULL argument");
+  if (!std::isfinite(tau)) return fail(nullptr, ED_ERR_ARG, "tau is not finite");
+  const size_t na = (size_t)batch * n, nbeta = (size_t)batch * (n - 1);
+  for (size_t i = 0; i < na; ++i)
+    if (!std::isfinite(alpha[i])) return fail(nullptr, ED_ERR_ARG, "alpha is not finite");
+  for (size_t i = 0; i < nbeta; ++i)
+    if (!std::isfinite(beta[i])) return fail(nullptr, ED_ERR_ARG, "beta is not finite");
+  DevMem da, db, dy;
+  cudaError_t e = da.alloc(na * sizeof(double));
+  if (e == cudaSuccess) e = db.alloc(std::max<size_t>(1, nbeta) * sizeof(double));
+  if (e == cudaSuccess) e = dy.alloc(2 * na * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(da.p, alpha, na * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nbeta)
+    e = cudaMemcpy(db.p, beta, nbeta * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = launch_tridiag_expm(static_cast<const double*>(da.p), static_cast<const double*>(db.p),
+                            n, tau, static_cast<double*>(dy.p), batch, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(y, dy.p, 2 * na * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "ed_tridiag_expm");
+  return ED_OK;
+}
+
 int ed_apply_config_count(void) { return apply_config_count(); }
 
 ed_status ed_apply_config_info(int config, int* fp64, int* rows_per_cta,

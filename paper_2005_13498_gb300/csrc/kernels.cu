@@ -1512,6 +1512,25 @@ __device__ void tridiag_expm_e1(const double* al, const double* be, int n,
   __syncwarp();
 }
 
+// ed_tridiag_expm: one warp per problem b runs tridiag_expm_e1 on
+// alpha[b n ..], beta[b (n-1) ..] (n <= 64) and writes y = exp(-i tau T) e_1
+// to y[b n ..] as (re, im) pairs.
+__global__ void __launch_bounds__(32) k_tridiag_expm(const double* alpha, const double* beta,
+                                                     int n, double tau, double* y) {
+  __shared__ double al[64], be[64], yre[64], yim[64], tre[64], tim[64];
+  const size_t b = blockIdx.x;
+  for (int i = threadIdx.x; i < 64; i += 32) {
+    al[i] = i < n ? alpha[b * n + i] : 0.0;
+    be[i] = i < n - 1 ? beta[b * (n - 1) + i] : 0.0;
+  }
+  __syncwarp();
+  tridiag_expm_e1(al, be, n, tau, yre, yim, tre, tim);
+  for (int i = threadIdx.x; i < n; i += 32) {
+    y[2 * (b * n + i)] = yre[i];
+    y[2 * (b * n + i) + 1] = yim[i];
+  }
+}
+
 // Two warps per vector: warp 0 computes y = exp(-i tau T_n) e_1, warp 1 the
 // one-smaller y^(n-1) that the a-posteriori delta compares with, at the same
 // time (each a chain of float64 warp operations).
@@ -2374,6 +2393,13 @@ cudaError_t launch_conv_check(const BatchArgs& a, int j, cudaStream_t s) {
 
 cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s) {
   k_expm<<<a.nvec, 64, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_expm(const double* alpha, const double* beta, int n, double tau,
+                                double* y, int batch, cudaStream_t s) {
+  if (n < 1 || n > kMaxKrylov || batch < 1) return cudaErrorInvalidValue;
+  k_tridiag_expm<<<batch, 32, 0, s>>>(alpha, beta, n, tau, y);
   return cudaGetLastError();
 }
 

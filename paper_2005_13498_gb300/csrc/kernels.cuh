@@ -140,6 +140,11 @@ cudaError_t launch_apply(bool fp64, const BatchArgs& a, int n_apply_blocks,
 cudaError_t launch_update(bool fp64, const BatchArgs& a, int n_ew_blocks, int j,
                           cudaStream_t s);
 cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s);
+// y[b] = exp(-i tau T_b) e_1 for batch real symmetric tridiagonals T_b of
+// order n <= kMaxKrylov (alpha: batch x n, beta: batch x (n - 1), y: batch x n
+// complex as (re, im) pairs), device pointers; the routine of k_expm.
+cudaError_t launch_tridiag_expm(const double* alpha, const double* beta, int n, double tau,
+                                double* y, int batch, cudaStream_t s);
 // Adaptive exit check after Lanczos step j (vectors with eps_tol > 0).
 cudaError_t launch_conv_check(const BatchArgs& a, int j, cudaStream_t s);
 cudaError_t launch_combine(bool fp64, const BatchArgs& a, int n_ew_blocks,

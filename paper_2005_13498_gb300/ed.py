@@ -88,6 +88,9 @@ def _load():
         "ed_set_workspace_limit": [P, ctypes.c_int64],
         "ed_set_wait_fault": [I, ctypes.c_int64],
         "ed_set_integrator": [P, I],
+        "ed_step_coefficients": [P, ctypes.POINTER(ed_pulse), D, D, I, P,
+                                 ctypes.POINTER(ctypes.c_int), P],
+        "ed_tridiag_expm": [I, I, P, P, D, P],
         "ed_get_apply_config": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "ed_destroy": [P],
     }
@@ -322,6 +325,32 @@ def ed_set_integrator(ctx, scheme):
     if isinstance(scheme, str):
         scheme = {"midpoint": ED_MIDPOINT, "cfet4": ED_CFET4}[scheme]
     _check(lib.ed_set_integrator(ctx, int(scheme)), ctx)
+
+
+def ed_step_coefficients(ctx, n_bonds, pulse, t_start, dt, n_steps):
+    """(coef[n_sub, n_bonds] complex: the hop p_b -> q_b of every Krylov
+    sub-step, tau of a sub-step)."""
+    pp = make_pulse(pulse)
+    pref = ctypes.byref(pp) if pp is not None else None
+    n_sub, tau = ctypes.c_int(), ctypes.c_double()
+    _check(lib.ed_step_coefficients(ctx, pref, float(t_start), float(dt), int(n_steps), None,
+                                    ctypes.byref(n_sub), ctypes.byref(tau)), ctx)
+    out = np.zeros((n_sub.value, n_bonds), dtype=np.complex128)
+    _check(lib.ed_step_coefficients(ctx, pref, float(t_start), float(dt), int(n_steps),
+                                    out.ctypes.data, None, None), ctx)
+    return out, tau.value
+
+
+def ed_tridiag_expm(alpha, beta, tau):
+    """y = exp(-i tau T) e_1 for a batch of tridiagonals: alpha [batch, n],
+    beta [batch, n-1] (float64) -> y [batch, n] complex128, on the GPU."""
+    a = np.ascontiguousarray(np.atleast_2d(alpha), dtype=np.float64)
+    batch, n = a.shape
+    b = np.ascontiguousarray(np.reshape(beta, (batch, max(0, n - 1))), dtype=np.float64)
+    y = np.zeros((batch, n), dtype=np.complex128)
+    _check(lib.ed_tridiag_expm(batch, n, a.ctypes.data, b.ctypes.data if n > 1 else None,
+                               float(tau), y.ctypes.data))
+    return y
 
 
 def ed_apply_config_count():

@@ -283,3 +283,77 @@ def test_new_control_calls_validate_arguments(ed):
     assert e.value.status == 1
     ed.ed_set_wait_fault(-1, 0)
     ed.ed_destroy(ctx)
+
+
+STEP_CASES = [
+    ("ring8", synth.lattice_from_name("ring8"), synth.workload("ring8")["pulse_params"]),
+    ("torus3x4", synth.lattice_from_name("torus3x4"), synth.workload("torus3x4")["pulse_params"]),
+    ("ladder2x7", synth.lattice_from_name("ladder2x7"),
+     synth.workload("ladder2x7")["pulse_params"]),
+    ("complete6", synth.complete_graph(6, seed=4),
+     {"A0": 0.9, "omega": 3.0, "sigma": 0.7, "t0": 0.3, "dir": (0.3, -1.0, 0.5)}),
+    ("triangle-cos-phase", synth.triangle(),
+     {"A0": 0.8, "omega": 4.0, "sigma": 1.0, "t0": 0.5, "dir": (1.0, 0.0, 0.0),
+      "shape": "cos_phase", "b": 0.3}),
+]
+
+
+@pytest.mark.parametrize("name,lat,pulse", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+def test_step_coefficients_match_oracle(ed, name, lat, pulse):
+    """The per-step hopping coefficients (S1) the propagation uploads, per
+    bond, against the oracle's one-electron Hamiltonian h[q, p] at the
+    midpoints (Eq. (32)) and, for CFET4, its two-field combinations: the
+    sub-step tau times the coefficient equals dt (a2 h(A1) + a1 h(A2)), then
+    dt (a1 h(A1) + a2 h(A2))."""
+    ctx = ed.ed_build_basis(lat["Ns"], 1, 1)
+    ed.ed_set_lattice(ctx, lat, 2.0)
+    p, q = np.asarray(lat["p"]), np.asarray(lat["q"])
+    nb = len(p)
+    t0, dt, n = 0.13, 0.05, 7
+    coef, tau = ed.ed_step_coefficients(ctx, nb, pulse, t0, dt, n)
+    assert coef.shape == (n, nb) and tau == dt
+    for s in range(n):
+        h = oracle.single_particle_matrix(lat, oracle.pulse_A(t0 + (s + 0.5) * dt, pulse))
+        assert np.abs(coef[s] - h[q, p]).max() <= 1e-15
+    ed.ed_set_integrator(ctx, "cfet4")
+    coef, tau = ed.ed_step_coefficients(ctx, nb, pulse, t0, dt, n)
+    assert coef.shape == (2 * n, nb) and abs(tau - dt / 2) <= 1e-18
+    (c1, c2), (a1, a2) = oracle.krylov.CFET4_C, oracle.krylov.CFET4_A
+    for s in range(n):
+        h1 = oracle.single_particle_matrix(lat, oracle.pulse_A(t0 + (s + c1) * dt, pulse))
+        h2 = oracle.single_particle_matrix(lat, oracle.pulse_A(t0 + (s + c2) * dt, pulse))
+        first, second = a2 * h1 + a1 * h2, a1 * h1 + a2 * h2
+        assert np.abs(tau * coef[2 * s] - dt * first[q, p]).max() <= 1e-15
+        assert np.abs(tau * coef[2 * s + 1] - dt * second[q, p]).max() <= 1e-15
+    # no pulse: the bare hoppings -t_b
+    ed.ed_set_integrator(ctx, "midpoint")
+    coef, _ = ed.ed_step_coefficients(ctx, nb, None, 0.0, dt, 2)
+    assert np.array_equal(coef, np.tile(-np.asarray(lat["t"], dtype=np.complex128), (2, 1)))
+    ed.ed_destroy(ctx)
+
+
+def test_step_coefficients_and_tridiag_expm_validate_arguments(ed):
+    ctx = ed.ed_build_basis(4, 2, 2)
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_step_coefficients(ctx, 4, None, 0.0, 0.02, 3)
+    assert e.value.status == 6          # ED_ERR_STATE: no lattice yet
+    ed.ed_set_lattice(ctx, synth.ring(4), 2.0)
+    for n_steps, dt in ((0, 0.02), (3, float("nan"))):
+        with pytest.raises(ed.EDError) as e:
+            ed.ed_step_coefficients(ctx, 4, None, 0.0, dt, n_steps)
+        assert e.value.status == 1
+    bad_pulse = {"A0": 1.0, "omega": 1.0, "sigma": 0.0, "t0": 0.0, "dir": (1.0, 0, 0)}
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_step_coefficients(ctx, 4, bad_pulse, 0.0, 0.02, 3)
+    assert e.value.status == 1
+    ed.ed_destroy(ctx)
+    # the exponential checks its arguments before any device work
+    for alpha, beta in ((np.zeros((1, 65)), np.zeros((1, 64))),
+                        (np.array([[1.0, np.nan]]), np.array([[0.5]])),
+                        (np.array([[1.0, 2.0]]), np.array([[np.inf]]))):
+        with pytest.raises(ed.EDError) as e:
+            ed.ed_tridiag_expm(alpha, beta, 0.1)
+        assert e.value.status == 1
+    with pytest.raises(ed.EDError) as e:
+        ed.ed_tridiag_expm(np.array([[1.0]]), np.zeros((1, 0)), float("inf"))
+    assert e.value.status == 1
