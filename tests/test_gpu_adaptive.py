@@ -97,3 +97,29 @@ def test_spectral_adaptive_matches_oracle(ed_lib):
     h.close()
     assert np.abs(Gl - ref["G_less"]).max() <= 1e-9
     assert np.abs(Gg - ref["G_greater"]).max() <= 1e-9
+
+
+def test_spectral_adaptive_multi_vector_configs(ed_lib):
+    """The adaptive ring-6 batch with each complex128 multi-vector
+    configuration pinned: vectors that share thread blocks exit at their own
+    Lanczos step, and the traces match the oracle's adaptive batch."""
+    torch = torch_cuda()
+    lat = LATTICES["ring6"]
+    pulse = {"A0": 0.6, "omega": 5.0, "sigma": 1.0, "t0": 0.3, "dir": (1.0, 0.0, 0.0)}
+    E0, psi0, gap = oracle.ground_state(lat, 3, 3, 4.0)
+    ref = oracle.spectral_batch(lat, 3, 3, 4.0, psi0, pulse, 0.05, 8, 16, eps_tol=1e-9)
+    mv = [c for c in range(ed_lib.ed_apply_config_count())
+          if ed_lib.ed_apply_config_info(c)["mv"] and ed_lib.ed_apply_config_info(c)["fp64"]]
+    assert mv
+    try:
+        for cfg in mv:
+            ed_lib.ed_set_apply_config(cfg)
+            h = ed_lib.Hubbard(lat, 3, 3, 4.0)
+            ed_lib.ed_set_krylov_tol(h.ctx, 1e-9)
+            Gl, Gg = ed_lib.ed_spectral_propagate(h.ctx, to_dev(torch, psi0, "c128"),
+                                                  ed_lib.ED_C128, pulse, 0.05, 8, 16, 6)
+            h.close()
+            assert np.abs(Gl - ref["G_less"]).max() <= 1e-9, cfg
+            assert np.abs(Gg - ref["G_greater"]).max() <= 1e-9, cfg
+    finally:
+        ed_lib.ed_set_apply_config(-1)

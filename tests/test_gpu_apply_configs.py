@@ -92,10 +92,10 @@ def test_every_config_matches_oracle(pinned, dtype, name, lat, nu, nd, U):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_split_propagation_with_energy_matches_oracle(pinned, dtype):
-    """A short propagation of the 3x4 torus, (6,5), with every split and
-    every TMA configuration of the precision pinned: state, <d>, norm and
-    energy (the energy runs H v once more per step) against the oracle's
-    trajectory."""
+    """A short propagation of the 3x4 torus, (6,5), with every split, every
+    TMA and every multi-vector configuration of the precision pinned (the
+    last with one-vector subgroups): state, <d>, norm and energy (the energy
+    runs H v once more per step) against the oracle's trajectory."""
     torch = torch_cuda()
     ed = pinned
     lat = LATTICES["torus3x4"]
@@ -104,7 +104,7 @@ def test_split_propagation_with_energy_matches_oracle(pinned, dtype):
     psi0 /= np.linalg.norm(psi0)
     ref = oracle.propagate(lat, 6, 5, 8.0, psi0, pulse, 0.02, 6, 16, with_energy=True)
     split = [c for c in configs(ed, dtype)
-             if ed.ed_apply_config_info(c)["split"] or ed.ed_apply_config_info(c)["tma"]]
+             if any(ed.ed_apply_config_info(c)[k] for k in ("split", "tma", "mv"))]
     for cfg in split:
         ed.ed_set_apply_config(cfg)
         h = ed.Hubbard(lat, 6, 5, 8.0)
