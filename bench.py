@@ -630,10 +630,11 @@ def main():
     ms_step = t_ms / args.steps
     m_eff = out["m_eff"]
     # kernels per step: m applies (two kernels each for the split apply),
-    # m - 1 updates, expm, combine; plus the observation launch
+    # m - 1 updates, expm, combine; plus the observation launch and the two
+    # column permutations (into the hop order of the down-spin tables and back)
     acfg = ed.ed_get_apply_config(h.ctx)[0]
     ainfo = ed.ed_apply_config_info(acfg)
-    gpu_launches = 1 + args.steps * ((2 + ainfo["split"]) * m + 1)
+    gpu_launches = 3 + args.steps * ((2 + ainfo["split"]) * m + 1)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

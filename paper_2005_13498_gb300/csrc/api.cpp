@@ -33,6 +33,7 @@ void build_sector_host(SectorGPU& S, const LatticeHost& L, int n_up, int n_dn) {
   S.n_dn = n_dn;
   S.up = build_spin_table(L, n_up);
   S.dn = build_spin_table(L, n_dn);
+  S.dn_hop = build_spin_table(L, n_dn, true);
   S.has_eps = L.has_eps;
   S.uploaded = false;
 }
@@ -97,13 +98,26 @@ cudaError_t upload_sector(SectorGPU& S) {
     if ((e = upload(S.dn_ellp32, pk)) != cudaSuccess) return e;
     if (!packed_copy(S.dn.ell, 16, &pk)) return cudaErrorInvalidValue;   // units = rank
     if ((e = upload(S.dn_ellpr, pk)) != cudaSuccess) return e;
+    // the same for the hop-ordered down-spin table
+    if ((e = upload(S.dnh_off, S.dn_hop.off)) != cudaSuccess) return e;
+    if ((e = upload(S.dnh_ent, S.dn_hop.ent)) != cudaSuccess) return e;
+    if ((e = upload(S.dnh_word, S.dn_hop.words)) != cudaSuccess) return e;
+    if ((e = upload(S.dnh_tslot_off, S.dn_hop.tslot_off)) != cudaSuccess) return e;
+    if ((e = upload(S.dnh_slot_grp, S.dn_hop.slot_grp)) != cudaSuccess) return e;
+    if ((e = upload(S.dn_order, S.dn_hop.order)) != cudaSuccess) return e;
+    if (!packed_copy(S.dn_hop.ell, 32, &pk)) return cudaErrorInvalidValue;
+    if ((e = upload(S.dnh_ellp32, pk)) != cudaSuccess) return e;
+    if (!packed_copy(S.dn_hop.ell, 16, &pk)) return cudaErrorInvalidValue;
+    if ((e = upload(S.dnh_ellpr, pk)) != cudaSuccess) return e;
   }
   if (S.has_eps) {
     if ((e = upload(S.up_eps, S.up.eps_sum)) != cudaSuccess) return e;
     if ((e = upload(S.dn_eps, S.dn.eps_sum)) != cudaSuccess) return e;
+    if ((e = upload(S.dnh_eps, S.dn_hop.eps_sum)) != cudaSuccess) return e;
   } else {
     S.up_eps.release();
     S.dn_eps.release();
+    S.dnh_eps.release();
   }
   SectorDev& d = S.dev;
   d.dim_up = S.up.dim;
@@ -130,6 +144,16 @@ cudaError_t upload_sector(SectorGPU& S) {
   d.up_ell16 = static_cast<const uint32_t*>(S.up_ell16.p);
   d.dn_ellp32 = static_cast<const uint32_t*>(S.dn_ellp32.p);
   d.dn_ellpr = static_cast<const uint32_t*>(S.dn_ellpr.p);
+  SectorDev& h = S.dev_hop;
+  h = d;
+  h.dn_off = static_cast<const int32_t*>(S.dnh_off.p);
+  h.dn_ent = static_cast<const uint32_t*>(S.dnh_ent.p);
+  h.dn_word = static_cast<const uint32_t*>(S.dnh_word.p);
+  h.dn_eps = S.has_eps ? static_cast<const double*>(S.dnh_eps.p) : nullptr;
+  h.dn_tslot_off = static_cast<const int32_t*>(S.dnh_tslot_off.p);
+  h.dn_slot_grp = static_cast<const uint32_t*>(S.dnh_slot_grp.p);
+  h.dn_ellp32 = static_cast<const uint32_t*>(S.dnh_ellp32.p);
+  h.dn_ellpr = static_cast<const uint32_t*>(S.dnh_ellpr.p);
   S.uploaded = true;
   return cudaSuccess;
 }
@@ -357,7 +381,10 @@ ed_status ed_device_bytes(const ed_ctx* ctx, int64_t* bytes) {
               S.dn_tslot_off.bytes +
               S.dn_slot_grp.bytes + S.up_tslot_off.bytes + S.up_slot_grp.bytes +
               S.up_ell.bytes + S.up_ell16.bytes +
-              S.dn_ellp32.bytes + S.dn_ellpr.bytes;
+              S.dn_ellp32.bytes + S.dn_ellpr.bytes + S.dnh_off.bytes + S.dnh_ent.bytes +
+              S.dnh_word.bytes + S.dnh_eps.bytes + S.dnh_tslot_off.bytes +
+              S.dnh_slot_grp.bytes + S.dnh_ellp32.bytes + S.dnh_ellpr.bytes +
+              S.dn_order.bytes;
   if (ctx->engine) b += ctx->engine->device_bytes();
   if (ctx->spec_engine) b += ctx->spec_engine->device_bytes();
   *bytes = b;
@@ -614,7 +641,9 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   if (!ctx->engine || !ctx->engine->compatible(cfg, vecs)) {
     ctx->engine.reset(new Engine());
     cfg.n_steps_cap = std::max(cfg.n_steps_cap, 64);
-    std::string err = ctx->engine->setup(cfg, {ctx->sec.dev}, vecs, 2 * ctx->lat.n_classes,
+    // the engine runs on the hop-ordered down-spin tables (fewer padded ELL
+    // slots): the state's columns are permuted into that order for the call
+    std::string err = ctx->engine->setup(cfg, {ctx->sec.dev_hop}, vecs, 2 * ctx->lat.n_classes,
                                          ctx->Ns, ctx->lat.U, fp64 ? 1e-13 : 1e-6, s,
                                          {&ctx->sec.up});
     if (!err.empty()) {
@@ -624,6 +653,13 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   }
   Engine& E = *ctx->engine;
   if (!on_device) CK(ctx, cudaMemcpyAsync(E.vec_x1(0), psi, D * esz, cudaMemcpyHostToDevice, s));
+  void* x1 = E.vec_x1(0);
+  const int32_t* order = static_cast<const int32_t*>(ctx->sec.dn_order.p);
+  CK(ctx, launch_permute_cols(fp64, x1, (int)ctx->dim_up, (int)ctx->dim_dn, order, true, s));
+  int status = 0;
+  // the steps; the state's columns go back to ascending-word order whatever
+  // they return
+  const ed_status run_st = [&]() -> ed_status {
   // energy at the time-step boundaries t_start + k dt / per of the sub-steps
   // (only every per-th entry, a whole time step, is reported)
   std::vector<double> coefs_obs;
@@ -632,7 +668,6 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   CKS(ctx, E.begin(sub.coefs, coefs_obs, n_sub, sub.tau, s));
   CKS(ctx, E.run(n_sub, profile, obs ? obs->kernel_ms : nullptr,
                  obs ? obs->kernel_launches : nullptr, s));
-  int status = 0;
   if (per == 1) {
     CKS(ctx, E.fetch(0, n_steps, obs ? obs->docc : nullptr, obs ? obs->norm2 : nullptr,
                      energy ? obs->energy : nullptr, obs ? obs->delta : nullptr,
@@ -660,6 +695,12 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
       }
     }
   }
+  return ED_OK;
+  }();
+  const cudaError_t pe =
+      launch_permute_cols(fp64, x1, (int)ctx->dim_up, (int)ctx->dim_dn, order, false, s);
+  if (run_st != ED_OK) return run_st;
+  CK(ctx, pe);
   if (!on_device) {
     CK(ctx, cudaMemcpyAsync(psi, E.vec_x1(0), D * esz, cudaMemcpyDeviceToHost, s));
     CK(ctx, cudaStreamSynchronize(s));

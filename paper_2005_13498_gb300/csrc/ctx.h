@@ -23,6 +23,13 @@ struct SectorGPU {
   DevMem up_tslot_off, up_slot_grp, up_ell, up_ell16;
   DevMem dn_ellp32, dn_ellpr;
   SectorDev dev{};
+  // the down-spin table in hop order (build_spin_table) with its device
+  // copies, and dev_hop: dev with those down-spin tables, for vectors whose
+  // columns are permuted into hop order (dn_order: position -> rank)
+  SpinTable dn_hop;
+  DevMem dnh_off, dnh_ent, dnh_word, dnh_eps, dnh_tslot_off, dnh_slot_grp, dnh_ellp32,
+      dnh_ellpr, dn_order;
+  SectorDev dev_hop{};
   bool has_eps = false;
   bool uploaded = false;
 };

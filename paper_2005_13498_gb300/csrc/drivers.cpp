@@ -99,7 +99,9 @@ struct GsApply {
 // x, w: device buffers of length D the autotuner may read and overwrite.
 std::string gs_apply_setup(GsApply& G, ed_ctx* ctx, const double2* x, double2* w,
                            cudaStream_t s) {
-  std::vector<SectorDev> secs = {ctx->sec.dev};
+  // hop-ordered down-spin tables: the Lanczos vectors keep their columns in
+  // that order, and the result goes back to ascending-word order at the end
+  std::vector<SectorDev> secs = {ctx->sec.dev_hop};
   std::vector<VecDev> vd(1);
   std::memset(vd.data(), 0, sizeof(VecDev));
   vd[0].D = ctx->dim_up * ctx->dim_dn;
@@ -290,7 +292,10 @@ ed_status ed_ground_state(ed_ctx* ctx, void* psi, double* E0, double tol, int ma
     // restart from the Ritz vector
     CK(ctx, cudaMemcpyAsync(vk(0), yp, (size_t)D * 16, cudaMemcpyDeviceToDevice, s));
   }
-  // phase fix on the host: largest-magnitude element real and positive
+  // columns back to ascending-word order, then the phase fix on the host:
+  // largest-magnitude element real and positive
+  CK(ctx, launch_permute_cols(true, yp, (int)ctx->dim_up, (int)ctx->dim_dn,
+                              static_cast<const int32_t*>(ctx->sec.dn_order.p), false, s));
   std::vector<std::complex<double>> h(D);
   CK(ctx, cudaMemcpyAsync(h.data(), yp, (size_t)D * 16, cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaStreamSynchronize(s));

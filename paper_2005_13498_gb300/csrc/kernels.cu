@@ -2396,6 +2396,46 @@ cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Column permutation of every row of a dim_up x dim_dn matrix, in place: one
+// CTA per row stages it in shared memory, then forward: x[u][i] =
+// x_old[u][order[i]] (ascending-word columns -> hop order); back:
+// x[u][order[i]] = x_old[u][i].
+template <typename C>
+__global__ void __launch_bounds__(256) k_permute_cols(C* x, int dim_dn, const int32_t* order,
+                                                      int forward) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* row = reinterpret_cast<C*>(smem_raw);
+  C* xr = x + (size_t)blockIdx.x * dim_dn;
+  for (int d = threadIdx.x; d < dim_dn; d += blockDim.x) row[d] = xr[d];
+  __syncthreads();
+  if (forward)
+    for (int i = threadIdx.x; i < dim_dn; i += blockDim.x) xr[i] = row[__ldg(order + i)];
+  else
+    for (int i = threadIdx.x; i < dim_dn; i += blockDim.x) xr[__ldg(order + i)] = row[i];
+}
+
+cudaError_t launch_permute_cols(bool fp64, void* x, int dim_up, int dim_dn, const int32_t* order,
+                                bool forward, cudaStream_t s) {
+  if (dim_up < 1 || dim_dn < 2) return cudaSuccess;   // nothing to permute
+  const size_t smem = (size_t)dim_dn * (fp64 ? 16 : 8);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (fp64) {
+    e = cudaFuncSetAttribute(k_permute_cols<double2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_permute_cols<double2><<<dim_up, 256, smem, s>>>(static_cast<double2*>(x), dim_dn, order,
+                                                      forward ? 1 : 0);
+  } else {
+    e = cudaFuncSetAttribute(k_permute_cols<float2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_permute_cols<float2><<<dim_up, 256, smem, s>>>(static_cast<float2*>(x), dim_dn, order,
+                                                     forward ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tridiag_expm(const double* alpha, const double* beta, int n, double tau,
                                 double* y, int batch, cudaStream_t s) {
   if (n < 1 || n > kMaxKrylov || batch < 1) return cudaErrorInvalidValue;

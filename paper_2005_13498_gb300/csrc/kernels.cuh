@@ -175,6 +175,10 @@ struct OverlapArgs {
 };
 cudaError_t launch_overlap(bool fp64, const BatchArgs& a, const OverlapArgs& o,
                            int n_ew_blocks, cudaStream_t s);
+// In-place column permutation of each row of a dim_up x dim_dn complex
+// matrix (device): forward x[u][i] = x_old[u][order[i]], else the inverse.
+cudaError_t launch_permute_cols(bool fp64, void* x, int dim_up, int dim_dn, const int32_t* order,
+                                bool forward, cudaStream_t s);
 // out[c * rows + r] = in[r * cols + c] for a rows x cols complex matrix.
 cudaError_t launch_transpose(bool fp64, const void* in, void* out, int rows, int cols,
                              cudaStream_t s);

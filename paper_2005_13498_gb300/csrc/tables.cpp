@@ -163,11 +163,40 @@ static std::vector<uint32_t> assign_slots(std::vector<std::vector<uint32_t>> lis
   return out;
 }
 
-SpinTable build_spin_table(const LatticeHost& L, int n) {
+SpinTable build_spin_table(const LatticeHost& L, int n, bool hop_order) {
   SpinTable T;
   T.n = n;
   T.words = spin_basis(L.Ns, n);
   T.dim = (int)T.words.size();
+  T.order.resize(T.dim);
+  for (int i = 0; i < T.dim; ++i) T.order[i] = i;
+  // pos[rank]: position of the state of that ascending-word rank
+  std::vector<uint32_t> pos(T.dim);
+  for (int i = 0; i < T.dim; ++i) pos[i] = (uint32_t)i;
+  if (hop_order) {
+    const int ngrp = 2 * L.n_classes;
+    std::vector<int32_t> key((size_t)T.dim * ngrp, 0);   // hops into each state, per group
+    for (int r = 0; r < T.dim; ++r) {
+      const uint32_t y = T.words[r];
+      for (int b = 0; b < L.n_bonds; ++b) {
+        const uint32_t bp = 1u << L.p[b], bq = 1u << L.q[b];
+        if ((y & bq) && !(y & bp)) key[(size_t)r * ngrp + 2 * L.bond_class[b]]++;
+        if ((y & bp) && !(y & bq)) key[(size_t)r * ngrp + 2 * L.bond_class[b] + 1]++;
+      }
+    }
+    std::stable_sort(T.order.begin(), T.order.end(), [&](int a, int b) {
+      return std::lexicographical_compare(key.begin() + (size_t)b * ngrp,
+                                          key.begin() + (size_t)(b + 1) * ngrp,
+                                          key.begin() + (size_t)a * ngrp,
+                                          key.begin() + (size_t)(a + 1) * ngrp);
+    });
+    std::vector<uint32_t> w(T.dim);
+    for (int i = 0; i < T.dim; ++i) {
+      w[i] = T.words[T.order[i]];
+      pos[T.order[i]] = (uint32_t)i;
+    }
+    T.words = w;
+  }
   T.off.assign(T.dim + 1, 0);
   struct E { uint32_t group, src, neg; };
   std::vector<E> row;
@@ -182,10 +211,10 @@ SpinTable build_spin_table(const LatticeHost& L, int n) {
       const uint32_t neg = (uint32_t)(popc(y & between) & 1);
       // orientation 0: hop p -> q produced y (q set, p clear in y)
       if ((y & bq) && !(y & bp))
-        row.push_back({(uint32_t)(2 * L.bond_class[b]), combinadic_rank(y ^ bp ^ bq), neg});
+        row.push_back({(uint32_t)(2 * L.bond_class[b]), pos[combinadic_rank(y ^ bp ^ bq)], neg});
       // orientation 1: hop q -> p produced y (p set, q clear in y)
       if ((y & bp) && !(y & bq))
-        row.push_back({(uint32_t)(2 * L.bond_class[b] + 1), combinadic_rank(y ^ bp ^ bq), neg});
+        row.push_back({(uint32_t)(2 * L.bond_class[b] + 1), pos[combinadic_rank(y ^ bp ^ bq)], neg});
     }
     std::sort(row.begin(), row.end(), [](const E& a, const E& b) {
       return a.group != b.group ? a.group < b.group : a.src < b.src;

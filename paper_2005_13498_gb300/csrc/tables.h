@@ -78,8 +78,18 @@ struct SpinTable {
   std::vector<int32_t> tslot_off;
   std::vector<uint32_t> slot_grp;
   std::vector<uint32_t> ell;
+  // order[i]: the rank (ascending-word position) of the basis state at
+  // position i of this table; the identity unless built in hop order
+  std::vector<int32_t> order;
 };
-SpinTable build_spin_table(const LatticeHost& L, int n);
+// The table of one spin species in ascending-word order (the basis order of
+// the C ABI), or with hop_order in the order of decreasing per-group hop
+// counts (ties by word): every quantity of the table (words, entries' source
+// positions, ELL) then refers to positions in that order, whose 64-column
+// ELL tiles hold columns of equal entry counts per group and so need fewer
+// padded slots.  A vector whose columns are in hop order is the ascending
+// one permuted by `order` (k_permute_cols in kernels.cu).
+SpinTable build_spin_table(const LatticeHost& L, int n, bool hop_order = false);
 
 // First rows of the blocks of nr consecutive rows of the target space of T
 // (the apply's CTAs), in reverse Cuthill-McKee order of the graph in which

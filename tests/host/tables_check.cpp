@@ -99,6 +99,7 @@ int main() {
     }
     // warp-tiled ELL: every column's slot entries are its CSR entries (same
     // rank and sign), the rest point at the zero columns dim .. dim + 7
+    auto check_ell = [&](const ed::SpinTable& T) -> int {
     const int ntile = (dim + 63) / 64;
     REQUIRE((int)T.tslot_off.size() == ntile + 1, "tslot_off size n=%d", n);
     for (int c = 0; c < ntile; ++c) {
@@ -124,6 +125,40 @@ int main() {
           REQUIRE(got == want, "ell column n=%d col=%d", n, col);
         }
     }
+    return 0;
+    };
+    if (check_ell(T)) return 1;
+    // hop order: a permutation of the basis whose table is the ascending
+    // one relabelled (same hops, groups and signs), with its own ELL
+    const ed::SpinTable H = ed::build_spin_table(L, n, true);
+    REQUIRE(H.dim == dim && (int)H.order.size() == dim, "hop table size n=%d", n);
+    {
+      std::vector<int> seen(dim, 0);
+      for (int i = 0; i < dim; ++i) {
+        const int o = H.order[i];
+        REQUIRE(o >= 0 && o < dim && !seen[o], "hop order permutation n=%d", n);
+        seen[o] = 1;
+        REQUIRE(H.words[i] == words[o], "hop order words n=%d i=%d", n, i);
+      }
+      for (int i = 0; i < dim; ++i) {
+        std::vector<uint32_t> a, b;
+        for (int e = H.off[i]; e < H.off[i + 1]; ++e)
+          a.push_back(((uint32_t)H.order[H.ent[e] & 0xFFFFu]) | (H.ent[e] & 0xFFFF0000u));
+        const int o = H.order[i];
+        for (int e = T.off[o]; e < T.off[o + 1]; ++e) b.push_back(T.ent[e]);
+        std::sort(a.begin(), a.end());
+        std::sort(b.begin(), b.end());
+        REQUIRE(a == b, "hop order row n=%d i=%d", n, i);
+      }
+      // per-group hop counts do not increase along the order
+      for (int i = 1; i < dim; ++i) {
+        std::vector<int> ka(ng, 0), kb(ng, 0);
+        for (int e = H.off[i - 1]; e < H.off[i]; ++e) ka[(H.ent[e] >> 16) & 0xFFu]++;
+        for (int e = H.off[i]; e < H.off[i + 1]; ++e) kb[(H.ent[e] >> 16) & 0xFFu]++;
+        REQUIRE(!(ka < kb), "hop order keys n=%d i=%d", n, i);
+      }
+    }
+    if (check_ell(H)) return 1;
     // CTA order: a permutation of the rows
     const std::vector<int> order = ed::block_order(T, 1);
     std::vector<int> seen(dim, 0);
