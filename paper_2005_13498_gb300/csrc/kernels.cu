@@ -5,15 +5,16 @@
 //          + sum_{(d',g,s) in C_dn(d)} s c_g Psi[u,d']      (T_dn: within a row)
 //          + (U popcount(up[u] & dn[d]) + eps_up[u] + eps_dn[d]) Psi[u,d]
 // (Eq. (1) with the Peierls phases of Eq. (3); c_g the per-step coefficient of
-// bond class g/2 in orientation g%2).  One CTA processes one row u: the row
-// Psi[u,:] is staged in shared memory for T_dn, the T_up gathers read whole
-// rows Psi[u',:] with coalesced loads along d, and the signed values of one
-// bond group are summed before a single complex multiply by c_g.
+// bond class g/2 in orientation g%2).  One CTA processes a block of rows u:
+// the rows Psi[u,:] are staged in shared memory for T_dn, the T_up gathers
+// read whole rows Psi[u',:] with coalesced loads along d, and the signed
+// values of one bond group are summed before a single complex multiply by
+// c_g.  The column index d is a position in the down-spin table's basis
+// order (ascending words, or the hop order the propagation uses).
 //
 // The Lanczos recursion (Algorithm 6) is split into two passes per step j:
 //   apply :  w = s_j H x_j - beta_{j-1} s_{j-1} x_{j-1},  alpha_j = Re<v_j, w>
-//   update:  x_{j+1} = w - h_jj s_j x_j,  beta_j = |x_{j+1}|,  with
-//            h_jj = <v_j, w> complex (alpha_j = Re h_jj enters T_m),
+//   update:  x_{j+1} = w - alpha_j s_j x_j,  beta_j = |x_{j+1}|,
 //            s_{j+1} = 1 / beta_j   (normalisation is applied lazily)
 // Reductions are deterministic: per-block partial sums in float64, then the
 // last block of each vector sums the partials in block order.
