@@ -36,7 +36,7 @@ UNIT = "ms/step"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=4)
@@ -77,7 +77,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 100 ms; each sample
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms; each sample
     keeps the host time it arrived at, so that summary() can keep the
     samples of one timed window."""
 
@@ -94,7 +94,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -122,7 +122,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         lines = self.lines
         if t0 is not None and t1 is not None:
-            win = [x for x in lines if t0 <= x[0] <= t1 + 0.1]
+            win = [x for x in lines if t0 <= x[0] <= t1 + 0.05]
             lines = win or lines
         window = "timed region" if lines is not self.lines else "whole sampler run"
         for _, ln in lines:
