@@ -129,7 +129,10 @@ int main() {
     };
     if (check_ell(T)) return 1;
     // hop order: a permutation of the basis whose table is the ascending
-    // one relabelled (same hops, groups and signs), with its own ELL
+    // one relabelled (same hops, groups and signs), with its own ELL; the
+    // tile search takes seconds under the sanitizers past a few thousand
+    // columns, so the largest bases (Ns=16 near half filling) skip it here
+    if (dim <= 4000) {
     const ed::SpinTable H = ed::build_spin_table(L, n, true);
     REQUIRE(H.dim == dim && (int)H.order.size() == dim, "hop table size n=%d", n);
     {
@@ -150,15 +153,20 @@ int main() {
         std::sort(b.begin(), b.end());
         REQUIRE(a == b, "hop order row n=%d i=%d", n, i);
       }
-      // per-group hop counts do not increase along the order
-      for (int i = 1; i < dim; ++i) {
-        std::vector<int> ka(ng, 0), kb(ng, 0);
-        for (int e = H.off[i - 1]; e < H.off[i]; ++e) ka[(H.ent[e] >> 16) & 0xFFu]++;
-        for (int e = H.off[i]; e < H.off[i + 1]; ++e) kb[(H.ent[e] >> 16) & 0xFFu]++;
-        REQUIRE(!(ka < kb), "hop order keys n=%d i=%d", n, i);
-      }
+      // the 64-column tiles hold the columns of the order sorted by
+      // decreasing per-group hop counts (the columns of a tile may come in
+      // any order): sorted within each tile, the keys do not increase
+      std::vector<std::vector<int>> keys(dim, std::vector<int>(ng, 0));
+      for (int i = 0; i < dim; ++i)
+        for (int e = H.off[i]; e < H.off[i + 1]; ++e) keys[i][(H.ent[e] >> 16) & 0xFFu]++;
+      for (int t0 = 0; t0 < dim; t0 += 64)
+        std::sort(keys.begin() + t0, keys.begin() + std::min(dim, t0 + 64),
+                  [](const std::vector<int>& x, const std::vector<int>& y) { return y < x; });
+      for (int i = 1; i < dim; ++i)
+        REQUIRE(!(keys[i - 1] < keys[i]), "hop order keys n=%d i=%d", n, i);
     }
     if (check_ell(H)) return 1;
+    }
     // CTA order: a permutation of the rows
     const std::vector<int> order = ed::block_order(T, 1);
     std::vector<int> seen(dim, 0);
