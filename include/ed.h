@@ -198,7 +198,12 @@ ed_status ed_ground_state(ed_ctx* ctx, void* psi, double* E0, double tol,
  * each exponential by m Lanczos steps (Algorithm 6 with fixed m, breakdown
  * exit when beta_j <= tol * max(1, max|alpha|, max beta), tol = 1e-13 for
  * ED_C128 and 1e-6 for ED_C64).  psi (DEVICE or host pointer of `dtype`) is
- * updated in place.  obs (nullable) receives observables at t_0..t_{n_steps}.
+ * updated in place; a host psi is back in place when the call returns.  A
+ * pinned host psi (cudaHostAlloc, or cudaHostRegister with mapping) is read
+ * and written by a kernel over the host link, any other host memory through
+ * a staged copy.  After an error a host psi holds the state as far as the
+ * steps got (pinned) or is unchanged (other host memory).
+ * obs (nullable) receives observables at t_0..t_{n_steps}.
  * One step is captured as a CUDA graph and replayed.  Requires 1 <= m <= 64.
  * Errors: ED_ERR_ARG, ED_ERR_STATE, ED_ERR_UNSUPPORTED (m > 64),
  * ED_ERR_NUMERIC (non-finite norm), ED_ERR_CUDA / ED_ERR_OOM.                */

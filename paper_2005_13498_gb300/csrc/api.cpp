@@ -104,7 +104,16 @@ cudaError_t upload_sector(SectorGPU& S) {
     if ((e = upload(S.dnh_word, S.dn_hop.words)) != cudaSuccess) return e;
     if ((e = upload(S.dnh_tslot_off, S.dn_hop.tslot_off)) != cudaSuccess) return e;
     if ((e = upload(S.dnh_slot_grp, S.dn_hop.slot_grp)) != cudaSuccess) return e;
-    if ((e = upload(S.dn_order, S.dn_hop.order)) != cudaSuccess) return e;
+    {
+      // the permutation and its inverse (the permutation kernel gathers both ways)
+      const std::vector<int32_t>& o = S.dn_hop.order;
+      std::vector<int32_t> oi(2 * o.size());
+      for (size_t i = 0; i < o.size(); ++i) {
+        oi[i] = o[i];
+        oi[o.size() + (size_t)o[i]] = (int32_t)i;
+      }
+      if ((e = upload(S.dn_order, oi)) != cudaSuccess) return e;
+    }
     if (!packed_copy(S.dn_hop.ell, 32, &pk)) return cudaErrorInvalidValue;
     if ((e = upload(S.dnh_ellp32, pk)) != cudaSuccess) return e;
     if (!packed_copy(S.dn_hop.ell, 16, &pk)) return cudaErrorInvalidValue;
@@ -204,6 +213,18 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The device's address of a pinned host buffer mapped into its address space
+// (cudaHostAlloc, or cudaHostRegister with mapping), or NULL for any other
+// pointer.
+static void* mapped_host_ptr(void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 // Event-based ordering between the caller's stream and the context stream.
@@ -652,10 +673,19 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
     }
   }
   Engine& E = *ctx->engine;
-  if (!on_device) CK(ctx, cudaMemcpyAsync(E.vec_x1(0), psi, D * esz, cudaMemcpyHostToDevice, s));
   void* x1 = E.vec_x1(0);
   const int32_t* order = static_cast<const int32_t*>(ctx->sec.dn_order.p);
-  CK(ctx, launch_permute_cols(fp64, x1, (int)ctx->dim_up, (int)ctx->dim_dn, order, true, s));
+  // A pinned host state is read (and at the end written) by the permutation
+  // kernel itself, in the same pass that puts its columns into hop order;
+  // other host memory goes through a copy and the in-place permutation.
+  void* host_dev = on_device ? nullptr : mapped_host_ptr(psi);
+  if (host_dev) {
+    CK(ctx, launch_permute_cols_copy(fp64, host_dev, x1, (int)ctx->dim_up, (int)ctx->dim_dn,
+                                     order, true, s));
+  } else {
+    if (!on_device) CK(ctx, cudaMemcpyAsync(x1, psi, D * esz, cudaMemcpyHostToDevice, s));
+    CK(ctx, launch_permute_cols(fp64, x1, (int)ctx->dim_up, (int)ctx->dim_dn, order, true, s));
+  }
   int status = 0;
   // the steps; the state's columns go back to ascending-word order whatever
   // they return
@@ -698,12 +728,23 @@ ed_status ed_propagate(ed_ctx* ctx, void* psi, ed_dtype dtype, const ed_pulse* p
   return ED_OK;
   }();
   const cudaError_t pe =
-      launch_permute_cols(fp64, x1, (int)ctx->dim_up, (int)ctx->dim_dn, order, false, s);
-  if (run_st != ED_OK) return run_st;
-  CK(ctx, pe);
-  if (!on_device) {
-    CK(ctx, cudaMemcpyAsync(psi, E.vec_x1(0), D * esz, cudaMemcpyDeviceToHost, s));
-    CK(ctx, cudaStreamSynchronize(s));
+      host_dev ? launch_permute_cols_copy(fp64, x1, host_dev, (int)ctx->dim_up,
+                                          (int)ctx->dim_dn, order, false, s)
+               : launch_permute_cols(fp64, x1, (int)ctx->dim_up, (int)ctx->dim_dn, order, false, s);
+  if (host_dev) {
+    // the permutation kernel writes psi: done before the call returns, also
+    // on an error
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (run_st != ED_OK) return run_st;
+    CK(ctx, pe);
+    CK(ctx, se);
+  } else {
+    if (run_st != ED_OK) return run_st;
+    CK(ctx, pe);
+    if (!on_device) {
+      CK(ctx, cudaMemcpyAsync(psi, x1, D * esz, cudaMemcpyDeviceToHost, s));
+      CK(ctx, cudaStreamSynchronize(s));
+    }
   }
   CK(ctx, join_streams(s, us));
   if (status == ED_ERR_TIMEOUT)

@@ -25,7 +25,8 @@ struct SectorGPU {
   SectorDev dev{};
   // the down-spin table in hop order (build_spin_table) with its device
   // copies, and dev_hop: dev with those down-spin tables, for vectors whose
-  // columns are permuted into hop order (dn_order: position -> rank)
+  // columns are permuted into hop order (dn_order: position -> rank, then
+  // its inverse rank -> position)
   SpinTable dn_hop;
   DevMem dnh_off, dnh_ent, dnh_word, dnh_eps, dnh_tslot_off, dnh_slot_grp, dnh_ellp32,
       dnh_ellpr, dn_order;

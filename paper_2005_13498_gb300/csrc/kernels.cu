@@ -387,22 +387,61 @@ struct TileIO {
 };
 
 // T_up gathers of one chunk of the apply (k_apply): for each of the CTA's
-// rows u the padded entry list of u (uniform over the block) is walked four
-// entries at a time, each a coalesced load of the thread's column pairs of
-// the source row per column-pair group k < KA, all loads of a batch in
-// flight before they are used (padding entries load row u itself and carry
-// a zero coefficient: skipping their loads measured slower, the extra
-// instructions cost more than the L2 bytes they save).  KA counts the groups
-// of this chunk that hold
-// valid pairs; in the last of them the pair index is clamped to the last
-// pair of the row (those sums are never stored).
+// rows u the entry list of u (uniform over the block) is walked four entries
+// at a time, each a coalesced load of the thread's column pairs of the
+// source row per column-pair group k < KA, all loads of a batch in flight
+// before they are used; the last 1-3 entries of a list form a batch of their
+// own (complex64: one batch of three guarded by the count, which keeps the
+// configurations free of spills; complex128: a batch of each size), so no
+// load serves a padding entry (the lists are stored padded to 4 entries,
+// which keeps their 16-byte metadata loads aligned).  KA counts the groups of this chunk that hold valid pairs; in
+// the last of them the pair index is clamped to the last pair of the row
+// (those sums are never stored).
 //  * complex64: no group sums.  Each entry reads its signed coefficient
 //    s c_g from the CTA's table coefQ[cs] = (s Re c, s Re c, s Im c, s Im c)
-//    (cs = 1 + 2 g + [s < 0], cs = 0 for padding: zero), one broadcast load,
-//    and accumulates a += (Re, Re) v, b += (Im, Im) v with two packed FMAs
-//    and no operand swaps; the row ends with acc += (a.x - b.y, a.y + b.x).
+//    (cs = 1 + 2 g + [s < 0]), one broadcast load, and accumulates
+//    a += (Re, Re) v, b += (Im, Im) v with two packed FMAs and no operand
+//    swaps; the row ends with acc += (a.x - b.y, a.y + b.x).
 //  * complex128 (FP64-pipe bound): signed sums per bond group, multiplied
 //    by c_g once per group.
+template <int NB, int KA, bool VEC>
+__device__ __forceinline__ void tup_batch_c64(const float2* xrow, const int (&pk)[KA],
+                                              const float4* coefQ, int dim_dn,
+                                              const uint32_t (&css)[4], const uint32_t (&rows)[4],
+                                              float2 (&sa)[2 * KA], float2 (&sb)[2 * KA],
+                                              int nb = NB) {
+  float2 v[NB][2 * KA];   // entries qq >= nb (uniform over the block) are not read
+#pragma unroll
+  for (int qq = 0; qq < NB; ++qq) {
+    if (qq >= nb) {
+#pragma unroll
+      for (int k = 0; k < 2 * KA; ++k) v[qq][k] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const float2* src = xrow + rows[qq];
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      if constexpr (VEC) {
+        const float4 f = __ldcg(reinterpret_cast<const float4*>(src) + pk[k]);
+        v[qq][2 * k] = make_float2(f.x, f.y);
+        v[qq][2 * k + 1] = make_float2(f.z, f.w);
+      } else {
+        load_pair<float2, false>(src, pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int qq = 0; qq < NB; ++qq) {
+    if (qq >= nb) continue;
+    const float4 q = coefQ[css[qq]];
+#pragma unroll
+    for (int k = 0; k < 2 * KA; ++k) {
+      sa[k] = ffma2(make_float2(q.x, q.y), v[qq][k], sa[k]);
+      sb[k] = ffma2(make_float2(q.z, q.w), v[qq][k], sb[k]);
+    }
+  }
+}
+
 template <int NR, int PP, int KA, bool VEC, int NT>
 __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd,
                                               const float2* const (&xr)[NR],
@@ -419,44 +458,28 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd,
   for (int r = 0; r < NR; ++r) {
     if (r >= nrows) continue;   // uniform over the block
     const int u = urow[r];
-    const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
+    const int e0 = __ldg(sd.up_pad_off + u);
+    const int e1 = e0 + (__ldg(sd.up_off + u + 1) - __ldg(sd.up_off + u));   // real entries
     if (e0 >= e1) continue;
     float2 sa[2 * KA], sb[2 * KA];
 #pragma unroll
     for (int k = 0; k < 2 * KA; ++k) { sa[k] = make_float2(0.f, 0.f); sb[k] = sa[k]; }
     uint4 ncs = __ldg(cs4p + (e0 >> 2)), nrow = __ldg(row4p + (e0 >> 2));
-    for (int e = e0; e < e1; e += 4) {
-      const uint4 cs4 = ncs, row4 = nrow;
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+      const uint32_t css[4] = {ncs.x, ncs.y, ncs.z, ncs.w};
+      const uint32_t rows[4] = {nrow.x, nrow.y, nrow.z, nrow.w};
       if (e + 4 < e1) {   // the next batch's entries load under this batch's rows
         ncs = __ldg(cs4p + ((e + 4) >> 2));
         nrow = __ldg(row4p + ((e + 4) >> 2));
       }
-      const uint32_t css[4] = {cs4.x, cs4.y, cs4.z, cs4.w};
-      const uint32_t rows[4] = {row4.x, row4.y, row4.z, row4.w};
-      float2 v[4][2 * KA];
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
-        const float2* src = xr[r] + rows[qq];
-#pragma unroll
-        for (int k = 0; k < KA; ++k) {
-          if constexpr (VEC) {
-            const float4 f = __ldcg(reinterpret_cast<const float4*>(src) + pk[k]);
-            v[qq][2 * k] = make_float2(f.x, f.y);
-            v[qq][2 * k + 1] = make_float2(f.z, f.w);
-          } else {
-            load_pair<float2, false>(src, pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
-          }
-        }
-      }
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
-        const float4 q = coefQ[css[qq]];
-#pragma unroll
-        for (int k = 0; k < 2 * KA; ++k) {
-          sa[k] = ffma2(make_float2(q.x, q.y), v[qq][k], sa[k]);
-          sb[k] = ffma2(make_float2(q.z, q.w), v[qq][k], sb[k]);
-        }
-      }
+      tup_batch_c64<4, KA, VEC>(xr[r], pk, coefQ, dim_dn, css, rows, sa, sb);
+    }
+    if (e < e1) {   // the last 1-3 entries (uniform over the block)
+      const uint32_t css[4] = {ncs.x, ncs.y, ncs.z, ncs.w};
+      const uint32_t rows[4] = {nrow.x, nrow.y, nrow.z, nrow.w};
+      const int nb = e1 - e;
+      tup_batch_c64<3, KA, VEC>(xr[r], pk, coefQ, dim_dn, css, rows, sa, sb, nb);
     }
 #pragma unroll
     for (int k = 0; k < 2 * KA; ++k) {
@@ -467,7 +490,39 @@ __device__ __forceinline__ void tup_chunk_c64(const SectorDev& sd,
 }
 
 // complex128: row r gathers from xr[r] (one vector, or one per row in
-// multi-vector blocks)
+// multi-vector blocks); the signed values of a bond group are summed and
+// multiplied by c_g when the group changes
+template <int NB, int KA, int PP>
+__device__ __forceinline__ void tup_batch_c128(const double2* xrow, const int (&pk)[KA],
+                                               int dim_dn, const uint32_t (&ents)[4],
+                                               const uint32_t (&rows)[4], const double2* coefS,
+                                               double2 (&sum)[2 * KA], uint32_t& gcur,
+                                               double2 (&accr)[2 * PP]) {
+  using C = double2;
+  C v[NB][2 * KA];
+#pragma unroll
+  for (int qq = 0; qq < NB; ++qq)
+#pragma unroll
+    for (int k = 0; k < KA; ++k)
+      load_pair<C, false>(xrow + rows[qq], pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
+#pragma unroll
+  for (int qq = 0; qq < NB; ++qq) {
+    const uint32_t g = (ents[qq] >> kEntGroupShift) & 0xFFu;
+    if (g != gcur) {                              // uniform over the block
+      const C c = coefS[gcur];
+#pragma unroll
+      for (int k = 0; k < 2 * KA; ++k) {
+        cmac(accr[k], c, sum[k]);
+        sum[k] = czero<C>();
+      }
+      gcur = g;
+    }
+    const double sg = sign_of<double>(ents[qq]);
+#pragma unroll
+    for (int k = 0; k < 2 * KA; ++k) cax(sum[k], sg, v[qq][k]);
+  }
+}
+
 template <int NR, int PP, int KA, int NT>
 __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd,
                                                const double2* const (&xr)[NR],
@@ -486,43 +541,34 @@ __device__ __forceinline__ void tup_chunk_c128(const SectorDev& sd,
   for (int r = 0; r < NR; ++r) {
     if (r >= nrows) continue;   // uniform over the block
     const int u = urow[r];
-    const int e0 = __ldg(sd.up_pad_off + u), e1 = __ldg(sd.up_pad_off + u + 1);
+    const int e0 = __ldg(sd.up_pad_off + u);
+    const int e1 = e0 + (__ldg(sd.up_off + u + 1) - __ldg(sd.up_off + u));   // real entries
     if (e0 >= e1) continue;
     C sum[2 * KA];
 #pragma unroll
     for (int k = 0; k < 2 * KA; ++k) sum[k] = czero<C>();
     uint4 nent = __ldg(ent4p + (e0 >> 2)), nrow = __ldg(row4p + (e0 >> 2));
     uint32_t gcur = (nent.x >> kEntGroupShift) & 0xFFu;
-    for (int e = e0; e < e1; e += 4) {
-      const uint4 ent4 = nent, row4 = nrow;
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+      const uint32_t ents[4] = {nent.x, nent.y, nent.z, nent.w};
+      const uint32_t rows[4] = {nrow.x, nrow.y, nrow.z, nrow.w};
       if (e + 4 < e1) {   // the next batch's entries load under this batch's rows
         nent = __ldg(ent4p + ((e + 4) >> 2));
         nrow = __ldg(row4p + ((e + 4) >> 2));
       }
-      const uint32_t ents[4] = {ent4.x, ent4.y, ent4.z, ent4.w};
-      const uint32_t rows[4] = {row4.x, row4.y, row4.z, row4.w};
-      C v[4][2 * KA];
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq)
-#pragma unroll
-        for (int k = 0; k < KA; ++k)
-          load_pair<C, false>(xr[r] + rows[qq], pk[k], dim_dn, v[qq][2 * k], v[qq][2 * k + 1]);
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
-        const uint32_t g = (ents[qq] >> kEntGroupShift) & 0xFFu;
-        if (g != gcur) {                              // uniform over the block
-          const C c = coefS[gcur];
-#pragma unroll
-          for (int k = 0; k < 2 * KA; ++k) {
-            cmac(acc[r][k], c, sum[k]);
-            sum[k] = czero<C>();
-          }
-          gcur = g;
-        }
-        const double sg = (ents[qq] & kNullEntryBit) ? 0.0 : sign_of<double>(ents[qq]);
-#pragma unroll
-        for (int k = 0; k < 2 * KA; ++k) cax(sum[k], sg, v[qq][k]);
-      }
+      tup_batch_c128<4, KA, PP>(xr[r], pk, dim_dn, ents, rows, coefS, sum, gcur, acc[r]);
+    }
+    if (e < e1) {   // the last 1-3 entries (uniform over the block)
+      const uint32_t ents[4] = {nent.x, nent.y, nent.z, nent.w};
+      const uint32_t rows[4] = {nrow.x, nrow.y, nrow.z, nrow.w};
+      const int nb = e1 - e;
+      if (nb == 1)
+        tup_batch_c128<1, KA, PP>(xr[r], pk, dim_dn, ents, rows, coefS, sum, gcur, acc[r]);
+      else if (nb == 2)
+        tup_batch_c128<2, KA, PP>(xr[r], pk, dim_dn, ents, rows, coefS, sum, gcur, acc[r]);
+      else
+        tup_batch_c128<3, KA, PP>(xr[r], pk, dim_dn, ents, rows, coefS, sum, gcur, acc[r]);
     }
     const C c = coefS[gcur];
 #pragma unroll
@@ -1433,12 +1479,27 @@ __global__ void __launch_bounds__(256, 4) k_update(BatchArgs a, int j) {
 }
 
 // -------------------------------------------------------------------- expm
+// 1/k for the Taylor coefficients (evaluated by the compiler)
+struct InvK {
+  double v[81];
+};
+constexpr InvK make_inv_k() {
+  InvK t{};
+  t.v[0] = 0.0;
+  for (int k = 1; k <= 80; ++k) t.v[k] = 1.0 / (double)k;
+  return t;
+}
+__constant__ InvK kInvK = make_inv_k();
+
 // exp(-i tau T) e_1 for the real symmetric tridiagonal T of size n <= 64,
 // one warp.  T is shifted by the centre sigma of its Gershgorin interval,
-// the time step is split into nsub pieces with tau*halfwidth/nsub <= 1/2, and
-// each piece is a Taylor series summed until the next term is below 1e-17 of
-// the sum (the truncation error is then below rounding).  Lane l owns rows l
-// and l + 32.
+// whose half-width h bounds |T - sigma| (2-norm), and the time step is split
+// into nsub pieces with rho = |tau| h / nsub <= 1/2.  Each piece is a Taylor
+// series with a term count K fixed up front: the k-th term of a piece has
+// norm at most rho^k / k! (the state keeps unit norm), and the terms past K
+// sum to less than rho^(K+1) / (K+1)! / (1 - rho / (K+2)) <= 1e-17, below
+// rounding; K <= 16 for rho <= 1/2.  No per-term norms are reduced across
+// the warp.  Lane l owns rows l and l + 32.
 __device__ void tridiag_expm_e1(const double* al, const double* be, int n,
                                 double tau, double* yre, double* yim,
                                 double* tre, double* tim) {
@@ -1459,6 +1520,27 @@ __device__ void tridiag_expm_e1(const double* al, const double* be, int n,
   if (nsub < 1) nsub = 1;
   if (nsub > 4096) nsub = 4096;
   const double ts = tau / nsub;
+  // the term count from the bound (uniform over the warp)
+  const double rho = fabs(ts) * half;
+  int K = 1;
+  {
+    double b = rho;   // rho^k / k!, k = 1
+    for (int k = 1; k <= 78; ++k) {
+      const double nb = b * rho * kInvK.v[k + 1];   // rho^(k+1) / (k+1)!
+      K = k;
+      if (nb <= 1e-17 * (1.0 - rho * kInvK.v[k + 2])) break;
+      b = nb;
+    }
+  }
+  // per-lane rows: shifted diagonal and off-diagonals
+  double ash[2], bl[2], bu[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    ash[h] = i < n ? al[i] - sigma : 0.0;
+    bl[h] = (i < n && i > 0) ? be[i - 1] : 0.0;
+    bu[h] = (i < n - 1) ? be[i] : 0.0;
+  }
   for (int i = lane; i < 64; i += 32) {
     yre[i] = (i == 0) ? 1.0 : 0.0;
     yim[i] = 0.0;
@@ -1467,18 +1549,17 @@ __device__ void tridiag_expm_e1(const double* al, const double* be, int n,
   for (int sub = 0; sub < nsub; ++sub) {
     for (int i = lane; i < 64; i += 32) { tre[i] = yre[i]; tim[i] = yim[i]; }
     __syncwarp();
-    for (int k = 1; k <= 80; ++k) {
+    for (int k = 1; k <= K; ++k) {
       double nre[2] = {0.0, 0.0}, nim[2] = {0.0, 0.0};
-      double tn = 0.0, an = 0.0;
-      const double f = ts / k;
+      const double f = ts * kInvK.v[k];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int i = lane + 32 * h;
         if (i < n) {
-          double qr = (al[i] - sigma) * tre[i];
-          double qi = (al[i] - sigma) * tim[i];
-          if (i > 0) { qr += be[i - 1] * tre[i - 1]; qi += be[i - 1] * tim[i - 1]; }
-          if (i < n - 1) { qr += be[i] * tre[i + 1]; qi += be[i] * tim[i + 1]; }
+          double qr = ash[h] * tre[i];
+          double qi = ash[h] * tim[i];
+          if (i > 0) { qr += bl[h] * tre[i - 1]; qi += bl[h] * tim[i - 1]; }
+          if (i < n - 1) { qr += bu[h] * tre[i + 1]; qi += bu[h] * tim[i + 1]; }
           // (-i f) (qr + i qi) = f qi - i f qr
           nre[h] = f * qi;
           nim[h] = -f * qr;
@@ -1491,18 +1572,10 @@ __device__ void tridiag_expm_e1(const double* al, const double* be, int n,
         if (i < n) {
           tre[i] = nre[h]; tim[i] = nim[h];
           yre[i] += nre[h]; yim[i] += nim[h];
-          tn += nre[h] * nre[h] + nim[h] * nim[h];
-          an += yre[i] * yre[i] + yim[i] * yim[i];
         }
       }
       __syncwarp();
-      for (int o = 16; o > 0; o >>= 1) {
-        tn += __shfl_xor_sync(full, tn, o);
-        an += __shfl_xor_sync(full, an, o);
-      }
-      if (tn <= 1e-34 * an) break;
     }
-    __syncwarp();
   }
   // undo the shift: multiply by exp(-i tau sigma)
   double sn, cs;
@@ -2401,27 +2474,33 @@ cudaError_t launch_expm(const BatchArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Column permutation of every row of a dim_up x dim_dn matrix, in place: one
-// CTA per row stages it in shared memory, then forward: x[u][i] =
-// x_old[u][order[i]] (ascending-word columns -> hop order); back:
-// x[u][order[i]] = x_old[u][i].
+// Column permutation of every row of a dim_up x dim_dn matrix, from src to
+// dst (the same matrix for the in-place form; either may be a pinned host
+// buffer mapped into the device's address space): one CTA per row stages it
+// in shared memory, then gathers dst[u][i] = src[u][g[i]], so that both the
+// row's reads and its writes are coalesced (a host row crosses the host link
+// once each way in whole lines).  g = order (ascending-word columns -> hop
+// order: dst[u][i] = src[u][order[i]]) or its inverse (back:
+// dst[u][order[i]] = src[u][i]).
 template <typename C>
-__global__ void __launch_bounds__(256) k_permute_cols(C* x, int dim_dn, const int32_t* order,
-                                                      int forward) {
+__global__ void __launch_bounds__(256) k_permute_cols(const C* src, C* dst, int dim_dn,
+                                                      const int32_t* g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* row = reinterpret_cast<C*>(smem_raw);
-  C* xr = x + (size_t)blockIdx.x * dim_dn;
-  for (int d = threadIdx.x; d < dim_dn; d += blockDim.x) row[d] = xr[d];
+  const C* sr = src + (size_t)blockIdx.x * dim_dn;
+  C* dr = dst + (size_t)blockIdx.x * dim_dn;
+#pragma unroll 4
+  for (int d = threadIdx.x; d < dim_dn; d += blockDim.x) row[d] = sr[d];
   __syncthreads();
-  if (forward)
-    for (int i = threadIdx.x; i < dim_dn; i += blockDim.x) xr[i] = row[__ldg(order + i)];
-  else
-    for (int i = threadIdx.x; i < dim_dn; i += blockDim.x) xr[__ldg(order + i)] = row[i];
+#pragma unroll 4
+  for (int i = threadIdx.x; i < dim_dn; i += blockDim.x) dr[i] = row[__ldg(g + i)];
 }
 
-cudaError_t launch_permute_cols(bool fp64, void* x, int dim_up, int dim_dn, const int32_t* order,
-                                bool forward, cudaStream_t s) {
-  if (dim_up < 1 || dim_dn < 2) return cudaSuccess;   // nothing to permute
+// order: the permutation (position -> rank) followed by its inverse, 2 dim_dn
+// entries
+static cudaError_t permute_cols(bool fp64, const void* src, void* dst, int dim_up, int dim_dn,
+                                const int32_t* order, bool forward, cudaStream_t s) {
+  const int32_t* g = forward ? order : order + dim_dn;
   const size_t smem = (size_t)dim_dn * (fp64 ? 16 : 8);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -2429,16 +2508,30 @@ cudaError_t launch_permute_cols(bool fp64, void* x, int dim_up, int dim_dn, cons
     e = cudaFuncSetAttribute(k_permute_cols<double2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_permute_cols<double2><<<dim_up, 256, smem, s>>>(static_cast<double2*>(x), dim_dn, order,
-                                                      forward ? 1 : 0);
+    k_permute_cols<double2><<<dim_up, 256, smem, s>>>(static_cast<const double2*>(src),
+                                                      static_cast<double2*>(dst), dim_dn, g);
   } else {
     e = cudaFuncSetAttribute(k_permute_cols<float2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_permute_cols<float2><<<dim_up, 256, smem, s>>>(static_cast<float2*>(x), dim_dn, order,
-                                                     forward ? 1 : 0);
+    k_permute_cols<float2><<<dim_up, 256, smem, s>>>(static_cast<const float2*>(src),
+                                                     static_cast<float2*>(dst), dim_dn, g);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_permute_cols(bool fp64, void* x, int dim_up, int dim_dn, const int32_t* order,
+                                bool forward, cudaStream_t s) {
+  if (dim_up < 1 || dim_dn < 2) return cudaSuccess;   // nothing to permute
+  return permute_cols(fp64, x, x, dim_up, dim_dn, order, forward, s);
+}
+
+cudaError_t launch_permute_cols_copy(bool fp64, const void* src, void* dst, int dim_up,
+                                     int dim_dn, const int32_t* order, bool forward,
+                                     cudaStream_t s) {
+  if (dim_up < 1 || dim_dn < 1) return cudaSuccess;   // empty matrix
+  if (!src || !dst || !order) return cudaErrorInvalidValue;
+  return permute_cols(fp64, src, dst, dim_up, dim_dn, order, forward, s);
 }
 
 cudaError_t launch_tridiag_expm(const double* alpha, const double* beta, int n, double tau,

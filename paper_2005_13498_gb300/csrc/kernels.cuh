@@ -177,8 +177,15 @@ cudaError_t launch_overlap(bool fp64, const BatchArgs& a, const OverlapArgs& o,
                            int n_ew_blocks, cudaStream_t s);
 // In-place column permutation of each row of a dim_up x dim_dn complex
 // matrix (device): forward x[u][i] = x_old[u][order[i]], else the inverse.
+// order holds 2 dim_dn entries: the permutation, then its inverse.
 cudaError_t launch_permute_cols(bool fp64, void* x, int dim_up, int dim_dn, const int32_t* order,
                                 bool forward, cudaStream_t s);
+// The same from src to dst (distinct buffers; either may be a pinned host
+// buffer's device-mapped address): forward dst[u][i] = src[u][order[i]],
+// else dst[u][order[i]] = src[u][i]; dim_dn = 1 copies.
+cudaError_t launch_permute_cols_copy(bool fp64, const void* src, void* dst, int dim_up,
+                                     int dim_dn, const int32_t* order, bool forward,
+                                     cudaStream_t s);
 // out[c * rows + r] = in[r * cols + c] for a rows x cols complex matrix.
 cudaError_t launch_transpose(bool fp64, const void* in, void* out, int rows, int cols,
                              cudaStream_t s);

@@ -18,7 +18,15 @@ pytestmark = pytest.mark.gpu
 def run_gpu(ed, torch, lat, nu, nd, U, psi0, pulse, dt, n, m, dtype, energy=False,
             host=False, profile=False):
     h = ed.Hubbard(lat, nu, nd, U)
-    if host:
+    if host == "pinned":
+        # pinned host memory: read and written by the library's permutation
+        # kernel over the host link
+        x = torch.from_numpy(np.array(psi0, dtype=np.complex128 if dtype == "c128"
+                                      else np.complex64, copy=True)).pin_memory()
+        out = ed.ed_propagate(h.ctx, x, ed_dtype(ed, dtype), pulse, 0.0, dt, n, m,
+                              energy=energy, profile=profile)
+        psi = x.numpy().astype(np.complex128)
+    elif host:
         # a private copy: the library writes the result into this buffer
         x = np.array(psi0, dtype=np.complex128 if dtype == "c128" else np.complex64,
                      copy=True)
@@ -145,7 +153,8 @@ def test_stationary_ground_state(ed_lib):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_host_pointer_and_profile_paths(ed_lib, dtype):
-    """Host buffers (copied in and out by the library) and the profiled
+    """Pageable host buffers (copied in and out by the library), pinned host
+    buffers (read and written by its permutation kernel) and the profiled
     launch path give the same result as device buffers with a CUDA graph."""
     torch = torch_cuda()
     lat = LATTICES["triangle"]
@@ -155,9 +164,34 @@ def test_host_pointer_and_profile_paths(ed_lib, dtype):
     b, ob = run_gpu(ed_lib, torch, lat, 2, 1, 2.0, psi0, pulse, 0.05, 20, 6, dtype, host=True)
     c, oc = run_gpu(ed_lib, torch, lat, 2, 1, 2.0, psi0, pulse, 0.05, 20, 6, dtype,
                     profile=True)
-    assert np.array_equal(a, b) and np.array_equal(a, c)
-    assert np.array_equal(oa["docc"], ob["docc"])
+    d, od = run_gpu(ed_lib, torch, lat, 2, 1, 2.0, psi0, pulse, 0.05, 20, 6, dtype,
+                    host="pinned")
+    assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
+    assert np.array_equal(oa["docc"], ob["docc"]) and np.array_equal(oa["docc"], od["docc"])
     assert oc["kernel_launches"][0] > 0 and oc["kernel_ms"][0] > 0
+
+
+@pytest.mark.parametrize("name,nu,nd,dtype", [("ladder2x7", 7, 7, "c64"),
+                                               ("ring7", 3, 2, "c128")])
+def test_pinned_host_state_equals_device_state(ed_lib, name, nu, nd, dtype):
+    """A pinned host state, read and written by the permutation kernel over
+    the host link, ends bit-equal to the same state kept on the device: the
+    Ns=14 ladder (rows of 3432 columns, every column moved by the hop order)
+    and a 7-site ring with rows of 21 columns."""
+    torch = torch_cuda()
+    if name == "ring7":
+        lat = synth.ring(7)
+        pulse = {"A0": 0.5, "omega": 8.0, "sigma": 2.0, "t0": 0.2, "dir": (1.0, 0, 0)}
+    else:
+        lat = LATTICES[name]
+        pulse = synth.workload(name)["pulse_params"]
+    D = oracle.sector_dims(lat["Ns"], nu, nd)[2]
+    psi0 = synth.complex_normal(D, 21)
+    a, oa = run_gpu(ed_lib, torch, lat, nu, nd, 8.0, psi0, pulse, 0.02, 2, 12, dtype)
+    b, ob = run_gpu(ed_lib, torch, lat, nu, nd, 8.0, psi0, pulse, 0.02, 2, 12, dtype,
+                    host="pinned")
+    assert np.array_equal(a, b)
+    assert np.array_equal(oa["docc"], ob["docc"]) and np.array_equal(oa["norm2"], ob["norm2"])
 
 
 def test_repeated_calls_reuse_and_resume(ed_lib):
