@@ -30,6 +30,16 @@ typedef struct {
  * the first failing CUDA call (out partially filled).                       */
 int ed_probe_ceilings(ed_ceilings* out);
 
+/* Launch, once each, four one-warp kernels (k_probe_lds<0..3>) that load
+ * 16-byte words from shared memory in fixed patterns: one address for all
+ * lanes; 32 consecutive words; every quarter warp 2-way in four bank groups
+ * with the two quarters of each half warp in disjoint groups; every quarter
+ * warp 8-way.  The call only launches them; the wavefronts each pattern
+ * costs are read with a profiler.  Allocates 128 bytes of device memory for
+ * the duration of the call.  Returns 0, or the cudaError_t code of the first
+ * failing CUDA call.                                                          */
+int ed_probe_shared_loads(void);
+
 #ifdef __cplusplus
 }
 #endif

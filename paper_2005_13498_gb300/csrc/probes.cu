@@ -234,3 +234,53 @@ extern "C" int ed_probe_ceilings(ed_ceilings* out) {
   cudaFree(sink);
   return 0;
 }
+
+namespace {
+
+// Access patterns of 16-byte shared-memory loads, one warp, for reading the
+// wavefronts each pattern costs with a profiler
+// (l1tex__data_pipe_lsu_wavefronts_mem_shared_op_ld.sum over
+// smsp__inst_executed_op_shared_ld.sum).  Every index is masked to the
+// 256 float4 words of the buffer.
+//   MODE 0: one address for all lanes (a broadcast)
+//   MODE 1: 32 consecutive words (conflict-free)
+//   MODE 2: every quarter warp 2-way in four bank groups, the two quarters
+//           of each half warp in disjoint bank groups (8 wavefronts if
+//           conflicts are resolved per quarter warp, 4 if per half warp)
+//   MODE 3: the eight lanes of every quarter warp in one bank group, the
+//           four quarters at the same addresses (8-way)
+template <int MODE>
+__global__ void __launch_bounds__(32) k_probe_lds(float* out, int salt) {
+  __shared__ float4 buf[256];
+  const int l = threadIdx.x;
+  for (int i = l; i < 256; i += 32) buf[i] = make_float4(i, i + 1, i + 2, i + 3);
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int it = 0; it < 1024; ++it) {
+    int idx;
+    if (MODE == 0) idx = (it * 7 + salt) & 255;
+    else if (MODE == 1) idx = (l + 32 * (it & 7)) & 255;
+    else if (MODE == 2)
+      idx = ((((l & 7) >> 1) + 4 * ((l >> 3) & 1)) + 8 * ((l & 1) + 2 * (l >> 4)) + 32 * (it & 3)) & 255;
+    else idx = ((l & 7) * 8 + (it & 7)) & 255;
+    const float4 v = buf[idx];
+    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+  }
+  out[l] = acc.x + acc.y + acc.z + acc.w;
+}
+
+}  // namespace
+
+extern "C" int ed_probe_shared_loads(void) {
+  float* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 32 * sizeof(float));
+  if (e != cudaSuccess) return (int)e;
+  k_probe_lds<0><<<1, 32>>>(d, 3);
+  k_probe_lds<1><<<1, 32>>>(d, 3);
+  k_probe_lds<2><<<1, 32>>>(d, 3);
+  k_probe_lds<3><<<1, 32>>>(d, 3);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d);
+  return (int)e;
+}

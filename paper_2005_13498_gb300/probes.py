@@ -21,6 +21,8 @@ def _load():
     lib = ctypes.CDLL(path)
     lib.ed_probe_ceilings.argtypes = [ctypes.POINTER(ed_ceilings)]
     lib.ed_probe_ceilings.restype = ctypes.c_int
+    lib.ed_probe_shared_loads.argtypes = []
+    lib.ed_probe_shared_loads.restype = ctypes.c_int
     return lib
 
 
@@ -34,3 +36,10 @@ def ed_probe_ceilings():
     if rc != 0:
         raise RuntimeError(f"ed_probe_ceilings failed with CUDA error {rc}")
     return {k: getattr(c, k) for k, _ in ed_ceilings._fields_}
+
+
+def ed_probe_shared_loads():
+    """Launch the four shared-memory load-pattern kernels (include/ed_probes.h)."""
+    rc = lib.ed_probe_shared_loads()
+    if rc != 0:
+        raise RuntimeError(f"ed_probe_shared_loads failed with CUDA error {rc}")
