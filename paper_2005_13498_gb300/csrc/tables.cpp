@@ -99,25 +99,10 @@ std::string make_lattice(LatticeHost& L, int Ns, int n_bonds, const int32_t* p,
   return "";
 }
 
-// Distributes the entries of 64 column lists (column l = 2 * lane + h) over
-// K slots, each list in its own column of the slots, so that the loads one
-// gather instruction makes (one slot, one h, 32 lanes) are spread over the
-// shared-memory banks.  The hardware serves a 16-byte-per-lane load a quarter
-// warp (8 lanes) at a time; sources of distinct rank mod 8 fall in distinct
-// 16-byte bank groups (16-byte columns: rank mod 8; 32-byte swizzled
-// columns: 2 (rank mod 4) + bit 2 of rank, also a bijection of rank mod 8).
-// Per quarter warp and h this is an edge colouring of a bipartite multigraph:
-// lanes on one side, bank groups on the other, an edge per entry, a colour
-// per slot; a slot whose entries all have distinct bank groups costs one
-// shared-memory wavefront.  A bank group with more than K entries is split
-// into virtual groups of at most K, so that every vertex has degree <= K and
-// K colours suffice (Konig's theorem); the colouring follows the alternating
-// path argument of that theorem, one edge at a time.  A lane with fewer
-// entries than K leaves slots empty: it reads one of the eight zero columns
-// dim .. dim + 7, the same one for every empty lane of the quarter warp (a
-// broadcast), picked in a bank group the quarter warp's real entries leave
-// free, so empty slots need no test in the kernel.  Returns [K][64] entries
-// (rank | sign << 31).
+// One quarter warp and h of assign_slots: the entries of its 8 lanes'
+// lists as the edges of a bipartite multigraph (lanes x virtual bank
+// groups), coloured with K colours; slot_of[i * maxlen + j] receives the
+// colour (slot) of entry j of lane i.
 static void colour_quarter(const std::vector<uint32_t>* lists8, int K,
                            std::vector<int>& slot_of /* [8 * maxlen] */, int maxlen) {
   struct Edge { int lane, vb, col; };
@@ -174,6 +159,25 @@ static void colour_quarter(const std::vector<uint32_t>* lists8, int K,
     for (size_t j = 0; j < lists8[i].size(); ++j, ++k) slot_of[(size_t)i * maxlen + j] = E[k].col;
 }
 
+// Distributes the entries of 64 column lists (column l = 2 * lane + h) over
+// K slots, each list in its own column of the slots, so that the loads one
+// gather instruction makes (one slot, one h, 32 lanes) are spread over the
+// shared-memory banks.  The hardware serves a 16-byte-per-lane load a quarter
+// warp (8 lanes) at a time; sources of distinct rank mod 8 fall in distinct
+// 16-byte bank groups (16-byte columns: rank mod 8; 32-byte swizzled
+// columns: 2 (rank mod 4) + bit 2 of rank, also a bijection of rank mod 8).
+// Per quarter warp and h this is an edge colouring of a bipartite multigraph:
+// lanes on one side, bank groups on the other, an edge per entry, a colour
+// per slot; a slot whose entries all have distinct bank groups costs one
+// shared-memory wavefront.  A bank group with more than K entries is split
+// into virtual groups of at most K, so that every vertex has degree <= K and
+// K colours suffice (Konig's theorem); the colouring follows the alternating
+// path argument of that theorem, one edge at a time.  A lane with fewer
+// entries than K leaves slots empty: it reads one of the eight zero columns
+// dim .. dim + 7, the same one for every empty lane of the quarter warp (a
+// broadcast), picked in a bank group the quarter warp's real entries leave
+// free, so empty slots need no test in the kernel.  Returns [K][64] entries
+// (rank | sign << 31).
 static std::vector<uint32_t> assign_slots(const std::vector<std::vector<uint32_t>>& lists, int K,
                                           uint32_t dim) {
   std::vector<uint32_t> out((size_t)K * 64, kEllNull);
